@@ -1,0 +1,475 @@
+#!/usr/bin/env python3
+"""Benchmark of the BYO hot path on GB300: BFS, CC, PageRank and TC on one graph.
+
+One step = one pass of the whole path over a resident graph: BFS from S
+seeded non-isolated sources (levels + parents), connected components,
+PageRank (d = 0.85, 20 iterations), triangle count.  The metric is traversed
+edges per second over the step (GTEPS), with each algorithm's edges counted by
+its usual convention:
+  BFS  undirected edges in the source's component, per source (Graph500)
+  CC   m/2 (every undirected edge once)
+  PR   20 * m (every stored entry, every iteration)
+  TC   m
+``value`` times the step with the graph already in HBM; ``e2e`` times the same
+step through the C ABI from host buffers: pinned host -> device copy of the
+pair arrays, CSR build, the four algorithms, device -> host copy of levels,
+labels and ranks.
+
+  python bench.py [--gpus N --steps K --warmup W --workload rmat25 --sources 8]
+  python bench.py --impl reference ...   # the serial CPU oracle, bounded sample
+
+N > 1 (torchrun, one rank per GPU) runs independent replicas: the path does not
+shard (replicas only), so value = edges of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS & % HBM roofline (BFS/PR/CC/TC, RMAT-25); learned vs heuristic schedule"
+PR_ITERS = 20
+DAMPING = 0.85
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="byo", choices=["byo", "reference"])
+    ap.add_argument("--workload", default="rmat25")
+    ap.add_argument("--sources", type=int, default=8)
+    ap.add_argument("--sched", default="heuristic", choices=["heuristic", "push", "pull", "learned"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedules", action="store_true", help="also time BFS under every schedule")
+    ap.add_argument("--sample-scale", type=int, default=18, help="RMAT scale of the oracle's bounded sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def dev_u32(torch, a):
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if one exists for
+    this kernel and workload (profiles/traffic.json); None otherwise."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(workload, {}).get(kernel)
+        return None if e is None else float(e)
+    except (OSError, ValueError):
+        return None
+
+
+def sched_struct(byo, name, mlp=None):
+    mode = {"heuristic": byo.BYO_SCHED_HEURISTIC, "push": byo.BYO_SCHED_PUSH, "pull": byo.BYO_SCHED_PULL,
+            "learned": byo.BYO_SCHED_LEARNED}[name]
+    return byo.make_sched(mode, 16, 1024, 15.0, 18.0, mlp)
+
+
+def load_mlp(byo):
+    import numpy as np
+    p = os.path.join(ROOT, "paper_2405_11671_gb300", "sched_mlp.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        prm = np.array(json.load(f)["params"], np.float32)
+    m = byo.byo_mlp_create(0)
+    byo.byo_mlp_set_params(m, prm)
+    return m
+
+
+# ----------------------------------------------------------------------------- algorithmic bytes
+
+def algo_bytes(kernel: str, n: int, m: int, off: int, trace=None) -> float | None:
+    """Bytes the method must move per launch of `kernel` (a model, not a counter)."""
+    if kernel == "pr_iter":
+        # offsets + neighbour ids + one read of every contribution + vertex order
+        # + read/write rank + write next contribution
+        return off * (n + 1) + 4.0 * m + 4.0 * n * 5
+    if kernel == "bfs_persistent" and trace is not None:
+        b = 8.0 * n + n / 8.0  # level + parent init, visited bits
+        for r in trace:
+            if r.direction == 1:   # push: offsets and ids of F, queue in/out, level/parent/bits of F'
+                b += 2 * off * r.frontier + 4.0 * r.edges_examined + 4.0 * r.frontier
+            else:                  # pull: offsets of the unvisited, ids scanned, 3 bit arrays
+                b += 2 * off * r.unvisited + 4.0 * r.edges_examined + 3 * n / 8.0
+        nxt = [r.frontier for r in trace[1:]] + [0]
+        b += 12.0 * sum(nxt)
+        return b
+    if kernel == "cc_hook":
+        return off * (n + 1) + 4.0 * n + 4.0 * (m / 2 + n) + 8.0 * (m / 2)
+    if kernel == "tc_outdeg" or kernel == "tc_fill":
+        return off * (n + 1) + 4.0 * n + 4.0 * m + 2 * off * m + (4.0 * m / 2 if kernel == "tc_fill" else 4.0 * n)
+    return None
+
+
+# ----------------------------------------------------------------------------- oracle sample
+
+def cpu_baseline(sample_scale: int, sources: int):
+    """The serial oracle on a bounded sample of the same workload family."""
+    import numpy as np
+
+    import graphgen
+    import oracle
+    n, src, dst = graphgen.rmat_small(sample_scale, 16, graphgen.SEEDS["rmat25"])
+    g = oracle.csr_build(n, src, dst)
+    srcs = graphgen.pick_sources(n, src, dst, sources, graphgen.SEEDS["rmat25"] + 1)
+    deg = np.diff(g.off).astype(np.int64)
+    t0 = time.perf_counter()
+    bfs_edges = 0
+    for s in srcs:
+        lv, _ = oracle.bfs(g, int(s))
+        bfs_edges += int(deg[lv != oracle.INF].sum()) // 2
+    oracle.cc(g)
+    oracle.pagerank(g, DAMPING, PR_ITERS)
+    oracle.tc(g)
+    dt = time.perf_counter() - t0
+    edges = bfs_edges + g.m // 2 + PR_ITERS * g.m + g.m
+    return {"value": edges / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"RMAT scale {sample_scale} ef16 (same a,b,c,d, ids permuted), {len(srcs)} BFS sources + "
+                      f"CC + PR20 + TC, serial oracle, {dt:.2f} s",
+            "seconds": dt, "host": platform.machine()}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import graphgen
+    import oracle
+    graphgen.build()
+    oracle.build()
+    vals = []
+    for _ in range(max(args.warmup, 0)):
+        cpu_baseline(max(args.sample_scale - 2, 8), args.sources)
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(args.sample_scale, args.sources)
+        vals.append(cb["seconds"])
+    v = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32",
+            "data": "synthetic", "config": {"workload": f"rmat{args.sample_scale} sample of {args.workload}",
+                                            "sources": args.sources, "pr_iters": PR_ITERS},
+            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import graphgen
+    from paper_2405_11671_gb300 import build as lib_build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        lib_build.build()
+    if dist:
+        dist.barrier()
+    import paper_2405_11671_gb300 as byo
+    byo.load()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # ---- inputs (seeded, synthetic; replicas use the same graph)
+    n, src, dst = graphgen.workload(args.workload)
+    srcs = graphgen.pick_sources(n, src, dst, args.sources, graphgen.SEEDS.get(args.workload, 0) + 1)
+    S = len(srcs)
+    src_d, dst_d = dev_u32(torch, src), dev_u32(torch, dst)
+    flags = byo.BYO_CSR | byo.BYO_SYMMETRIZE | (byo.BYO_OFFSETS64 if args.workload.startswith("rmat") else 0)
+    torch.cuda.synchronize()
+    tb0 = time.perf_counter()
+    g = byo.Graph(n, src_d, dst_d, flags)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - tb0
+    m = g.m
+    off_bytes = 8 if (flags & byo.BYO_OFFSETS64) or m >= 2 ** 32 else 4
+    levels = torch.empty((S, n), dtype=torch.int32, device="cuda")
+    parents = torch.empty((S, n), dtype=torch.int32, device="cuda")
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    ranks = torch.empty(n, dtype=torch.float32, device="cuda")
+    mlp = load_mlp(byo) if args.sched == "learned" else None
+    if args.sched == "learned" and mlp is None:
+        raise SystemExit("--sched learned needs paper_2405_11671_gb300/sched_mlp.json (train it first)")
+    sp = sched_struct(byo, args.sched, mlp)
+    stream = torch.cuda.current_stream()
+    algos = ["bfs", "cc", "pr", "tc"]
+    ev = {a: [] for a in algos}
+    tri = {"count": None}
+
+    def step(record: bool):
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
+        if record:
+            marks[0].record(stream)
+        byo.byo_bfs(g.handle, srcs, levels, parents, sp)
+        if record:
+            marks[1].record(stream)
+        byo.byo_cc(g.handle, labels)
+        if record:
+            marks[2].record(stream)
+        byo.byo_pagerank(g.handle, DAMPING, PR_ITERS, ranks, want_residual=False)
+        if record:
+            marks[3].record(stream)
+        tri["count"] = byo.byo_tc(g.handle)
+        if record:
+            marks[4].record(stream)
+            for i, a in enumerate(algos):
+                ev[a].append((marks[i], marks[i + 1]))
+
+    for _ in range(max(args.warmup, 0)):
+        step(False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    byo.byo_profile_enable(True)
+    byo.byo_profile_reset()
+    launches0 = byo.byo_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = byo.byo_kernel_launches() - launches0
+    prof = byo.byo_profile_read()
+    byo.byo_profile_enable(False)
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = max_over_ranks(total_ms / args.steps)
+    algo_ms = {a: statistics.mean(x.elapsed_time(y) for x, y in ev[a]) for a in algos}
+
+    # ---- edges per step (from the parity-checked outputs)
+    deg = byo.byo_degree(g.handle).to(torch.int64)
+    reached = levels != -1
+    bfs_edges = int((reached.to(torch.int64) * deg.unsqueeze(0)).sum().item()) // 2
+    edges = {"bfs": bfs_edges, "cc": m // 2, "pr": PR_ITERS * m, "tc": m}
+    step_edges = sum(edges.values())
+    value = sum_over_ranks(step_edges) / (step_ms / 1e3) / 1e9
+    per_algo = {a: {"ms": round(algo_ms[a], 4), "gteps": round(edges[a] / (algo_ms[a] / 1e3) / 1e9, 3)}
+                for a in algos}
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    bfs_bytes = []
+    for s_ in srcs:  # one trace per source: the BFS launch processes one source
+        byo.byo_bfs(g.handle, [int(s_)], levels[:1], parents[:1], sp)
+        bfs_bytes.append(algo_bytes("bfs_persistent", n, m, off_bytes, byo.byo_bfs_trace(g.handle)))
+    trace = byo.byo_bfs_trace(g.handle)
+    tot = sum(v[1] for v in prof.values()) or 1.0
+    ranked = sorted(prof.items(), key=lambda kv: -kv[1][1])
+    roof = None
+    for name, (nl, ms) in ranked:
+        b = statistics.mean(bfs_bytes) if name == "bfs_persistent" else algo_bytes(name, n, m, off_bytes)
+        if b is None:
+            continue
+        avg_ms = ms / nl
+        achieved = b / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(name, args.workload),
+                "algorithmic_bytes_per_launch": b, "avg_launch_ms": round(avg_ms, 4),
+                "share": round(ms / tot, 4), "peak_kind": peak_kind}
+        break
+    kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot, 4)}
+                    for k, v in ranked}
+
+    # ---- schedules side by side (BFS only)
+    sched_cmp = None
+    if args.schedules:
+        sched_cmp = {}
+        cands = ["heuristic", "push", "pull"] + (["learned"] if load_mlp(byo) is not None else [])
+        for name in cands:
+            mm = load_mlp(byo) if name == "learned" else None
+            spx = sched_struct(byo, name, mm)
+            byo.byo_bfs(g.handle, srcs, levels, parents, spx)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                byo.byo_bfs(g.handle, srcs, levels, parents, spx)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 3
+            sched_cmp[name] = {"bfs_ms": round(ms, 4), "bfs_gteps": round(bfs_edges / (ms / 1e3) / 1e9, 3)}
+            if mm:
+                byo.byo_mlp_destroy(mm)
+
+    # ---- end to end through the C ABI from host buffers
+    e2e = None
+    if not args.no_e2e:
+        src_h = torch.from_numpy(np.ascontiguousarray(src, np.uint32).view(np.int32)).pin_memory()
+        dst_h = torch.from_numpy(np.ascontiguousarray(dst, np.uint32).view(np.int32)).pin_memory()
+        lv_h = torch.empty((S, n), dtype=torch.int32).pin_memory()
+        lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        rk_h = torch.empty(n, dtype=torch.float32).pin_memory()
+        g.close()
+        del src_d, dst_d
+        torch.cuda.synchronize()
+        e2e_steps = max(1, args.e2e_steps)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(e2e_steps):
+            sd = torch.empty_like(src_h, device="cuda")
+            dd = torch.empty_like(dst_h, device="cuda")
+            sd.copy_(src_h, non_blocking=True)
+            dd.copy_(dst_h, non_blocking=True)
+            ge = byo.Graph(n, sd, dd, flags)
+            byo.byo_bfs(ge.handle, srcs, levels, parents, sp)
+            byo.byo_cc(ge.handle, labels)
+            byo.byo_pagerank(ge.handle, DAMPING, PR_ITERS, ranks, want_residual=False)
+            byo.byo_tc(ge.handle)
+            lv_h.copy_(levels, non_blocking=True)
+            lab_h.copy_(labels, non_blocking=True)
+            rk_h.copy_(ranks, non_blocking=True)
+            torch.cuda.synchronize()
+            ge.close()
+            del sd, dd
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps)
+        e2e = {"value": round(sum_over_ranks(step_edges) / (e2e_ms / 1e3) / 1e9, 3), "unit": "GTEPS",
+               "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(src_h.numel() * 8),
+               "d2h_bytes_per_step": int(lv_h.numel() * 4 + lab_h.numel() * 4 + rk_h.numel() * 4 + 8)}
+    else:
+        g.close()
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(args.sample_scale, args.sources)
+        cb.pop("seconds", None)
+        cb.pop("host", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
+                "config": {"workload": args.workload, "n": n, "m": m, "draws": int(len(src)),
+                           "offsets": f"u{8 * off_bytes}", "sources": S, "pr_iters": PR_ITERS,
+                           "sched": args.sched, "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "inputs larger than L2 (graph >> 129 MB)", "build_s": round(build_s, 3),
+                           "triangles": tri["count"]},
+                "algos": per_algo, "edges_per_step": edges, "roofline": roof, "kernels": kernel_share,
+                "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cb}
+        if sched_cmp is not None:
+            line["schedules"] = sched_cmp
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

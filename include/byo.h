@@ -1,0 +1,240 @@
+/*
+ * byo.h -- C ABI of libbyo.so, a GB300 (sm_103a) implementation of the graph
+ * container API and the driving graph algorithms of BYO (Wheatman et al.,
+ * "BYO: A Unified Framework for Benchmarking Large-Scale Graph Containers",
+ * arXiv 2405.11671).
+ *
+ * Conventions for every call
+ *   - Pointers are DEVICE pointers owned by the caller, unless the parameter
+ *     name starts with host_.  The library owns only what a byo_graph holds
+ *     (the container and its scratch) and frees it in byo_graph_destroy.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it; calls that return a host value or a
+ *     device-side status synchronise that stream before returning.
+ *   - Every call returns a byo_status; BYO_OK is 0.  byo_last_error() gives a
+ *     message for the last failure on the calling host thread.  Nothing is
+ *     thrown across the ABI and the library never exits the process.
+ *   - Vertex ids are uint32 in [0, n); "INF" is 0xFFFFFFFF.
+ *   - A byo_graph may be read by several calls at once only if they run on
+ *     the same stream: its scratch is shared.
+ */
+#ifndef BYO_H
+#define BYO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum byo_status {
+  BYO_OK = 0,
+  BYO_ERR_INVALID_ARG = 1,   /* bad pointer, size, id >= n, or flag combination */
+  BYO_ERR_OUT_OF_MEMORY = 2, /* a device allocation failed; nothing was changed */
+  BYO_ERR_CUDA = 3,          /* a CUDA runtime call or a kernel launch failed */
+  BYO_ERR_TIMEOUT = 4,       /* a device-side wait gave up (BYO_TIMEOUT_MS, default 10000) */
+  BYO_ERR_UNSUPPORTED = 5,   /* e.g. a batch update on a static CSR */
+  BYO_ERR_NOT_SYMMETRIC = 6  /* BYO_SYMMETRIZE not given and some (u,v) lacks (v,u) */
+} byo_status;
+
+#define BYO_INF 0xFFFFFFFFu
+
+/* byo_graph_build flags */
+#define BYO_CSR 0x1u        /* static compressed sparse row container */
+#define BYO_DYNAMIC 0x2u    /* dynamic blocked-adjacency container (batch updates) */
+#define BYO_SYMMETRIZE 0x4u /* store every input pair (u,v) also as (v,u) */
+#define BYO_OFFSETS64 0x8u  /* CSR offsets as uint64 even when m < 2^32 */
+
+typedef struct byo_graph byo_graph;
+
+/* Message for the last failed call on this host thread ("" if none). */
+const char* byo_last_error(void);
+
+/*
+ * Build a graph container from k raw pairs src[i] -> dst[i] (device arrays).
+ * Follows the graph model of Section 3 (vertices 0..n-1, a neighbour SET per
+ * vertex, Section 3.1) and the CSR layout named in Section 4.2: duplicate
+ * pairs collapse, self-loops are dropped, neighbours are stored ascending.
+ * With BYO_SYMMETRIZE each pair is stored in both directions; without it the
+ * input must already be symmetric (BYO_ERR_NOT_SYMMETRIC otherwise), since
+ * every algorithm here is for undirected graphs (Section 6.2).
+ * Offsets are uint64 when BYO_OFFSETS64 is set or m >= 2^32, else uint32.
+ * The input arrays are only read; *out receives a new handle.
+ * Synchronises the stream (to learn m).  Errors: INVALID_ARG (NULL pointers
+ * with k > 0, id >= n, no container flag), OUT_OF_MEMORY, CUDA.
+ */
+byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t k, uint32_t flags,
+                           void* stream, byo_graph** out);
+
+/* Free a handle and everything it owns (NULL is accepted).  Synchronises the device. */
+byo_status byo_graph_destroy(byo_graph* g);
+
+/* num_vertices() of the GraphContainer API (Section 4.2). */
+byo_status byo_num_vertices(const byo_graph* g, uint32_t* host_n);
+
+/* num_edges() of the GraphContainer API (Section 4.2): stored directed entries m
+ * (2x the undirected edge count).  Kept as graph metadata (Section 4.3). */
+byo_status byo_num_edges(const byo_graph* g, uint64_t* host_m);
+
+/* degree(i) of the GraphContainer API (Section 4.2) for k vertex ids vs[]
+ * (device), written to out[k]; vs == NULL means all n vertices (out[n]).
+ * Ids >= n give BYO_ERR_INVALID_ARG (checked on the device; synchronises). */
+byo_status byo_degree(const byo_graph* g, const uint32_t* vs, uint64_t k, uint32_t* out, void* stream);
+
+/* Copy the container out as a CSR: offsets[n+1] (uint64) and col[m], neighbours
+ * ascending.  For a dynamic container this is the snapshot used to compare its
+ * contents after each batch. */
+byo_status byo_graph_export_csr(const byo_graph* g, uint64_t* offsets, uint32_t* col, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Schedules: which edgeMap direction (Section 3.2, sparse/push vs           */
+/* dense/pull, chosen from degree and num_edges as Section 6.3 describes)   */
+/* and which degree bins a push iteration uses.                             */
+typedef enum byo_sched_mode {
+  BYO_SCHED_HEURISTIC = 0, /* Beamer-style direction switch with alpha/beta below */
+  BYO_SCHED_LEARNED = 1,   /* the schedule network picks each iteration (needs mlp) */
+  BYO_SCHED_PUSH = 2,      /* sparse edgeMap every iteration */
+  BYO_SCHED_PULL = 3       /* dense edgeMap every iteration */
+} byo_sched_mode;
+
+typedef struct byo_mlp byo_mlp;
+
+typedef struct byo_sched {
+  uint32_t mode;       /* byo_sched_mode */
+  uint32_t thr_thread; /* push: degree < thr_thread -> one thread per vertex (power of two, >= 1) */
+  uint32_t thr_warp;   /* push: degree < thr_warp -> one warp per vertex, else CTA chunks (power of two) */
+  float alpha;         /* heuristic: push -> pull when frontier edges > unvisited edges / alpha */
+  float beta;          /* heuristic: pull -> push when frontier vertices < n / beta */
+  const byo_mlp* mlp;  /* LEARNED only */
+} byo_sched;
+
+/* ------------------------------------------------------------------------ */
+/* Schedule network (not in the paper: it only picks among equivalent       */
+/* execution paths, so results never depend on it).  A 12 -> 32 -> 32 -> 4  */
+/* ReLU MLP over the frontier features of one BFS iteration (the fields of   */
+/* byo_bfs_iter), outputs = scores of the 4 schedule actions.  Parameters    */
+/* are FP32, packed W1[32][12], b1[32], W2[32][32], b2[32], W3[4][32], b3[4]. */
+
+/* Number of FP32 parameters (1,604). */
+uint32_t byo_mlp_num_params(void);
+
+/* New network with He-uniform weights drawn from `seed` (biases zero). */
+byo_status byo_mlp_create(uint64_t seed, byo_mlp** out);
+byo_status byo_mlp_destroy(byo_mlp* m);
+
+/* Copy the parameters to / from a HOST array of byo_mlp_num_params() floats
+ * (save / load).  Setting parameters resets the optimiser state. */
+byo_status byo_mlp_get_params(const byo_mlp* m, float* host_params);
+byo_status byo_mlp_set_params(byo_mlp* m, const float* host_params);
+
+/* Loss and gradient on a batch: X[B][12] features, y[B] action labels, w[B]
+ * sample weights (nullable = 1), all device arrays.  L = sum_i w_i *
+ * CE(softmax(z_i), y_i) / sum_i w_i.  grad (nullable, device, num_params
+ * floats) receives dL/dparams; *host_loss (nullable) the loss (synchronises). */
+byo_status byo_mlp_loss_grad(byo_mlp* m, const float* X, const int32_t* y, const float* w, uint32_t B,
+                             float* grad, float* host_loss, void* stream);
+
+/* `epochs` full-batch Adam steps (lr, betas 0.9/0.999) on the same loss;
+ * *host_loss (nullable) receives the final loss (synchronises). */
+byo_status byo_mlp_train(byo_mlp* m, const float* X, const int32_t* y, const float* w, uint32_t B,
+                         uint32_t epochs, float lr, float* host_loss, void* stream);
+
+/* actions[i] = argmax of the network output for X[i] (device arrays). */
+byo_status byo_mlp_predict(const byo_mlp* m, const float* X, uint32_t B, int32_t* actions, void* stream);
+
+/* Defaults: HEURISTIC, thr_thread 16, thr_warp 1024, alpha 15, beta 18. */
+byo_sched byo_sched_default(void);
+
+/*
+ * Breadth-first search (the paper's BFS, Section 6.2, expressed with edgeMap
+ * over a vertexSubset, Section 3.2) from each of num_sources sources, one after
+ * another.  levels[i*n + v] = hop distance of v from sources[i], INF if
+ * unreached.  parents (nullable) [i*n + v] = a neighbour of v one level closer
+ * (sources[i] for the source itself, INF if unreached); push iterations may
+ * pick any such neighbour, pull iterations pick the first one in ascending id
+ * order.  sources is a HOST array.  sched NULL = byo_sched_default().
+ * The whole traversal of one source runs in one persistent cooperative launch:
+ * no host round trip per iteration.  Synchronises the stream.
+ * Errors: INVALID_ARG (source >= n, NULL levels), TIMEOUT, CUDA.
+ */
+byo_status byo_bfs(const byo_graph* g, const uint32_t* host_sources, uint32_t num_sources, uint32_t* levels,
+                   uint32_t* parents, const byo_sched* sched, void* stream);
+
+/* Per-iteration record of the last byo_bfs source on this graph.  These are
+ * the schedule features (and, with t_ns, the training data of the schedule
+ * network). */
+typedef struct byo_bfs_iter {
+  uint32_t level;           /* frontier level processed */
+  uint32_t direction;       /* 0 = pull, 1 = push */
+  uint32_t action;          /* schedule action (0 = pull, 1..3 = push bin settings) */
+  uint32_t frontier;        /* |F| */
+  uint64_t frontier_edges;  /* sum of degrees over F */
+  uint64_t edges_examined;  /* neighbour ids read in this iteration */
+  uint64_t unvisited_edges; /* sum of degrees over vertices not yet visited (F excluded) */
+  uint32_t unvisited;       /* vertices not yet visited (F excluded) */
+  uint32_t hist[4];         /* |F| split by degree: < 4, < 32, < 256, >= 256 */
+  uint32_t reserved;
+  uint64_t t_ns;            /* device time of the iteration (globaltimer) */
+} byo_bfs_iter;
+
+/* Copy up to cap records (host array) of the last BFS source; *host_count gets
+ * the number of iterations.  Synchronises the stream. */
+byo_status byo_bfs_trace(const byo_graph* g, byo_bfs_iter* host_records, uint32_t cap, uint32_t* host_count,
+                         void* stream);
+
+/*
+ * Connected components (the paper's connectivity algorithm, Section 6.2):
+ * labels[v] = the minimum vertex id of v's component.  Concurrent union-find
+ * over every edge, hooking the larger root under the smaller, then full path
+ * compression.  labels is caller-owned device memory of n entries and doubles
+ * as the union-find parent array.  Errors: INVALID_ARG, CUDA.
+ */
+byo_status byo_cc(const byo_graph* g, uint32_t* labels, void* stream);
+
+/*
+ * PageRank (named in Section 6.2).  ranks[v] after `iters` iterations of
+ *   p_0 = 1/n,  p_{t+1}(v) = (1-d)/n + d*( sum_{u in N(v)} p_t(u)/deg(u) + D_t/n ),
+ * D_t = sum of p_t over degree-0 vertices.  Contributions p/deg are FP32 and
+ * summed per vertex with compensated (Neumaier) FP32 arithmetic; the dangling
+ * mass D_t and the L1 residual are reduced in FP64.  host_residual (nullable)
+ * receives sum_v |p_iters(v) - p_{iters-1}(v)|; if non-NULL the call
+ * synchronises.  Errors: INVALID_ARG (d outside [0,1], NULL ranks), CUDA.
+ */
+byo_status byo_pagerank(const byo_graph* g, float damping, uint32_t iters, float* ranks, double* host_residual,
+                        void* stream);
+
+/*
+ * Triangle count (Section 4.4: filter to a DAG, then intersect).  Each edge is
+ * kept in the direction of increasing (degree, id); the count is the sum over
+ * DAG edges u->v of |N+(u) intersect N+(v)|, with N+(u) staged in shared
+ * memory by TMA bulk copies.  *host_count receives the number of triangles;
+ * synchronises.  Errors: INVALID_ARG, OUT_OF_MEMORY, TIMEOUT, CUDA.
+ */
+byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Tracing.  Every kernel launch of the library increments a process-wide    */
+/* counter.  With profiling on, the main kernels of each call are bracketed  */
+/* by CUDA events on the caller's stream; byo_profile_read resolves them     */
+/* (synchronising) into per-kernel launch counts and device milliseconds.    */
+typedef struct byo_kernel_stat {
+  char name[48];
+  uint64_t launches;
+  double total_ms;
+} byo_kernel_stat;
+
+/* Kernels launched by this library in this process so far. */
+uint64_t byo_kernel_launches(void);
+byo_status byo_profile_enable(int on);
+/* Drop every recorded timing. */
+byo_status byo_profile_reset(void);
+/* Up to cap per-kernel records (host array) accumulated since the last reset;
+ * *host_count gets the number of distinct kernels. */
+byo_status byo_profile_read(byo_kernel_stat* host_stats, uint32_t cap, uint32_t* host_count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BYO_H */

@@ -1,0 +1,642 @@
+// bfs.cu -- breadth-first search by edgeMap over a vertexSubset (Section 3.2),
+// direction-optimising between the sparse (push) and dense (pull) forms with a
+// cutoff that uses degree and num_edges (Section 6.3), in ONE persistent
+// cooperative launch per source.
+//
+// Frontier representations (the vertexSubset of Section 3.2):
+//   sparse: the queue.  One array of n ids split into per-degree-bucket
+//           regions (bucket b >= 1 = degrees [2^(b-1), 2^b)); every vertex
+//           enters the frontier at most once, so each region is append-only
+//           across levels and level l's entries of bucket b are a contiguous
+//           run.  Binning by degree is therefore free, and a push iteration
+//           can pick its thread/warp/CTA split per iteration.
+//   dense:  a bit-vector (1 bit per vertex; Section 4.4 reports the bit array
+//           beating a bool array), double-buffered by level parity.
+// Push (sparse edgeMap): degree-binned.  Small-degree vertices: a warp takes
+//   32 of them and walks their concatenated edges 32 at a time (edge-balanced
+//   inside the warp); mid-degree: one warp per vertex; high degree: CTA-wide
+//   chunks of at most kChunk edges.  A neighbour is claimed in the visited bit
+//   array with one atomicOr per distinct 32-bit word per warp (same-word claims
+//   merged with __match_any_sync and a warp OR).
+// Pull (dense edgeMap): a warp owns one 32-vertex word of the visited bit
+//   array; each unvisited vertex scans its sorted neighbour list with 16-byte
+//   vector loads until the first neighbour in the frontier bit-vector
+//   (map_neighbors_early_exit, Section 4.2); high-degree vertices are scanned
+//   by the whole warp, 128 ids per step.  The warp writes its visited and next-
+//   frontier words without atomics, and appends the discovered vertices to the
+//   queue (warp-scan compaction), so both representations of the next
+//   frontier exist after a pull.
+#include <math.h>
+
+#include "byo_internal.cuh"
+#include "container.cuh"
+#include "prof.cuh"
+#include "sched.cuh"
+
+namespace byo {
+
+constexpr int kBfsThreads = 256;
+constexpr int kPullThreadMax = 32;  // pull: degrees above this are scanned by a whole warp
+constexpr uint32_t kChunk = 2048;   // push: edges per CTA work item in the CTA bin
+constexpr uint32_t kTraceCap = 1u << 16;
+
+struct BfsCtl {
+  GridBar bar;
+  uint32_t err;
+  uint32_t levels;
+  unsigned long long cnt[3][kBuckets];  // appends per bucket, by level mod 3
+  unsigned long long sdeg[3];           // sum of degrees of the frontier being built
+  unsigned long long scanned[3];        // neighbour ids read while building it
+};
+
+struct BfsWork {
+  uint32_t n = 0;
+  uint32_t nw = 0;
+  uint32_t* vis = nullptr;
+  uint32_t* fb = nullptr;  // 2 * nw words
+  uint32_t* queue = nullptr;
+  BfsCtl* ctl = nullptr;
+  byo_bfs_iter* trace = nullptr;
+};
+
+void bfs_free(BfsWork* w) {
+  if (!w) return;
+  dev_free(w->vis);
+  dev_free(w->fb);
+  dev_free(w->queue);
+  dev_free(w->ctl);
+  dev_free(w->trace);
+  delete w;
+}
+
+template <typename G>
+struct BfsArgs {
+  G g;
+  uint32_t src;
+  uint32_t* level;
+  uint32_t* parent;
+  uint32_t* vis;
+  uint32_t* fb;
+  uint32_t* queue;
+  const uint64_t* bstart;
+  BfsCtl* ctl;
+  byo_bfs_iter* trace;
+  SchedParams sp;
+  uint64_t limit_ns;
+  uint32_t nw;
+};
+
+namespace {
+
+struct BfsShared {
+  uint64_t bstart[kBuckets + 1];
+  uint64_t base[kBuckets];   // start of the current level's run inside each bucket region
+  uint64_t pre[kBuckets + 1];   // prefix of current counts over buckets
+  uint64_t preC[kBuckets + 1];  // prefix of CTA-bin work items (counts * chunks)
+  uint32_t cnt[kBuckets];
+  uint64_t nvis, mvis;
+  uint32_t nf;
+  uint64_t mf;
+  int dir, action, bt, bw, prev_dir;
+  int fb_valid;
+  uint64_t t_top;
+  float logits[kActions];
+};
+
+__device__ __forceinline__ int find_bucket(const uint64_t* pre, int lo, int hi, uint64_t i) {
+  // largest b in [lo, hi] with pre[b] <= i
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Warp-collective: claim v for every lane with `cand`, then record the
+// winners and append them to the next level's queue.  All 32 lanes call it.
+template <typename G, bool kParents>
+__device__ __forceinline__ void claim_emit(const BfsArgs<G>& a, BfsShared& S, bool cand, uint32_t v, uint32_t u,
+                                           uint32_t next_level, int nxt, uint64_t& acc_deg) {
+  const uint32_t lane = lane_id();
+  if (cand) cand = !((ld_cg(a.vis + (v >> 5)) >> (v & 31)) & 1u);
+  if (__ballot_sync(0xFFFFFFFFu, cand) == 0) return;
+  // one claim per distinct vertex, then one atomicOr per distinct word
+  uint32_t same_v = __match_any_sync(0xFFFFFFFFu, cand ? v : 0xFFFFFFFFu);
+  bool first = cand && (same_v & lanemask_lt()) == 0;
+  uint32_t same_w = __match_any_sync(0xFFFFFFFFu, first ? (v >> 5) : 0xFFFFFFFFu);
+  uint32_t bit = first ? (1u << (v & 31)) : 0u;
+  uint32_t orbits = __reduce_or_sync(same_w, bit);
+  uint32_t leader = __ffs(same_w) - 1;
+  uint32_t old = 0;
+  if (first && lane == leader) old = atomicOr(a.vis + (v >> 5), orbits);
+  old = __shfl_sync(0xFFFFFFFFu, old, leader);
+  bool won = first && !(old & bit);
+  uint32_t b = 0xFFFFFFFFu;
+  if (won) {
+    a.level[v] = next_level;
+    if (kParents) a.parent[v] = u;
+    uint32_t d = a.g.degree(v);
+    acc_deg += d;
+    b = (uint32_t)degree_bucket(d);
+  }
+  if (__ballot_sync(0xFFFFFFFFu, won) == 0) return;
+  uint32_t same_b = __match_any_sync(0xFFFFFFFFu, b);
+  uint32_t bl = __ffs(same_b) - 1;
+  unsigned long long pos = 0;
+  if (won && lane == bl) pos = atomicAdd(&a.ctl->cnt[nxt][b], (unsigned long long)__popc(same_b));
+  pos = __shfl_sync(0xFFFFFFFFu, pos, bl);
+  if (won) {
+    uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + pos + __popc(same_b & lanemask_lt());
+    if (at < S.bstart[b + 1]) a.queue[at] = v;
+    else atomicCAS(&a.ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is claimed once
+  }
+}
+
+template <typename G>
+__device__ __forceinline__ uint32_t frontier_vertex(const BfsArgs<G>& a, const BfsShared& S, int b, uint64_t i) {
+  return ld_cg(a.queue + S.bstart[b] + S.base[b] + i);
+}
+
+// ---------------------------------------------------------------- push
+template <typename G, bool kParents>
+__device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, uint32_t L, int nxt, uint64_t& acc_deg,
+                           uint64_t& acc_scan) {
+  const uint32_t lane = lane_id();
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int bt = S.bt, bw = S.bw;
+
+  // CTA bin: chunks of high-degree vertices
+  const uint64_t totC = S.preC[kBuckets] - S.preC[bw + 1];
+  for (uint64_t j = blockIdx.x; j < totC; j += gridDim.x) {
+    uint64_t jj = j + S.preC[bw + 1];
+    int b = find_bucket(S.preC, bw + 1, kBuckets - 1, jj);
+    uint64_t K = (b >= 12) ? (1ull << (b - 11)) : 1ull;  // chunks per vertex: 2^b / kChunk
+    uint64_t r = jj - S.preC[b];
+    uint32_t u = frontier_vertex(a, S, b, r / K);
+    uint32_t chunk = (uint32_t)(r % K);
+    Seg s = a.g.seg(u);
+    uint32_t per = (uint32_t)((s.len + K - 1) / K);
+    uint32_t lo = chunk * per, hi = min(s.len, lo + per);
+    for (uint32_t base = lo; base < hi; base += blockDim.x) {
+      uint32_t e = base + threadIdx.x;
+      bool ok = e < hi;
+      uint32_t v = ok ? __ldg(s.p + e) : 0;
+      if (ok) ++acc_scan;
+      claim_emit<G, kParents>(a, S, ok, v, u, L + 1, nxt, acc_deg);
+    }
+  }
+  // warp bin: one warp per vertex
+  const uint64_t w0 = S.pre[bt + 1], w1 = S.pre[bw + 1];
+  for (uint64_t j = w0 + gwarp; j < w1; j += nwarps) {
+    int b = find_bucket(S.pre, bt + 1, bw, j);
+    uint32_t u = frontier_vertex(a, S, b, j - S.pre[b]);
+    Seg s = a.g.seg(u);
+    for (uint32_t base = 0; base < s.len; base += 32) {
+      uint32_t e = base + lane;
+      bool ok = e < s.len;
+      uint32_t v = ok ? __ldg(s.p + e) : 0;
+      if (ok) ++acc_scan;
+      claim_emit<G, kParents>(a, S, ok, v, u, L + 1, nxt, acc_deg);
+    }
+  }
+  // thread bin: 32 vertices per warp, their edges walked 32 at a time
+  const uint64_t t1 = S.pre[bt + 1];
+  for (uint64_t jb = (uint64_t)gwarp * 32; jb < t1; jb += (uint64_t)nwarps * 32) {
+    uint64_t j = jb + lane;
+    uint32_t u = 0;
+    Seg s{nullptr, 0};
+    if (j < t1) {
+      int b = find_bucket(S.pre, 0, bt, j);
+      u = frontier_vertex(a, S, b, j - S.pre[b]);
+      s = a.g.seg(u);
+    }
+    uint32_t incl = s.len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    uint32_t excl = incl - s.len;
+    for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+      uint32_t e = e0 + lane;
+      // owner: the largest lane l with excl_l <= e
+      int owner = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        int probe = owner + step;
+        uint32_t ex = __shfl_sync(0xFFFFFFFFu, excl, probe & 31);
+        if (probe < 32 && ex <= e) owner = probe;
+      }
+      uint32_t oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
+      uint32_t ou = __shfl_sync(0xFFFFFFFFu, u, owner);
+      const uint32_t* op = reinterpret_cast<const uint32_t*>(
+          __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(s.p), owner));
+      bool ok = e < total;
+      uint32_t v = ok ? __ldg(op + (e - oex)) : 0;
+      if (ok) ++acc_scan;
+      claim_emit<G, kParents>(a, S, ok, v, ou, L + 1, nxt, acc_deg);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- pull
+__device__ __forceinline__ bool in_frontier(const uint32_t* fb, uint32_t u) {
+  return (ld_cg(fb + (u >> 5)) >> (u & 31)) & 1u;
+}
+
+template <typename G, bool kParents>
+__device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, uint32_t L, int nxt, uint64_t& acc_deg,
+                           uint64_t& acc_scan) {
+  const uint32_t lane = lane_id();
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t* fb = a.fb + (size_t)(L & 1) * a.nw;
+  uint32_t* fbn = a.fb + (size_t)((L + 1) & 1) * a.nw;
+  const uint32_t n = a.g.num_vertices();
+  for (uint32_t w = gwarp; w < a.nw; w += nwarps) {
+    uint32_t vw = ld_cg(a.vis + w);
+    uint32_t v = w * 32 + lane;
+    bool todo = v < n && !((vw >> lane) & 1u);
+    if (__ballot_sync(0xFFFFFFFFu, todo) == 0) {
+      if (lane == 0) fbn[w] = 0;
+      continue;
+    }
+    Seg s{nullptr, 0};
+    if (todo) s = a.g.seg(v);
+    bool found = false;
+    uint32_t par = kInf;
+    if (todo && s.len <= (uint32_t)kPullThreadMax && s.len > 0) {
+      const uint32_t* al = align16_down(s.p);
+      uint32_t head = (uint32_t)(s.p - al);
+      uint32_t end = head + s.len;
+      for (uint32_t i = 0; i < end && !found; i += 4) {
+        uint4 q = ld_nc_v4(al + i);
+        uint32_t x[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t idx = i + c;
+          if (!found && idx >= head && idx < end) {
+            ++acc_scan;
+            if (in_frontier(fb, x[c])) {
+              found = true;
+              par = x[c];
+            }
+          }
+        }
+      }
+    }
+    uint32_t big = __ballot_sync(0xFFFFFFFFu, todo && s.len > (uint32_t)kPullThreadMax);
+    while (big) {
+      int l = __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t* p = reinterpret_cast<const uint32_t*>(
+          __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(s.p), l));
+      uint32_t len = __shfl_sync(0xFFFFFFFFu, s.len, l);
+      const uint32_t* al = align16_down(p);
+      uint32_t head = (uint32_t)(p - al);
+      uint32_t end = head + len;
+      uint32_t got = kInf;
+      for (uint32_t i0 = 0; i0 < end; i0 += 128) {
+        uint32_t i = i0 + lane * 4;
+        uint32_t hit = kInf;
+        if (i < end) {
+          uint4 q = ld_nc_v4(al + i);
+          uint32_t x[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t idx = i + c;
+            if (hit == kInf && idx >= head && idx < end && in_frontier(fb, x[c])) hit = x[c];
+          }
+        }
+        uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit != kInf);
+        if (hm) {
+          int fl = __ffs(hm) - 1;
+          got = __shfl_sync(0xFFFFFFFFu, hit, fl);
+          if (lane == 0) acc_scan += min(end, i0 + 128) - max(head, i0);  // upper bound of ids read
+          break;
+        }
+        if (lane == 0) acc_scan += min(end, i0 + 128) - max(head, i0);
+      }
+      if (lane == (uint32_t)l && got != kInf) {
+        found = true;
+        par = got;
+      }
+    }
+    uint32_t fm = __ballot_sync(0xFFFFFFFFu, found);
+    if (lane == 0) {
+      a.vis[w] = vw | fm;
+      fbn[w] = fm;
+    }
+    uint32_t b = 0xFFFFFFFFu;
+    if (found) {
+      a.level[v] = L + 1;
+      if (kParents) a.parent[v] = par;
+      acc_deg += s.len;
+      b = (uint32_t)degree_bucket(s.len);
+    }
+    if (fm == 0) continue;
+    uint32_t same_b = __match_any_sync(0xFFFFFFFFu, b);
+    uint32_t bl = __ffs(same_b) - 1;
+    unsigned long long pos = 0;
+    if (found && lane == bl) pos = atomicAdd(&a.ctl->cnt[nxt][b], (unsigned long long)__popc(same_b));
+    pos = __shfl_sync(0xFFFFFFFFu, pos, bl);
+    if (found) {
+      uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + pos + __popc(same_b & lanemask_lt());
+      if (at < S.bstart[b + 1]) a.queue[at] = v;
+      else atomicCAS(&a.ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_acc(unsigned long long* dst, uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  if (lane_id() == 0 && v) atomicAdd(dst, (unsigned long long)v);
+}
+
+template <typename G, bool kParents>
+__global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
+  __shared__ BfsShared S;
+  const uint32_t tid = threadIdx.x;
+  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
+  const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint32_t n = a.g.num_vertices();
+  BfsCtl* ctl = a.ctl;
+
+  // ---- init: levels, parents, visited bits, counters
+  for (uint64_t v = gtid; v < n; v += gthreads) {
+    a.level[v] = kInf;
+    if (kParents) a.parent[v] = kInf;
+  }
+  for (uint64_t w = gtid; w < a.nw; w += gthreads) a.vis[w] = 0;
+  if (blockIdx.x == 0) {
+    for (int i = tid; i < 3 * kBuckets; i += blockDim.x) (&ctl->cnt[0][0])[i] = 0;
+    if (tid < 3) {
+      ctl->sdeg[tid] = 0;
+      ctl->scanned[tid] = 0;
+    }
+  }
+  if (tid <= (uint32_t)kBuckets) S.bstart[tid] = a.bstart[tid];
+  if (tid < (uint32_t)kBuckets) S.base[tid] = 0;
+  if (tid == 0) {
+    S.nvis = 0;
+    S.mvis = 0;
+    S.prev_dir = 1;
+    S.fb_valid = 0;
+  }
+  if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
+  if (blockIdx.x == 0 && tid == 0) {
+    uint32_t s = a.src;
+    uint32_t d = a.g.degree(s);
+    int b = degree_bucket(d);
+    a.level[s] = 0;
+    if (kParents) a.parent[s] = s;
+    a.vis[s >> 5] = 1u << (s & 31);
+    a.queue[S.bstart[b]] = s;
+    ctl->cnt[0][b] = 1;
+    ctl->sdeg[0] = d;
+  }
+  if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
+
+  const uint64_t m = a.g.num_edges();
+  const uint64_t t_begin = globaltimer();
+  for (uint32_t L = 0;; ++L) {
+    const int cur = L % 3, nxt = (L + 1) % 3, old = (L + 2) % 3;
+    // a BFS has at most n levels; the whole traversal is also time-bounded
+    if (L > n || ld_cg(&ctl->err) != 0 || globaltimer() - t_begin > a.limit_ns) {
+      if (tid == 0) atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_TIMEOUT);
+      return;
+    }
+    if (tid < (uint32_t)kBuckets) S.cnt[tid] = (uint32_t)ld_cg(&ctl->cnt[cur][tid]);
+    __syncthreads();
+    if (tid == 0) {
+      uint64_t now = globaltimer();
+      S.pre[0] = 0;
+      for (int b = 0; b < kBuckets; ++b) S.pre[b + 1] = S.pre[b] + S.cnt[b];
+      S.nf = (uint32_t)S.pre[kBuckets];
+      S.mf = ld_cg(&ctl->sdeg[cur]);
+      if (blockIdx.x == 0 && L > 0 && L - 1 < kTraceCap) {
+        byo_bfs_iter* r = a.trace + (L - 1);
+        r->t_ns = now - S.t_top;
+        r->edges_examined = ld_cg(&ctl->scanned[cur]);
+      }
+      S.t_top = now;
+    }
+    __syncthreads();
+    if (S.nf == 0) {
+      if (blockIdx.x == 0 && tid == 0) ctl->levels = L;
+      break;
+    }
+    if (blockIdx.x == 0 && tid < (uint32_t)kBuckets) ctl->cnt[old][tid] = 0;
+    if (blockIdx.x == 0 && tid == 0) {
+      ctl->sdeg[old] = 0;
+      ctl->scanned[old] = 0;
+    }
+    // ---- schedule: direction and bins for this iteration
+    if (tid < 32) {
+      SchedFeatures f;
+      f.nf = S.nf;
+      f.mf = S.mf;
+      f.nu = (uint64_t)n - S.nvis - S.nf;
+      f.mu = m - S.mvis - S.mf;
+      f.n = n;
+      f.m = m;
+      f.h[0] = (uint32_t)(S.pre[3]);
+      f.h[1] = (uint32_t)(S.pre[6] - S.pre[3]);
+      f.h[2] = (uint32_t)(S.pre[9] - S.pre[6]);
+      f.h[3] = (uint32_t)(S.pre[kBuckets] - S.pre[9]);
+      int action = sched_decide(a.sp, f, S.prev_dir);  // warp-collective
+      if (tid == 0) {
+        S.action = action;
+        S.dir = action == 0 ? 0 : 1;
+        sched_bins(a.sp, action, &S.bt, &S.bw);
+        if (blockIdx.x == 0 && L < kTraceCap) {
+          byo_bfs_iter* r = a.trace + L;
+          r->level = L;
+          r->direction = (uint32_t)S.dir;
+          r->action = (uint32_t)action;
+          r->frontier = S.nf;
+          r->frontier_edges = S.mf;
+          r->unvisited = (uint32_t)f.nu;
+          r->unvisited_edges = f.mu;
+          for (int k = 0; k < 4; ++k) r->hist[k] = f.h[k];
+          r->reserved = 0;
+          r->edges_examined = 0;
+          r->t_ns = 0;
+        }
+        // CTA-bin work items: vertices * chunks per vertex
+        S.preC[0] = 0;
+        for (int b = 0; b < kBuckets; ++b) {
+          uint64_t K = (b >= 12) ? (1ull << (b - 11)) : 1ull;
+          S.preC[b + 1] = S.preC[b] + (b > S.bw ? (uint64_t)S.cnt[b] * K : 0ull);
+        }
+      }
+    }
+    __syncthreads();
+    uint64_t acc_deg = 0, acc_scan = 0;
+    if (S.dir == 0) {
+      if (!S.fb_valid) {
+        // queue -> bit-vector for this level
+        uint32_t* fb = a.fb + (size_t)(L & 1) * a.nw;
+        for (uint64_t w = gtid; w < a.nw; w += gthreads) fb[w] = 0;
+        if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
+        for (uint64_t i = gtid; i < S.nf; i += gthreads) {
+          int b = find_bucket(S.pre, 0, kBuckets - 1, i);
+          uint32_t v = frontier_vertex(a, S, b, i - S.pre[b]);
+          atomicOr(fb + (v >> 5), 1u << (v & 31));
+        }
+        if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
+      }
+      pull_phase<G, kParents>(a, S, L, nxt, acc_deg, acc_scan);
+    } else {
+      push_phase<G, kParents>(a, S, L, nxt, acc_deg, acc_scan);
+    }
+    flush_acc(&ctl->sdeg[nxt], acc_deg);
+    flush_acc(&ctl->scanned[nxt], acc_scan);
+    __syncthreads();
+    if (tid < (uint32_t)kBuckets) S.base[tid] += S.cnt[tid];
+    if (tid == 0) {
+      S.nvis += S.nf;
+      S.mvis += S.mf;
+      S.prev_dir = S.dir;
+      S.fb_valid = S.dir == 0;
+    }
+    if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
+  }
+}
+
+template <typename G, bool kParents>
+byo_status launch_bfs(BfsArgs<G>& args, cudaStream_t s) {
+  auto fn = bfs_kernel<G, kParents>;
+  int per_sm = 0;
+  BYO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBfsThreads, 0));
+  if (per_sm < 1) {
+    set_error("bfs_kernel cannot be resident");
+    return BYO_ERR_CUDA;
+  }
+  int grid = per_sm * sm_count();
+  void* kargs[] = {&args};
+  ProfScope ps("bfs_persistent", s);
+  BYO_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kBfsThreads), kargs, 0, s));
+  note_launch();
+  return BYO_OK;
+}
+
+template <typename OffT>
+byo_status run_bfs(const byo_graph* g, const uint32_t* sources, uint32_t ns, uint32_t* levels, uint32_t* parents,
+                   const SchedParams& sp, cudaStream_t s) {
+  BfsWork* w = g->bfs;
+  BfsArgs<CsrView<OffT>> args;
+  args.g = CsrView<OffT>{g->n, g->m, static_cast<const OffT*>(g->off), g->col};
+  args.vis = w->vis;
+  args.fb = w->fb;
+  args.queue = w->queue;
+  args.bstart = g->d_bstart;
+  args.ctl = w->ctl;
+  args.trace = w->trace;
+  args.sp = sp;
+  args.limit_ns = timeout_ns();
+  args.nw = w->nw;
+  for (uint32_t i = 0; i < ns; ++i) {
+    args.src = sources[i];
+    args.level = levels + (size_t)i * g->n;
+    args.parent = parents ? parents + (size_t)i * g->n : nullptr;
+    if (parents) BYO_RETURN_IF((launch_bfs<CsrView<OffT>, true>(args, s)));
+    else BYO_RETURN_IF((launch_bfs<CsrView<OffT>, false>(args, s)));
+  }
+  return BYO_OK;
+}
+
+byo_status ensure_bfs_work(byo_graph* g) {
+  if (g->bfs) return BYO_OK;
+  BfsWork* w = new (std::nothrow) BfsWork();
+  if (!w) {
+    set_error("host allocation failed");
+    return BYO_ERR_OUT_OF_MEMORY;
+  }
+  w->n = g->n;
+  w->nw = (g->n + 31) / 32;
+  byo_status st = dev_alloc_t(&w->vis, w->nw, "BFS visited bits");
+  if (st == BYO_OK) st = dev_alloc_t(&w->fb, 2ull * w->nw, "BFS frontier bits");
+  if (st == BYO_OK) st = dev_alloc_t(&w->queue, g->n, "BFS queue");
+  if (st == BYO_OK) st = dev_alloc_t(&w->ctl, 1, "BFS control");
+  if (st == BYO_OK) st = dev_alloc_t(&w->trace, kTraceCap, "BFS trace");
+  if (st == BYO_OK) {
+    cudaError_t e = cudaMemset(w->ctl, 0, sizeof(BfsCtl));
+    if (e != cudaSuccess) st = cuda_status(e, "cudaMemset");
+  }
+  if (st != BYO_OK) {
+    bfs_free(w);
+    return st;
+  }
+  g->bfs = w;
+  return BYO_OK;
+}
+
+}  // namespace
+}  // namespace byo
+
+using namespace byo;
+
+extern "C" byo_status byo_bfs(const byo_graph* gc, const uint32_t* host_sources, uint32_t num_sources,
+                              uint32_t* levels, uint32_t* parents, const byo_sched* sched, void* stream) {
+  clear_error();
+  BYO_RETURN_IF(check_graph(gc));
+  byo_graph* g = const_cast<byo_graph*>(gc);
+  if (num_sources == 0) return BYO_OK;
+  if (!host_sources || !levels) {
+    set_error("byo_bfs: NULL sources or levels");
+    return BYO_ERR_INVALID_ARG;
+  }
+  for (uint32_t i = 0; i < num_sources; ++i) {
+    if (host_sources[i] >= g->n) {
+      set_error("byo_bfs: source %u is >= n (%u)", host_sources[i], g->n);
+      return BYO_ERR_INVALID_ARG;
+    }
+  }
+  SchedParams sp;
+  BYO_RETURN_IF(sched_params(sched, &sp));
+  BYO_RETURN_IF(ensure_bfs_work(g));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  byo_status st = g->off64 ? run_bfs<uint64_t>(g, host_sources, num_sources, levels, parents, sp, s)
+                           : run_bfs<uint32_t>(g, host_sources, num_sources, levels, parents, sp, s);
+  BYO_RETURN_IF(st);
+  uint32_t err = 0;
+  BYO_CUDA(cudaMemcpyAsync(&err, &g->bfs->ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  BYO_CUDA(cudaStreamSynchronize(s));
+  if (err) {
+    cudaMemsetAsync(&g->bfs->ctl->err, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(&g->bfs->ctl->bar, 0, sizeof(GridBar), s);
+    cudaStreamSynchronize(s);
+    set_error("byo_bfs: a device-side wait exceeded BYO_TIMEOUT_MS");
+    return BYO_ERR_TIMEOUT;
+  }
+  return BYO_OK;
+}
+
+extern "C" byo_status byo_bfs_trace(const byo_graph* g, byo_bfs_iter* host_records, uint32_t cap,
+                                    uint32_t* host_count, void* stream) {
+  clear_error();
+  BYO_RETURN_IF(check_graph(g));
+  if (!host_count || (cap && !host_records)) {
+    set_error("byo_bfs_trace: NULL output");
+    return BYO_ERR_INVALID_ARG;
+  }
+  *host_count = 0;
+  if (!g->bfs) return BYO_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t levels = 0;
+  BYO_CUDA(cudaMemcpyAsync(&levels, &g->bfs->ctl->levels, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  BYO_CUDA(cudaStreamSynchronize(s));
+  *host_count = levels;
+  uint32_t c = levels < cap ? levels : cap;
+  if (c > kTraceCap) c = kTraceCap;
+  if (c) {
+    BYO_CUDA(cudaMemcpyAsync(host_records, g->bfs->trace, sizeof(byo_bfs_iter) * c, cudaMemcpyDeviceToHost, s));
+    BYO_CUDA(cudaStreamSynchronize(s));
+  }
+  return BYO_OK;
+}

@@ -1,0 +1,178 @@
+// byo_internal.cuh -- shared declarations of libbyo.so (host structs, error
+// plumbing, device helpers).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/byo.h"
+
+namespace byo {
+
+// ---------------------------------------------------------------- constants
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+// Degree buckets: bucket(0) = 0, bucket(d) = 1 + floor(log2 d) for d >= 1, so
+// bucket b >= 1 holds degrees [2^(b-1), 2^b).  33 buckets cover uint32 degrees.
+constexpr int kBuckets = 33;
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+byo_status cuda_status(cudaError_t e, const char* what);
+
+#define BYO_CUDA(call)                                                     \
+  do {                                                                     \
+    cudaError_t _e = (call);                                               \
+    if (_e != cudaSuccess) return ::byo::cuda_status(_e, #call);           \
+  } while (0)
+
+#define BYO_CHECK_LAUNCH(what)                                             \
+  do {                                                                     \
+    cudaError_t _e = cudaGetLastError();                                   \
+    if (_e != cudaSuccess) return ::byo::cuda_status(_e, what);            \
+  } while (0)
+
+#define BYO_RETURN_IF(st)                                                  \
+  do {                                                                     \
+    byo_status _s = (st);                                                  \
+    if (_s != BYO_OK) return _s;                                           \
+  } while (0)
+
+// Device allocation that reports OUT_OF_MEMORY through the error string.
+byo_status dev_alloc(void** p, size_t bytes, const char* what);
+template <typename T>
+inline byo_status dev_alloc_t(T** p, size_t count, const char* what) {
+  return dev_alloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16, what);
+}
+void dev_free(void* p);
+// Stream-ordered temporaries (cudaMallocAsync / cudaFreeAsync on stream s).
+byo_status tmp_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
+template <typename T>
+inline byo_status tmp_alloc_t(T** p, size_t count, cudaStream_t s, const char* what) {
+  return tmp_alloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16, s, what);
+}
+void tmp_free(void* p, cudaStream_t s);
+
+int sm_count();
+uint64_t timeout_ns();
+
+// ---------------------------------------------------------------- scan / sort
+// Exclusive scan of n uint32 flags/counts into uint64 (out may alias nothing).
+// *host_total (nullable) receives the total and synchronises the stream.
+byo_status scan_u32_to_u64(const uint32_t* in, uint64_t* out, uint64_t n, uint64_t* host_total, cudaStream_t s);
+byo_status scan_u64_inplace(uint64_t* data, uint64_t n, cudaStream_t s);
+// LSD radix sort of n uint64 keys on bits [0, bits).  Uses keys and tmp
+// (both n entries); *sorted points at whichever holds the result.
+byo_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint64_t n, int bits, uint64_t** sorted, cudaStream_t s);
+
+// ---------------------------------------------------------------- workspaces
+struct BfsWork;
+struct PrWork;
+struct TcWork;
+
+}  // namespace byo
+
+// The graph handle.  Static CSR: off (uint32 or uint64, n+1), col (m + 4
+// padding entries, 16-byte aligned).  vorder lists the vertices grouped by
+// degree bucket, ascending inside each bucket; bstart[b] is where bucket b
+// starts in vorder (host copy and device copy).
+struct byo_graph {
+  uint32_t n = 0;
+  uint64_t m = 0;
+  uint32_t flags = 0;
+  bool off64 = false;
+  int device = 0;
+  void* off = nullptr;
+  uint32_t* col = nullptr;
+  uint32_t* vorder = nullptr;
+  uint64_t bstart[byo::kBuckets + 1] = {0};
+  uint64_t* d_bstart = nullptr;
+  byo::BfsWork* bfs = nullptr;
+  byo::PrWork* pr = nullptr;
+  byo::TcWork* tc = nullptr;
+};
+
+namespace byo {
+void bfs_free(BfsWork* w);
+void pr_free(PrWork* w);
+void tc_free(TcWork* w);
+byo_status check_graph(const byo_graph* g);
+}  // namespace byo
+
+// ================================================================ device side
+namespace byo {
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// L2-only loads for data that other SMs write during the same kernel.
+__device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ uint64_t ld_cg(const unsigned long long* p) { return __ldcg(p); }
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int degree_bucket(uint32_t d) { return d == 0 ? 0 : 32 - __clz(d); }
+
+// Grid-wide barrier for a cooperative launch.  Sense by generation counter.
+// Every wait is bounded by `limit_ns`; on timeout the error word is set and
+// false is returned (the caller then leaves its loop and exits).
+struct GridBar {
+  uint32_t count;
+  uint32_t gen;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, uint32_t nblocks, uint32_t* err, uint64_t limit_ns) {
+  __shared__ uint32_t ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t ok = 1;
+    uint32_t g = ld_acquire(&bar->gen);
+    __threadfence();
+    uint32_t arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == nblocks - 1) {
+      bar->count = 0;
+      __threadfence();
+      st_release(&bar->gen, g + 1);
+    } else {
+      uint64_t t0 = globaltimer();
+      uint32_t spins = 0;
+      while (ld_acquire(&bar->gen) == g) {
+        if (++spins > 64) {
+          spins = 0;
+          if (ld_cg(err) != 0 || globaltimer() - t0 > limit_ns) {
+            atomicCAS(err, 0u, (uint32_t)BYO_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+}  // namespace byo

@@ -1,0 +1,510 @@
+// graph.cu -- error plumbing, allocation helpers, and the static CSR
+// container: build (Section 3.1 neighbour sets stored contiguously, Section
+// 4.2), num_vertices / num_edges / degree (Section 4.2, kept as metadata as in
+// Section 4.3), export, destroy.
+#include <stdarg.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "byo_internal.cuh"
+#include "prof.cuh"
+#include "container.cuh"
+
+namespace byo {
+
+// ---------------------------------------------------------------- errors
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+byo_status cuda_status(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return BYO_ERR_OUT_OF_MEMORY;
+  return BYO_ERR_CUDA;
+}
+
+byo_status dev_alloc(void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMalloc(%zu bytes) for %s: %s", bytes, what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BYO_ERR_OUT_OF_MEMORY : BYO_ERR_CUDA;
+  }
+  return BYO_OK;
+}
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+byo_status tmp_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
+  *p = nullptr;
+  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMallocAsync(%zu bytes) for %s: %s", bytes, what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BYO_ERR_OUT_OF_MEMORY : BYO_ERR_CUDA;
+  }
+  return BYO_OK;
+}
+void tmp_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+int sm_count() {
+  int dev = 0, c = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+  return c > 0 ? c : 1;
+}
+
+uint64_t timeout_ns() {
+  const char* e = getenv("BYO_TIMEOUT_MS");
+  uint64_t ms = 10000;
+  if (e && *e) {
+    long long v = atoll(e);
+    if (v > 0) ms = (uint64_t)v;
+  }
+  return ms * 1000000ull;
+}
+
+byo_status check_graph(const byo_graph* g) {
+  if (!g) {
+    set_error("graph handle is NULL");
+    return BYO_ERR_INVALID_ARG;
+  }
+  return BYO_OK;
+}
+
+// ---------------------------------------------------------------- kernels
+namespace {
+
+__global__ void make_keys_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t k,
+                                 uint32_t n, int lb, bool sym, uint64_t* __restrict__ keys, uint32_t* bad) {
+  const uint64_t sentinel = (lb == 32) ? ~0ull : ((1ull << (2 * lb)) - 1);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t u = src[i], v = dst[i];
+    uint64_t a = sentinel, b = sentinel;
+    if (u >= n || v >= n) {
+      atomicOr(bad, 1u);
+    } else if (u != v) {
+      a = ((uint64_t)u << lb) | v;
+      b = ((uint64_t)v << lb) | u;
+    }
+    if (sym) {
+      keys[2 * i] = a;
+      keys[2 * i + 1] = b;
+    } else {
+      keys[i] = a;
+    }
+  }
+}
+
+// flag[i] = 1 iff keys[i] is the first copy of a valid key.
+__global__ void unique_flags_kernel(const uint64_t* __restrict__ keys, uint64_t cnt, int lb, uint32_t* flags) {
+  const uint64_t sentinel = (lb == 32) ? ~0ull : ((1ull << (2 * lb)) - 1);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t x = keys[i];
+    flags[i] = (x != sentinel && (i == 0 || keys[i - 1] != x)) ? 1u : 0u;
+  }
+}
+
+__global__ void compact_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ pos,
+                               const uint32_t* __restrict__ flags, uint64_t cnt, int lb, uint32_t* __restrict__ col,
+                               uint32_t* __restrict__ rows) {
+  const uint64_t lowmask = (lb == 32) ? 0xFFFFFFFFull : ((1ull << lb) - 1);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (flags[i]) {
+      uint64_t p = pos[i];
+      col[p] = (uint32_t)(keys[i] & lowmask);
+      rows[p] = (uint32_t)(keys[i] >> lb);
+    }
+  }
+}
+
+// off[s] for every s from the sorted row ids: the first entry of row s.
+template <typename OffT>
+__global__ void offsets_kernel(const uint32_t* __restrict__ rows, uint64_t m, uint32_t n, OffT* __restrict__ off) {
+  uint64_t total = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= m; p += total) {
+    uint32_t hi = p < m ? rows[p] : n;  // rows [prev+1, hi] start at p
+    uint32_t lo = p == 0 ? 0 : rows[p - 1] + 1;
+    if (p == 0) lo = 0;
+    for (uint64_t s = lo; s <= hi && s <= n; ++s) off[s] = (OffT)p;
+  }
+}
+
+// keys for grouping vertices by degree bucket, ascending id inside a bucket
+template <typename OffT>
+__global__ void bucket_keys_kernel(const OffT* __restrict__ off, uint32_t n, int lb, uint64_t* keys,
+                                   unsigned long long* hist) {
+  __shared__ unsigned long long h[kBuckets];
+  for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t d = (uint32_t)(off[v + 1] - off[v]);
+    int b = degree_bucket(d);
+    keys[v] = ((uint64_t)b << lb) | v;
+    atomicAdd(&h[b], 1ull);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBuckets; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+__global__ void low32_kernel(const uint64_t* __restrict__ keys, uint64_t n, int lb, uint32_t* out) {
+  const uint64_t lowmask = (lb == 32) ? 0xFFFFFFFFull : ((1ull << lb) - 1);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)(keys[i] & lowmask);
+}
+
+// symmetry check: (u,v) present => (v,u) present
+template <typename OffT>
+__global__ void symmetric_kernel(const OffT* __restrict__ off, const uint32_t* __restrict__ col,
+                                 const uint32_t* __restrict__ rows, uint64_t m, uint32_t* bad) {
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t u = rows[p], v = col[p];
+    uint64_t lo = off[v], hi = off[v + 1];
+    while (lo < hi) {
+      uint64_t mid = (lo + hi) >> 1;
+      if (col[mid] < u) lo = mid + 1;
+      else hi = mid;
+    }
+    if (!(lo < off[v + 1] && col[lo] == u)) atomicOr(bad, 1u);
+  }
+}
+
+template <typename OffT>
+__global__ void degree_kernel(CsrView<OffT> g, const uint32_t* __restrict__ vs, uint64_t k, uint32_t* out,
+                              uint32_t* bad) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v = vs ? vs[i] : (uint32_t)i;
+    if (v >= g.n) {
+      atomicOr(bad, 1u);
+      out[i] = 0;
+    } else {
+      out[i] = g.degree(v);
+    }
+  }
+}
+
+template <typename OffT>
+__global__ void export_off_kernel(const OffT* __restrict__ off, uint32_t n, uint64_t* out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (uint64_t)off[i];
+}
+
+unsigned grid_for(uint64_t work, int threads) {
+  uint64_t b = (work + threads - 1) / threads;
+  uint64_t cap = (uint64_t)sm_count() * 16;
+  if (b > cap) b = cap;
+  if (b == 0) b = 1;
+  return (unsigned)b;
+}
+
+int bits_for(uint32_t n) {
+  int lb = 1;
+  while (lb < 32 && (1ull << lb) < (uint64_t)n) ++lb;
+  return lb;
+}
+
+template <typename OffT>
+byo_status finish_csr(byo_graph* g, const uint32_t* rows, cudaStream_t s) {
+  OffT* off = static_cast<OffT*>(g->off);
+  offsets_kernel<OffT><<<grid_for(g->m + 1, 256), 256, 0, s>>>(rows, g->m, g->n, off); ::byo::note_launch();
+  BYO_CHECK_LAUNCH("offsets_kernel");
+  return BYO_OK;
+}
+
+template <typename OffT>
+byo_status build_buckets(byo_graph* g, cudaStream_t s) {
+  uint32_t n = g->n;
+  int lb = bits_for(n > 1 ? n : 2);
+  uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr;
+  unsigned long long* hist = nullptr;
+  BYO_RETURN_IF(tmp_alloc_t(&keys, n, s, "bucket keys"));
+  byo_status st = tmp_alloc_t(&tmp, n, s, "bucket keys tmp");
+  if (st == BYO_OK) st = tmp_alloc_t(&hist, kBuckets, s, "bucket histogram");
+  if (st == BYO_OK) st = dev_alloc_t(&g->vorder, n, "vertex order");
+  if (st == BYO_OK) st = dev_alloc_t(&g->d_bstart, kBuckets + 1, "bucket starts");
+  if (st == BYO_OK) {
+    cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kBuckets, s);
+    bucket_keys_kernel<OffT><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const OffT*>(g->off), n, lb, keys, hist); ::byo::note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_status(e, "bucket_keys_kernel");
+  }
+  if (st == BYO_OK) st = radix_sort_u64(keys, tmp, n, lb + 6, &sorted, s);
+  if (st == BYO_OK) {
+    low32_kernel<<<grid_for(n, 256), 256, 0, s>>>(sorted, n, lb, g->vorder); ::byo::note_launch();
+    cudaError_t e = cudaGetLastError();
+    unsigned long long h[kBuckets];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "degree buckets");
+    else {
+      g->bstart[0] = 0;
+      for (int b = 0; b < kBuckets; ++b) g->bstart[b + 1] = g->bstart[b] + h[b];
+      e = cudaMemcpyAsync(g->d_bstart, g->bstart, sizeof(uint64_t) * (kBuckets + 1), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = cuda_status(e, "bucket starts");
+    }
+  }
+  tmp_free(keys, s);
+  tmp_free(tmp, s);
+  tmp_free(hist, s);
+  return st;
+}
+
+void graph_free(byo_graph* g) {
+  if (!g) return;
+  dev_free(g->off);
+  dev_free(g->col);
+  dev_free(g->vorder);
+  dev_free(g->d_bstart);
+  bfs_free(g->bfs);
+  pr_free(g->pr);
+  tc_free(g->tc);
+  delete g;
+}
+
+byo_status build_csr(byo_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t k, bool sym, cudaStream_t s) {
+  const uint32_t n = g->n;
+  const int lb = bits_for(n > 1 ? n : 2);
+  const uint64_t cnt = sym ? 2 * k : k;
+  uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr, *pos = nullptr;
+  uint32_t *flags = nullptr, *rows = nullptr, *bad = nullptr;
+  byo_status st = tmp_alloc_t(&bad, 4, s, "flag");
+  if (st == BYO_OK) st = tmp_alloc_t(&keys, cnt, s, "edge keys");
+  if (st == BYO_OK) st = tmp_alloc_t(&tmp, cnt, s, "edge keys tmp");
+  if (st == BYO_OK) {
+    cudaMemsetAsync(bad, 0, 16, s);
+    if (k) make_keys_kernel<<<grid_for(k, 256), 256, 0, s>>>(src, dst, k, n, lb, sym, keys, bad); ::byo::note_launch();
+    cudaError_t e = cudaGetLastError();
+    uint32_t hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "make_keys_kernel");
+    else if (hbad) {
+      set_error("byo_graph_build: a vertex id is >= n (%u)", n);
+      st = BYO_ERR_INVALID_ARG;
+    }
+  }
+  if (st == BYO_OK) st = radix_sort_u64(keys, tmp, cnt, 2 * lb, &sorted, s);
+  // reuse the other key buffer for the positions
+  if (st == BYO_OK) {
+    pos = sorted == keys ? tmp : keys;
+    st = tmp_alloc_t(&flags, cnt, s, "unique flags");
+  }
+  uint64_t m = 0;
+  if (st == BYO_OK) {
+    if (cnt) unique_flags_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(sorted, cnt, lb, flags); ::byo::note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_status(e, "unique_flags_kernel");
+  }
+  if (st == BYO_OK) st = scan_u32_to_u64(flags, pos, cnt, &m, s);
+  if (st == BYO_OK) {
+    g->m = m;
+    g->off64 = (g->flags & BYO_OFFSETS64) || m >= (1ull << 32);
+    st = dev_alloc(&g->off, (size_t)(n + 1) * (g->off64 ? 8 : 4) + 16, "CSR offsets");
+  }
+  if (st == BYO_OK) st = dev_alloc_t(&g->col, m + 4, "CSR neighbours");
+  if (st == BYO_OK) st = tmp_alloc_t(&rows, m + 1, s, "CSR rows");
+  if (st == BYO_OK) {
+    cudaMemsetAsync(g->col + m, 0, 16, s);
+    if (cnt) compact_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(sorted, pos, flags, cnt, lb, g->col, rows); ::byo::note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_status(e, "compact_kernel");
+  }
+  if (st == BYO_OK) st = g->off64 ? finish_csr<uint64_t>(g, rows, s) : finish_csr<uint32_t>(g, rows, s);
+  if (st == BYO_OK && !sym && m) {
+    cudaMemsetAsync(bad, 0, 4, s);
+    if (g->off64)
+      symmetric_kernel<uint64_t><<<grid_for(m, 256), 256, 0, s>>>(static_cast<uint64_t*>(g->off), g->col, rows, m, bad);
+    else
+      symmetric_kernel<uint32_t><<<grid_for(m, 256), 256, 0, s>>>(static_cast<uint32_t*>(g->off), g->col, rows, m, bad); ::byo::note_launch();
+    cudaError_t e = cudaGetLastError();
+    uint32_t hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "symmetric_kernel");
+    else if (hbad) {
+      set_error("byo_graph_build: input is not symmetric and BYO_SYMMETRIZE was not given");
+      st = BYO_ERR_NOT_SYMMETRIC;
+    }
+  }
+  tmp_free(keys, s);
+  tmp_free(tmp, s);
+  tmp_free(flags, s);
+  tmp_free(rows, s);
+  tmp_free(bad, s);
+  if (st == BYO_OK) st = g->off64 ? build_buckets<uint64_t>(g, s) : build_buckets<uint32_t>(g, s);
+  if (st == BYO_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "byo_graph_build");
+  }
+  return st;
+}
+
+}  // namespace
+}  // namespace byo
+
+using namespace byo;
+
+extern "C" {
+
+const char* byo_last_error(void) { return g_err; }
+
+byo_sched byo_sched_default(void) {
+  byo_sched s;
+  s.mode = BYO_SCHED_HEURISTIC;
+  s.thr_thread = 16;
+  s.thr_warp = 1024;
+  s.alpha = 15.0f;
+  s.beta = 18.0f;
+  s.mlp = nullptr;
+  return s;
+}
+
+byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t k, uint32_t flags,
+                           void* stream, byo_graph** out) {
+  clear_error();
+  if (!out) {
+    set_error("byo_graph_build: out is NULL");
+    return BYO_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (k > 0 && (!src || !dst)) {
+    set_error("byo_graph_build: NULL edge arrays with k = %llu", (unsigned long long)k);
+    return BYO_ERR_INVALID_ARG;
+  }
+  if (!(flags & (BYO_CSR | BYO_DYNAMIC)) || (flags & BYO_CSR && flags & BYO_DYNAMIC)) {
+    set_error("byo_graph_build: exactly one of BYO_CSR / BYO_DYNAMIC is required");
+    return BYO_ERR_INVALID_ARG;
+  }
+  if (flags & BYO_DYNAMIC) {
+    set_error("byo_graph_build: the dynamic container is not available in this build");
+    return BYO_ERR_UNSUPPORTED;
+  }
+  if (n == 0xFFFFFFFFu) {
+    set_error("byo_graph_build: n must be < 2^32 - 1 (0xFFFFFFFF is the INF marker)");
+    return BYO_ERR_INVALID_ARG;
+  }
+  if (k > (1ull << 36)) {
+    set_error("byo_graph_build: k too large");
+    return BYO_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  byo_graph* g = new (std::nothrow) byo_graph();
+  if (!g) {
+    set_error("byo_graph_build: host allocation failed");
+    return BYO_ERR_OUT_OF_MEMORY;
+  }
+  g->n = n;
+  g->flags = flags;
+  cudaGetDevice(&g->device);
+  byo_status st;
+  {
+    ProfScope ps("csr_build", s);
+    st = build_csr(g, src, dst, k, (flags & BYO_SYMMETRIZE) != 0, s);
+  }
+  if (st != BYO_OK) {
+    cudaStreamSynchronize(s);
+    graph_free(g);
+    return st;
+  }
+  *out = g;
+  return BYO_OK;
+}
+
+byo_status byo_graph_destroy(byo_graph* g) {
+  clear_error();
+  if (!g) return BYO_OK;
+  cudaDeviceSynchronize();
+  graph_free(g);
+  return BYO_OK;
+}
+
+byo_status byo_num_vertices(const byo_graph* g, uint32_t* host_n) {
+  clear_error();
+  BYO_RETURN_IF(check_graph(g));
+  if (!host_n) {
+    set_error("byo_num_vertices: NULL output");
+    return BYO_ERR_INVALID_ARG;
+  }
+  *host_n = g->n;
+  return BYO_OK;
+}
+
+byo_status byo_num_edges(const byo_graph* g, uint64_t* host_m) {
+  clear_error();
+  BYO_RETURN_IF(check_graph(g));
+  if (!host_m) {
+    set_error("byo_num_edges: NULL output");
+    return BYO_ERR_INVALID_ARG;
+  }
+  *host_m = g->m;
+  return BYO_OK;
+}
+
+byo_status byo_degree(const byo_graph* g, const uint32_t* vs, uint64_t k, uint32_t* out, void* stream) {
+  clear_error();
+  BYO_RETURN_IF(check_graph(g));
+  if (!vs) k = g->n;
+  if (k && !out) {
+    set_error("byo_degree: NULL output");
+    return BYO_ERR_INVALID_ARG;
+  }
+  if (k == 0) return BYO_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t* bad = nullptr;
+  BYO_RETURN_IF(tmp_alloc_t(&bad, 1, s, "flag"));
+  cudaMemsetAsync(bad, 0, 4, s);
+  if (g->off64)
+    degree_kernel<uint64_t><<<grid_for(k, 256), 256, 0, s>>>(
+        CsrView<uint64_t>{g->n, g->m, static_cast<const uint64_t*>(g->off), g->col}, vs, k, out, bad);
+  else
+    degree_kernel<uint32_t><<<grid_for(k, 256), 256, 0, s>>>(
+        CsrView<uint32_t>{g->n, g->m, static_cast<const uint32_t*>(g->off), g->col}, vs, k, out, bad); ::byo::note_launch();
+  cudaError_t e = cudaGetLastError();
+  uint32_t hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
+  tmp_free(bad, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, "byo_degree");
+  if (hbad) {
+    set_error("byo_degree: a vertex id is >= n");
+    return BYO_ERR_INVALID_ARG;
+  }
+  return BYO_OK;
+}
+
+byo_status byo_graph_export_csr(const byo_graph* g, uint64_t* offsets, uint32_t* col, void* stream) {
+  clear_error();
+  BYO_RETURN_IF(check_graph(g));
+  if (!offsets || (g->m && !col)) {
+    set_error("byo_graph_export_csr: NULL output");
+    return BYO_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (g->off64)
+    export_off_kernel<uint64_t><<<grid_for(g->n + 1ull, 256), 256, 0, s>>>(static_cast<const uint64_t*>(g->off), g->n,
+                                                                           offsets);
+  else
+    export_off_kernel<uint32_t><<<grid_for(g->n + 1ull, 256), 256, 0, s>>>(static_cast<const uint32_t*>(g->off), g->n,
+                                                                           offsets); ::byo::note_launch();
+  BYO_CHECK_LAUNCH("export_off_kernel");
+  if (g->m) BYO_CUDA(cudaMemcpyAsync(col, g->col, sizeof(uint32_t) * g->m, cudaMemcpyDeviceToDevice, s));
+  return BYO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// sched.cuh -- per-iteration edgeMap schedule: direction (sparse/push vs
+// dense/pull, Section 3.2; the cutoff uses degree and num_edges, Section 6.3)
+// and the push iteration's degree bins.  Three deciders share one action set:
+//   HEURISTIC  Beamer-style switch: push -> pull when the frontier's edges
+//              exceed the unvisited edges / alpha; pull -> push when the
+//              frontier has fewer than n / beta vertices.
+//   LEARNED    a 12 -> 32 -> 32 -> 4 ReLU network over frontier features,
+//              evaluated by one warp of every CTA inside the persistent loop.
+//   PUSH/PULL  fixed.
+// Schedules never change results, only which kernel path runs.
+#pragma once
+
+#include "byo_internal.cuh"
+
+namespace byo {
+
+constexpr int kFeatures = 12;
+constexpr int kHidden = 32;
+constexpr int kActions = 4;  // 0 pull; 1 push (thr_thread, thr_warp); 2 push (4, 128); 3 push (64, 4096)
+constexpr int kMlpParams = kHidden * kFeatures + kHidden + kHidden * kHidden + kHidden + kActions * kHidden + kActions;
+
+struct SchedParams {
+  int mode;
+  int bt, bw;  // log2 of thr_thread / thr_warp
+  float alpha, beta;
+  const float* w;  // device MLP parameters (LEARNED)
+};
+
+struct SchedFeatures {
+  uint32_t nf;
+  uint64_t mf;
+  uint64_t nu;
+  uint64_t mu;
+  uint64_t n;
+  uint64_t m;
+  uint32_t h[4];
+};
+
+// Host: validate a byo_sched and turn it into kernel parameters.
+byo_status sched_params(const byo_sched* s, SchedParams* out);
+// Host: device pointer of a network's FP32 parameters (packed as in the oracle).
+const float* mlp_device_params(const byo_mlp* m);
+
+// The 12 network inputs, all in [0, ~1]: log-scaled sizes, ratios and the
+// degree histogram of the frontier.  Host code that builds training samples
+// from byo_bfs_iter records computes the same numbers.
+__host__ __device__ inline void sched_feature_vector(const SchedFeatures& f, float* x) {
+  x[0] = log2f(1.0f + (float)f.nf) / 32.0f;
+  x[1] = log2f(1.0f + (float)f.mf) / 40.0f;
+  x[2] = log2f(1.0f + (float)f.nu) / 32.0f;
+  x[3] = log2f(1.0f + (float)f.mu) / 40.0f;
+  x[4] = log2f(1.0f + (float)f.n) / 32.0f;
+  x[5] = log2f(1.0f + (float)f.m) / 40.0f;
+  x[6] = (float)f.nf / (float)(f.n ? f.n : 1);
+  x[7] = (float)((double)f.mf / (double)(f.mf + f.mu + 1));
+  float inv = 1.0f / (float)(f.nf ? f.nf : 1);
+  for (int k = 0; k < 4; ++k) x[8 + k] = (float)f.h[k] * inv;
+}
+
+__device__ __forceinline__ void sched_bins(const SchedParams& sp, int action, int* bt, int* bw) {
+  switch (action) {
+    case 2: *bt = 2; *bw = 7; break;
+    case 3: *bt = 6; *bw = 12; break;
+    default: *bt = sp.bt; *bw = sp.bw; break;
+  }
+}
+
+// Warp-collective (all 32 lanes of one warp); returns the action on every lane.
+__device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFeatures& f, int prev_dir) {
+  if (sp.mode == BYO_SCHED_PUSH) return 1;
+  if (sp.mode == BYO_SCHED_PULL) return 0;
+  if (sp.mode == BYO_SCHED_HEURISTIC || sp.w == nullptr) {
+    if (prev_dir == 1) return (double)f.mf > (double)f.mu / (double)sp.alpha ? 0 : 1;
+    return (double)f.nf < (double)f.n / (double)sp.beta ? 1 : 0;
+  }
+  // LEARNED: lane j owns hidden unit j of both layers
+  const uint32_t lane = lane_id();
+  float x[kFeatures];
+  sched_feature_vector(f, x);
+  const float* W1 = sp.w;
+  const float* b1 = W1 + kHidden * kFeatures;
+  const float* W2 = b1 + kHidden;
+  const float* b2 = W2 + kHidden * kHidden;
+  const float* W3 = b2 + kHidden;
+  const float* b3 = W3 + kActions * kHidden;
+  float h1 = __ldg(b1 + lane);
+#pragma unroll
+  for (int i = 0; i < kFeatures; ++i) h1 = fmaf(__ldg(W1 + lane * kFeatures + i), x[i], h1);
+  h1 = fmaxf(h1, 0.0f);
+  float h2 = __ldg(b2 + lane);
+#pragma unroll
+  for (int k = 0; k < kHidden; ++k) h2 = fmaf(__ldg(W2 + lane * kHidden + k), __shfl_sync(0xFFFFFFFFu, h1, k), h2);
+  h2 = fmaxf(h2, 0.0f);
+  int best = 0;
+  float bestz = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kActions; ++c) {
+    float t = __ldg(W3 + c * kHidden + lane) * h2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    float z = t + __ldg(b3 + c);
+    if (c == 0 || z > bestz) {
+      bestz = z;
+      best = c;
+    }
+  }
+  return best;
+}
+
+}  // namespace byo
