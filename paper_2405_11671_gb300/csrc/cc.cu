@@ -95,9 +95,20 @@ __global__ void __launch_bounds__(kCcThreads) cc_hook_kernel(G g, VBins bins, ui
   }
 }
 
+// Final labels.  Each thread writes only its own entry: a path-halving write
+// here could land after the owner stored the root and replace it with an
+// older ancestor, so the walk only reads.  Entries already finished by their
+// owners shorten the walks of the others.
 __global__ void cc_compress_kernel(uint32_t* p, uint32_t n) {
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
-    p[v] = cc_find(p, (uint32_t)v);
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x = (uint32_t)v;
+    uint32_t px = ld_cg(p + x);
+    while (px != x) {
+      x = px;
+      px = ld_cg(p + x);
+    }
+    p[v] = x;
+  }
 }
 
 template <typename OffT>
