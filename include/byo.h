@@ -214,6 +214,39 @@ byo_status byo_pagerank(const byo_graph* g, float damping, uint32_t iters, float
 byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* BFS that allocates nothing (the paper has no counterpart; this is a       */
+/* deployment variant of byo_bfs).  Some callers cannot allocate device      */
+/* memory: code whose device memory belongs to another allocator (a          */
+/* framework's caching allocator or a fixed arena handed out by the host     */
+/* application), code under a hard memory budget that must not grow, and    */
+/* latency-critical loops where cudaMalloc / cudaFree would synchronise the  */
+/* device.  They cannot create a byo_graph either, since building one        */
+/* allocates, so this call takes the CSR itself.                            */
+/*                                                                          */
+/* It runs the same persistent BFS kernel as byo_bfs for ONE source.  All    */
+/* scratch lives in a fixed file-scope device array of 9,308,160 bytes,    */
+/* sized for n <= BYO_NOALLOC_MAX_VERTICES; every GPU that loads the       */
+/* library holds it until the process exits.  The call makes no cudaMalloc, */
+/* cudaFree or other allocating call.                                       */
+/*   n, m     vertices (1 <= n <= BYO_NOALLOC_MAX_VERTICES, else             */
+/*            BYO_ERR_INVALID_ARG) and stored entries                        */
+/*   offsets  device uint64[n+1]; col device uint32 ids, neighbours of each */
+/*            vertex ascending, the graph symmetric without self-loops (as  */
+/*            byo_graph_export_csr returns it); col must start on a 16-byte */
+/*            boundary and be readable up to index m+3 (vector reads)       */
+/*   levels   device uint32[n] out; parents device uint32[n] out or NULL;   */
+/*            same meaning as byo_bfs                                        */
+/*   sched    as for byo_bfs (NULL = default)                               */
+/* The first call on a device looks up the array's device address (with     */
+/* that device current) and caches it; make that first call before any     */
+/* stream capture.  Every call shares the one array: calls that overlap on  */
+/* the GPU (other streams, other host threads) race and must not be issued. */
+/* Synchronises the stream.  Errors: INVALID_ARG, TIMEOUT, CUDA.            */
+#define BYO_NOALLOC_MAX_VERTICES (1u << 20)
+byo_status byo_bfs_noalloc(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* col, uint32_t source,
+                           uint32_t* levels, uint32_t* parents, const byo_sched* sched, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Tracing.  Every kernel launch of the library increments a process-wide    */
 /* counter.  With profiling on, the main kernels of each call are bracketed  */
 /* by CUDA events on the caller's stream; byo_profile_read resolves them     */

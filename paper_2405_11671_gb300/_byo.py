@@ -88,6 +88,7 @@ SIGNATURES = [
     ("byo_mlp_loss_grad", _st, [_vp, _vp, _vp, _vp, _u32, _vp, ctypes.POINTER(ctypes.c_float), _vp]),
     ("byo_mlp_train", _st, [_vp, _vp, _vp, _vp, _u32, _u32, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp]),
     ("byo_mlp_predict", _st, [_vp, _vp, _u32, _vp, _vp]),
+    ("byo_bfs_noalloc", _st, [_u32, _u64, _vp, _vp, _u32, _vp, _vp, ctypes.POINTER(byo_sched), _vp]),
     ("byo_kernel_launches", _u64, []),
     ("byo_profile_enable", _st, [ctypes.c_int]),
     ("byo_profile_reset", _st, []),
@@ -309,6 +310,25 @@ def byo_mlp_predict(m: int, X: torch.Tensor, stream=None) -> torch.Tensor:
     out = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
     _check(load().byo_mlp_predict(m, X.data_ptr(), X.shape[0], out.data_ptr(), _stream(stream)))
     return out
+
+
+BYO_NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def byo_bfs_noalloc(n: int, m: int, offsets: torch.Tensor, col: torch.Tensor, source: int, levels: torch.Tensor,
+                    parents: torch.Tensor | None = None, sched: byo_sched | None = None, stream=None) -> None:
+    """BFS from one source over a caller-owned CSR, using only the library's
+    built-in scratch array (no device allocation by the library or here).
+    offsets: int64 CUDA tensor [n+1]; col: int32 CUDA tensor, 16-byte aligned,
+    with at least m+4 entries; levels/parents: int32 CUDA tensors [n]."""
+    _dev(offsets, torch.int64, "offsets")
+    _u32t(col, "col")
+    _u32t(levels, "levels")
+    if parents is not None:
+        _u32t(parents, "parents")
+    sp = ctypes.byref(sched) if sched is not None else None
+    _check(load().byo_bfs_noalloc(n, m, offsets.data_ptr(), col.data_ptr(), source, levels.data_ptr(),
+                                  parents.data_ptr() if parents is not None else None, sp, _stream(stream)))
 
 
 # ----------------------------------------------------------------------------- tracing

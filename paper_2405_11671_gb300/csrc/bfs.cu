@@ -28,6 +28,8 @@
 //   frontier exist after a pull.
 #include <math.h>
 
+#include <mutex>
+
 #include "byo_internal.cuh"
 #include "container.cuh"
 #include "prof.cuh"
@@ -637,6 +639,137 @@ extern "C" byo_status byo_bfs_trace(const byo_graph* g, byo_bfs_iter* host_recor
   if (c) {
     BYO_CUDA(cudaMemcpyAsync(host_records, g->bfs->trace, sizeof(byo_bfs_iter) * c, cudaMemcpyDeviceToHost, s));
     BYO_CUDA(cudaStreamSynchronize(s));
+  }
+  return BYO_OK;
+}
+
+// ============================================================================
+// BFS without any device allocation, for callers that cannot allocate device
+// memory themselves or through this library.  The caller passes the CSR and
+// the outputs; every piece of scratch the persistent BFS kernel needs (control
+// block, bucket starts, visited and frontier bits, the bucketed queue, the
+// iteration trace) lives in one file-scope __device__ array of fixed size,
+// shared by every call on a device and kept until the process exits.
+
+namespace byo {
+namespace {
+
+constexpr uint32_t kNoallocMaxVertices = 1u << 20;
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kNaWords = (kNoallocMaxVertices + 31) / 32;
+constexpr size_t kNaCtl = 0;
+constexpr size_t kNaBstart = kNaCtl + na_align(sizeof(BfsCtl));
+constexpr size_t kNaHist = kNaBstart + na_align(sizeof(uint64_t) * (kBuckets + 1));
+constexpr size_t kNaVis = kNaHist + na_align(sizeof(unsigned long long) * kBuckets);
+constexpr size_t kNaFb = kNaVis + na_align(4 * kNaWords);
+constexpr size_t kNaQueue = kNaFb + na_align(8 * kNaWords);
+constexpr size_t kNaTrace = kNaQueue + na_align(4ull * kNoallocMaxVertices);
+constexpr size_t kNaBytes = kNaTrace + na_align(sizeof(byo_bfs_iter) * kTraceCap);
+
+// 9,308,160 bytes (8.9 MiB).  In host code this name is only a host-side stand-in for the
+// array; kernels get its device address from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+std::mutex g_na_mu;
+void* g_na_addr[256] = {nullptr};
+
+// Device address of the array on the current device, looked up once per device.
+byo_status noalloc_scratch(void** out) {
+  int dev = 0;
+  BYO_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) {
+    set_error("byo_bfs_noalloc: device index %d out of range", dev);
+    return BYO_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (!g_na_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
+    g_na_addr[dev] = p;
+  }
+  *out = g_na_addr[dev];
+  return BYO_OK;
+}
+
+__global__ void noalloc_hist_kernel(const uint64_t* __restrict__ off, uint32_t n, unsigned long long* hist) {
+  __shared__ unsigned long long h[kBuckets];
+  for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[degree_bucket((uint32_t)(off[v + 1] - off[v]))], 1ull);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBuckets; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+__global__ void noalloc_bstart_kernel(const unsigned long long* hist, uint64_t* bstart) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    bstart[0] = 0;
+    for (int b = 0; b < kBuckets; ++b) bstart[b + 1] = bstart[b] + hist[b];
+  }
+}
+
+}  // namespace
+}  // namespace byo
+
+extern "C" byo_status byo_bfs_noalloc(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* col,
+                                      uint32_t source, uint32_t* levels, uint32_t* parents, const byo_sched* sched,
+                                      void* stream) {
+  clear_error();
+  if (n == 0 || n > kNoallocMaxVertices) {
+    set_error("byo_bfs_noalloc: n = %u is outside [1, %u], the size of the built-in scratch", n,
+              kNoallocMaxVertices);
+    return BYO_ERR_INVALID_ARG;
+  }
+  if (!offsets || !levels || (m && !col) || source >= n) {
+    set_error("byo_bfs_noalloc: NULL offsets/levels/col or source >= n");
+    return BYO_ERR_INVALID_ARG;
+  }
+  if (m && (reinterpret_cast<uintptr_t>(col) & 15)) {
+    set_error("byo_bfs_noalloc: col must start on a 16-byte boundary");
+    return BYO_ERR_INVALID_ARG;
+  }
+  SchedParams sp;
+  BYO_RETURN_IF(sched_params(sched, &sp));
+  void* base = nullptr;
+  BYO_RETURN_IF(noalloc_scratch(&base));
+  unsigned char* b = static_cast<unsigned char*>(base);
+  BfsCtl* ctl = reinterpret_cast<BfsCtl*>(b + kNaCtl);
+  uint64_t* bstart = reinterpret_cast<uint64_t*>(b + kNaBstart);
+  unsigned long long* hist = reinterpret_cast<unsigned long long*>(b + kNaHist);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: clear what must start at zero
+  BYO_CUDA(cudaMemsetAsync(ctl, 0, sizeof(BfsCtl), s));
+  BYO_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kBuckets, s));
+  noalloc_hist_kernel<<<(unsigned)sm_count() * 2, 256, 0, s>>>(offsets, n, hist);
+  note_launch();
+  BYO_CHECK_LAUNCH("noalloc_hist_kernel");
+  noalloc_bstart_kernel<<<1, 32, 0, s>>>(hist, bstart);
+  note_launch();
+  BYO_CHECK_LAUNCH("noalloc_bstart_kernel");
+  BfsArgs<CsrView<uint64_t>> args;
+  args.g = CsrView<uint64_t>{n, m, offsets, col};
+  args.src = source;
+  args.level = levels;
+  args.parent = parents;
+  args.vis = reinterpret_cast<uint32_t*>(b + kNaVis);
+  args.fb = reinterpret_cast<uint32_t*>(b + kNaFb);
+  args.queue = reinterpret_cast<uint32_t*>(b + kNaQueue);
+  args.bstart = bstart;
+  args.ctl = ctl;
+  args.trace = reinterpret_cast<byo_bfs_iter*>(b + kNaTrace);
+  args.sp = sp;
+  args.limit_ns = timeout_ns();
+  args.nw = (n + 31) / 32;
+  if (parents) BYO_RETURN_IF((launch_bfs<CsrView<uint64_t>, true>(args, s)));
+  else BYO_RETURN_IF((launch_bfs<CsrView<uint64_t>, false>(args, s)));
+  uint32_t err = 0;
+  BYO_CUDA(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  BYO_CUDA(cudaStreamSynchronize(s));
+  if (err) {
+    set_error("byo_bfs_noalloc: a device-side wait exceeded BYO_TIMEOUT_MS");
+    return BYO_ERR_TIMEOUT;
   }
   return BYO_OK;
 }
