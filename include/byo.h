@@ -53,6 +53,10 @@ const char* byo_last_error(void);
 
 /*
  * Build a graph container from k raw pairs src[i] -> dst[i] (device arrays).
+ * BYO_CSR builds the static CSR; BYO_DYNAMIC the blocked adjacency (a 64-byte
+ * record per vertex with up to 12 neighbours inline -- the inline optimisation
+ * of Section 4.1 -- else a run of 128-byte blocks from a device pool), which
+ * accepts byo_insert_batch / byo_delete_batch.
  * Follows the graph model of Section 3 (vertices 0..n-1, a neighbour SET per
  * vertex, Section 3.1) and the CSR layout named in Section 4.2: duplicate
  * pairs collapse, self-loops are dropped, neighbours are stored ascending.
@@ -81,6 +85,19 @@ byo_status byo_num_edges(const byo_graph* g, uint64_t* host_m);
  * (device), written to out[k]; vs == NULL means all n vertices (out[n]).
  * Ids >= n give BYO_ERR_INVALID_ARG (checked on the device; synchronises). */
 byo_status byo_degree(const byo_graph* g, const uint32_t* vs, uint64_t k, uint32_t* out, void* stream);
+
+/*
+ * Batch updates of a BYO_DYNAMIC container: insert_sorted_batch and
+ * delete_sorted_batch of the GraphContainer API (Section 4.2).  The batch is k
+ * raw device pairs in any order; as BYO does, the library sorts it first.  Set
+ * semantics (Section 3.1): each pair is applied in both directions, self-loops
+ * are ignored, duplicates collapse, inserting a present edge or deleting an
+ * absent one changes nothing.  num_edges() and degree() reflect the batch when
+ * the call returns.  Synchronises the stream.  Errors: UNSUPPORTED (static
+ * CSR), INVALID_ARG (NULL arrays with k > 0, id >= n), OUT_OF_MEMORY, CUDA.
+ */
+byo_status byo_insert_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t k, void* stream);
+byo_status byo_delete_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t k, void* stream);
 
 /* Copy the container out as a CSR: offsets[n+1] (uint64) and col[m], neighbours
  * ascending.  For a dynamic container this is the snapshot used to compare its
@@ -212,6 +229,33 @@ byo_status byo_pagerank(const byo_graph* g, float damping, uint32_t iters, float
  * synchronises.  Errors: INVALID_ARG, OUT_OF_MEMORY, TIMEOUT, CUDA.
  */
 byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Many graphs at once.  byo_batch_build stores num_graphs graphs as one      */
+/* container over their disjoint union: member i owns the global ids          */
+/* [base_i, base_i + n_i), base_i = n_0 + ... + n_{i-1} (byo_batch_member_base */
+/* returns it).  Every call of this header then works on all members at once  */
+/* (e.g. byo_cc labels every member's components by their minimum global id). */
+/*   host_n[i], host_k[i]  vertices and raw pairs of member i (host arrays)    */
+/*   src, dst              the members' pairs concatenated, LOCAL ids (device) */
+/*   flags                 as for byo_graph_build                             */
+/* Errors: INVALID_ARG (a local id >= n_i, total vertices >= 2^32 - 1), OOM,  */
+/* CUDA.  Synchronises the stream.                                           */
+byo_status byo_batch_build(uint32_t num_graphs, const uint32_t* host_n, const uint64_t* host_k, const uint32_t* src,
+                           const uint32_t* dst, uint32_t flags, void* stream, byo_graph** out);
+byo_status byo_batch_member_base(const byo_graph* g, uint32_t i, uint32_t* host_base);
+
+/*
+ * Multi-source BFS: num_sources (1..64) sources in EVERY member, traversed
+ * together with one bit per source (edgeMap over 64 frontiers at once, Section
+ * 3.2), top-down or bottom-up per level, in one persistent launch for the whole
+ * batch.  host_sources[i * num_sources + j] is source j of member i as a LOCAL
+ * id (a plain graph is a batch of one).  levels[j * n + v] (device, n = total
+ * vertices) = hop distance of global vertex v from source j of v's member, INF
+ * if unreached.  Synchronises the stream.  Errors: INVALID_ARG, TIMEOUT, CUDA.
+ */
+byo_status byo_msbfs(const byo_graph* g, const uint32_t* host_sources, uint32_t num_sources, uint32_t* levels,
+                     void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* BFS that allocates nothing (the paper has no counterpart; this is a       */

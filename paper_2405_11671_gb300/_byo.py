@@ -74,6 +74,8 @@ SIGNATURES = [
     ("byo_num_edges", _st, [_vp, ctypes.POINTER(_u64)]),
     ("byo_degree", _st, [_vp, _vp, _u64, _vp, _vp]),
     ("byo_graph_export_csr", _st, [_vp, _vp, _vp, _vp]),
+    ("byo_insert_batch", _st, [_vp, _vp, _vp, _u64, _vp]),
+    ("byo_delete_batch", _st, [_vp, _vp, _vp, _u64, _vp]),
     ("byo_sched_default", byo_sched, []),
     ("byo_bfs", _st, [_vp, ctypes.POINTER(_u32), _u32, _vp, _vp, ctypes.POINTER(byo_sched), _vp]),
     ("byo_bfs_trace", _st, [_vp, ctypes.POINTER(byo_bfs_iter), _u32, ctypes.POINTER(_u32), _vp]),
@@ -88,6 +90,10 @@ SIGNATURES = [
     ("byo_mlp_loss_grad", _st, [_vp, _vp, _vp, _vp, _u32, _vp, ctypes.POINTER(ctypes.c_float), _vp]),
     ("byo_mlp_train", _st, [_vp, _vp, _vp, _vp, _u32, _u32, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp]),
     ("byo_mlp_predict", _st, [_vp, _vp, _u32, _vp, _vp]),
+    ("byo_batch_build", _st, [_u32, ctypes.POINTER(_u32), ctypes.POINTER(_u64), _vp, _vp, _u32, _vp,
+                               ctypes.POINTER(_vp)]),
+    ("byo_batch_member_base", _st, [_vp, _u32, ctypes.POINTER(_u32)]),
+    ("byo_msbfs", _st, [_vp, ctypes.POINTER(_u32), _u32, _vp, _vp]),
     ("byo_bfs_noalloc", _st, [_u32, _u64, _vp, _vp, _u32, _vp, _vp, ctypes.POINTER(byo_sched), _vp]),
     ("byo_kernel_launches", _u64, []),
     ("byo_profile_enable", _st, [ctypes.c_int]),
@@ -197,6 +203,20 @@ def byo_graph_export_csr(g: int, stream=None):
     col = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
     _check(load().byo_graph_export_csr(g, off.data_ptr(), col.data_ptr(), _stream(stream)))
     return off, col[:m]
+
+
+def byo_insert_batch(g: int, src: torch.Tensor, dst: torch.Tensor, stream=None) -> None:
+    src, dst = _u32t(src, "src"), _u32t(dst, "dst")
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst differ in length")
+    _check(load().byo_insert_batch(g, src.data_ptr(), dst.data_ptr(), src.numel(), _stream(stream)))
+
+
+def byo_delete_batch(g: int, src: torch.Tensor, dst: torch.Tensor, stream=None) -> None:
+    src, dst = _u32t(src, "src"), _u32t(dst, "dst")
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst differ in length")
+    _check(load().byo_delete_batch(g, src.data_ptr(), dst.data_ptr(), src.numel(), _stream(stream)))
 
 
 # ----------------------------------------------------------------------------- algorithms
@@ -310,6 +330,38 @@ def byo_mlp_predict(m: int, X: torch.Tensor, stream=None) -> torch.Tensor:
     out = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
     _check(load().byo_mlp_predict(m, X.data_ptr(), X.shape[0], out.data_ptr(), _stream(stream)))
     return out
+
+
+def byo_batch_build(ns, ks, src: torch.Tensor, dst: torch.Tensor, flags: int = BYO_CSR | BYO_SYMMETRIZE,
+                    stream=None) -> int:
+    """One container over the disjoint union of len(ns) graphs (local-id pairs concatenated)."""
+    n_arr = np.ascontiguousarray(np.asarray(ns, dtype=np.uint32))
+    k_arr = np.ascontiguousarray(np.asarray(ks, dtype=np.uint64))
+    src, dst = _u32t(src, "src"), _u32t(dst, "dst")
+    if src.numel() != int(k_arr.sum()) or dst.numel() != src.numel():
+        raise ValueError("pair arrays do not match the per-member counts")
+    out = _vp()
+    _check(load().byo_batch_build(len(n_arr), n_arr.ctypes.data_as(ctypes.POINTER(_u32)),
+                                  k_arr.ctypes.data_as(ctypes.POINTER(_u64)), src.data_ptr(), dst.data_ptr(), flags,
+                                  _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def byo_batch_member_base(g: int, i: int) -> int:
+    v = _u32()
+    _check(load().byo_batch_member_base(g, i, ctypes.byref(v)))
+    return v.value
+
+
+def byo_msbfs(g: int, sources, num_sources: int, levels: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """levels[num_sources, n]; sources = members x num_sources LOCAL ids (row-major)."""
+    srcs = np.ascontiguousarray(np.asarray(sources, dtype=np.uint32).reshape(-1))
+    n = byo_num_vertices(g)
+    if levels is None:
+        levels = torch.empty((num_sources, n), dtype=torch.int32, device="cuda")
+    _check(load().byo_msbfs(g, srcs.ctypes.data_as(ctypes.POINTER(_u32)), num_sources, levels.data_ptr(),
+                            _stream(stream)))
+    return levels
 
 
 BYO_NOALLOC_MAX_VERTICES = 1 << 20

@@ -527,12 +527,12 @@ byo_status launch_bfs(BfsArgs<G>& args, cudaStream_t s) {
   return BYO_OK;
 }
 
-template <typename OffT>
-byo_status run_bfs(const byo_graph* g, const uint32_t* sources, uint32_t ns, uint32_t* levels, uint32_t* parents,
+template <typename G>
+byo_status run_bfs(const byo_graph* g, G view, const uint32_t* sources, uint32_t ns, uint32_t* levels, uint32_t* parents,
                    const SchedParams& sp, cudaStream_t s) {
   BfsWork* w = g->bfs;
-  BfsArgs<CsrView<OffT>> args;
-  args.g = CsrView<OffT>{g->n, g->m, static_cast<const OffT*>(g->off), g->col};
+  BfsArgs<G> args;
+  args.g = view;
   args.vis = w->vis;
   args.fb = w->fb;
   args.queue = w->queue;
@@ -546,8 +546,8 @@ byo_status run_bfs(const byo_graph* g, const uint32_t* sources, uint32_t ns, uin
     args.src = sources[i];
     args.level = levels + (size_t)i * g->n;
     args.parent = parents ? parents + (size_t)i * g->n : nullptr;
-    if (parents) BYO_RETURN_IF((launch_bfs<CsrView<OffT>, true>(args, s)));
-    else BYO_RETURN_IF((launch_bfs<CsrView<OffT>, false>(args, s)));
+    if (parents) BYO_RETURN_IF((launch_bfs<G, true>(args, s)));
+    else BYO_RETURN_IF((launch_bfs<G, false>(args, s)));
   }
   return BYO_OK;
 }
@@ -603,8 +603,9 @@ extern "C" byo_status byo_bfs(const byo_graph* gc, const uint32_t* host_sources,
   BYO_RETURN_IF(sched_params(sched, &sp));
   BYO_RETURN_IF(ensure_bfs_work(g));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  byo_status st = g->off64 ? run_bfs<uint64_t>(g, host_sources, num_sources, levels, parents, sp, s)
-                           : run_bfs<uint32_t>(g, host_sources, num_sources, levels, parents, sp, s);
+  byo_status st = with_view(g, [&](auto view) {
+    return run_bfs(g, view, host_sources, num_sources, levels, parents, sp, s);
+  });
   BYO_RETURN_IF(st);
   uint32_t err = 0;
   BYO_CUDA(cudaMemcpyAsync(&err, &g->bfs->ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -73,6 +73,7 @@ byo_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint64_t n, int bits, u
 struct BfsWork;
 struct PrWork;
 struct TcWork;
+struct DynStore;
 
 }  // namespace byo
 
@@ -94,13 +95,35 @@ struct byo_graph {
   byo::BfsWork* bfs = nullptr;
   byo::PrWork* pr = nullptr;
   byo::TcWork* tc = nullptr;
+  byo::DynStore* dyn = nullptr;  // set for BYO_DYNAMIC (then off/col are unused)
+  // batch of graphs (byo_batch_build): member i owns ids [member_base[i], member_base[i+1])
+  uint32_t members = 0;
+  uint32_t* member_base = nullptr;       // device
+  uint32_t* member_base_host = nullptr;  // host
+  // multi-source BFS scratch
+  unsigned long long* ms_seen = nullptr;  // seen, frontier, next words (3n)
+  void* ms_ctl = nullptr;
+  uint32_t* ms_src = nullptr;
+  uint64_t ms_src_cap = 0;
 };
 
 namespace byo {
 void bfs_free(BfsWork* w);
 void pr_free(PrWork* w);
 void tc_free(TcWork* w);
+void dyn_free(DynStore* d);
 byo_status check_graph(const byo_graph* g);
+// Sorted, unique (row, col) pairs of k raw pairs (both directions when sym,
+// self-loops dropped).  *rows and *cols are stream-ordered temporaries of
+// *count + 4 entries that the caller releases with tmp_free.  Ids >= n give
+// BYO_ERR_INVALID_ARG.  Synchronises the stream.
+byo_status sort_unique_pairs(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t k, bool sym,
+                             cudaStream_t s, uint32_t** rows, uint32_t** cols, uint64_t* count);
+// Recompute vorder / bstart from the container's current degrees.
+byo_status rebuild_buckets(byo_graph* g, cudaStream_t s);
+// Fill g->dyn from the CSR just built in g (then releases the CSR arrays).
+byo_status dyn_from_csr(byo_graph* g, cudaStream_t s);
+unsigned grid_for(uint64_t work, int threads);
 }  // namespace byo
 
 // ================================================================ device side

@@ -51,7 +51,7 @@ __global__ void cc_init_kernel(G g, uint32_t* p) {
 }
 
 template <typename G>
-__global__ void __launch_bounds__(kCcThreads) cc_hook_kernel(G g, VBins bins, uint32_t* p) {
+__global__ void __launch_bounds__(kCcThreads) cc_hook_kernel(G g, VBins bins, CtaChunks hubs, uint32_t* p) {
   VRange r = vbins_range(bins);
   const uint32_t lane = lane_id();
   if (r.role == kRoleThread) {
@@ -76,15 +76,20 @@ __global__ void __launch_bounds__(kCcThreads) cc_hook_kernel(G g, VBins bins, ui
       }
     }
   } else {
+    // high degree: chunks of the list spread over CTAs (unions are independent)
     __shared__ int stop;
-    for (uint64_t i = r.begin; i < r.end; i += r.stride) {
-      uint32_t v = __ldg(bins.vorder + i);
+    for (uint64_t j = blockIdx.x - bins.nbT - bins.nbW; j < hubs.items; j += bins.nbC) {
+      ChunkItem it = chunk_item(hubs, j);
+      uint32_t v = __ldg(bins.vorder + it.vidx);
       Seg s = g.seg(v);
-      for (uint32_t base = 1; base < s.len; base += blockDim.x) {
+      uint32_t lo, hi;
+      chunk_range(s.len, it.chunk, it.K, &lo, &hi);
+      if (lo == 0) lo = 1;  // entry 0 was hooked by the init
+      for (uint32_t base = lo; base < hi; base += blockDim.x) {
         if (threadIdx.x == 0) stop = 0;
         __syncthreads();
         uint32_t k = base + threadIdx.x;
-        uint32_t u = k < s.len ? __ldg(s.p + k) : kInf;
+        uint32_t u = k < hi ? __ldg(s.p + k) : kInf;
         if (u < v) cc_union(p, u, v);
         else stop = 1;
         __syncthreads();
@@ -111,9 +116,8 @@ __global__ void cc_compress_kernel(uint32_t* p, uint32_t n) {
   }
 }
 
-template <typename OffT>
-byo_status run_cc(const byo_graph* g, uint32_t* labels, cudaStream_t s) {
-  CsrView<OffT> view{g->n, g->m, static_cast<const OffT*>(g->off), g->col};
+template <typename G>
+byo_status run_cc(const byo_graph* g, G view, uint32_t* labels, cudaStream_t s) {
   unsigned grid = (unsigned)((uint64_t)sm_count() * 8);
   {
     ProfScope ps("cc_init", s);
@@ -121,9 +125,14 @@ byo_status run_cc(const byo_graph* g, uint32_t* labels, cudaStream_t s) {
   }
   BYO_CHECK_LAUNCH("cc_init_kernel");
   VBins bins = make_vbins(g, 5, 11, kCcThreads);
+  CtaChunks hubs = make_cta_chunks(g, 12, 12);  // degrees >= 2048, chunks of <= 4096 ids
+  {
+    uint64_t cap = (uint64_t)sm_count() * 8;
+    bins.nbC = (uint32_t)(hubs.items < cap ? hubs.items : cap);
+  }
   {
     ProfScope ps("cc_hook", s);
-    cc_hook_kernel<<<vbins_grid(bins), kCcThreads, 0, s>>>(view, bins, labels); ::byo::note_launch();
+    cc_hook_kernel<<<vbins_grid(bins), kCcThreads, 0, s>>>(view, bins, hubs, labels); ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("cc_hook_kernel");
   {
@@ -148,5 +157,5 @@ extern "C" byo_status byo_cc(const byo_graph* g, uint32_t* labels, void* stream)
     return BYO_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return g->off64 ? run_cc<uint64_t>(g, labels, s) : run_cc<uint32_t>(g, labels, s);
+  return with_view(g, [&](auto view) { return run_cc(g, view, labels, s); });
 }

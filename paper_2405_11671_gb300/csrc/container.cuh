@@ -63,3 +63,75 @@ __device__ __forceinline__ const uint32_t* align16_down(const uint32_t* p) {
 }
 
 }  // namespace byo
+
+namespace byo {
+
+// ---------------------------------------------------------------- dynamic container
+// Blocked adjacency with an inline head (the inline optimisation of Section
+// 4.1, here ~12 ids next to the vertex record).  A vertex with at most
+// kInline neighbours keeps them in its 64-byte record; a larger one keeps all
+// of them, ascending, in a run of 2^cls blocks of 32 ids (128 bytes each) from
+// a device pool.  Either way the list is ONE contiguous ascending segment, so
+// every algorithm kernel runs unchanged over both containers.
+constexpr uint32_t kInline = 12;
+constexpr uint32_t kBlockIds = 32;
+constexpr uint32_t kNoRun = 0xFFFFFFFFu;
+
+struct __align__(64) DynVertex {
+  uint32_t deg;
+  uint32_t cls;  // kNoRun when the list is inline
+  uint64_t run;  // first block of the run (block index into the pool)
+  uint32_t inl[kInline];
+};
+
+struct DynView {
+  uint32_t n;
+  uint64_t m;
+  const DynVertex* vtx;
+  const uint32_t* pool;
+
+  __device__ __forceinline__ uint32_t num_vertices() const { return n; }
+  __device__ __forceinline__ uint64_t num_edges() const { return m; }
+  __device__ __forceinline__ uint32_t degree(uint32_t v) const { return __ldg(&vtx[v].deg); }
+  __device__ __forceinline__ Seg seg(uint32_t v) const {
+    uint32_t d = __ldg(&vtx[v].deg);
+    const uint32_t* p = d <= kInline ? vtx[v].inl : pool + __ldg(&vtx[v].run) * kBlockIds;
+    return Seg{p, d};
+  }
+  template <typename F>
+  __device__ __forceinline__ void map_neighbors(uint32_t v, F&& f) const {
+    Seg s = seg(v);
+    for (uint32_t i = 0; i < s.len; ++i) f(__ldg(s.p + i));
+  }
+  template <typename F>
+  __device__ __forceinline__ uint32_t map_neighbors_early_exit(uint32_t v, F&& f) const {
+    Seg s = seg(v);
+    for (uint32_t i = 0; i < s.len; ++i)
+      if (f(__ldg(s.p + i))) return i;
+    return s.len;
+  }
+};
+
+constexpr int kClasses = 27;  // run sizes 2^0 .. 2^26 blocks
+
+struct DynStore {
+  DynVertex* vtx = nullptr;        // n + 1 records (the spare keeps vector tail reads inside)
+  uint32_t* pool = nullptr;        // pool_blocks * 32 ids
+  uint64_t pool_blocks = 0;
+  unsigned long long* bump = nullptr;  // next free block (device)
+  uint32_t* stacks[kClasses] = {nullptr};  // free runs per class
+  uint64_t stack_cap[kClasses] = {0};
+  long long* tops = nullptr;       // kClasses stack tops (device)
+};
+
+inline DynView dyn_view(const byo_graph* g) { return DynView{g->n, g->m, g->dyn->vtx, g->dyn->pool}; }
+
+// Call f with the device view of g's container.
+template <typename F>
+inline byo_status with_view(const byo_graph* g, F&& f) {
+  if (g->dyn) return f(dyn_view(g));
+  if (g->off64) return f(CsrView<uint64_t>{g->n, g->m, static_cast<const uint64_t*>(g->off), g->col});
+  return f(CsrView<uint32_t>{g->n, g->m, static_cast<const uint32_t*>(g->off), g->col});
+}
+
+}  // namespace byo

@@ -145,15 +145,14 @@ __global__ void offsets_kernel(const uint32_t* __restrict__ rows, uint64_t m, ui
 }
 
 // keys for grouping vertices by degree bucket, ascending id inside a bucket
-template <typename OffT>
-__global__ void bucket_keys_kernel(const OffT* __restrict__ off, uint32_t n, int lb, uint64_t* keys,
-                                   unsigned long long* hist) {
+template <typename G>
+__global__ void bucket_keys_kernel(G g, int lb, uint64_t* keys, unsigned long long* hist) {
   __shared__ unsigned long long h[kBuckets];
   for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) h[i] = 0;
   __syncthreads();
+  const uint32_t n = g.num_vertices();
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t d = (uint32_t)(off[v + 1] - off[v]);
-    int b = degree_bucket(d);
+    int b = degree_bucket(g.degree((uint32_t)v));
     keys[v] = ((uint64_t)b << lb) | v;
     atomicAdd(&h[b], 1ull);
   }
@@ -184,12 +183,11 @@ __global__ void symmetric_kernel(const OffT* __restrict__ off, const uint32_t* _
   }
 }
 
-template <typename OffT>
-__global__ void degree_kernel(CsrView<OffT> g, const uint32_t* __restrict__ vs, uint64_t k, uint32_t* out,
-                              uint32_t* bad) {
+template <typename G>
+__global__ void degree_kernel(G g, const uint32_t* __restrict__ vs, uint64_t k, uint32_t* out, uint32_t* bad) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t v = vs ? vs[i] : (uint32_t)i;
-    if (v >= g.n) {
+    if (v >= g.num_vertices()) {
       atomicOr(bad, 1u);
       out[i] = 0;
     } else {
@@ -198,11 +196,30 @@ __global__ void degree_kernel(CsrView<OffT> g, const uint32_t* __restrict__ vs, 
   }
 }
 
-template <typename OffT>
-__global__ void export_off_kernel(const OffT* __restrict__ off, uint32_t n, uint64_t* out) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x)
-    out[i] = (uint64_t)off[i];
+template <typename G>
+__global__ void degrees_kernel(G g, uint32_t* deg) {
+  const uint32_t n = g.num_vertices();
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+    deg[v] = g.degree((uint32_t)v);
 }
+
+// one warp per vertex copies its list to col[off[v]...]
+template <typename G>
+__global__ void export_col_kernel(G g, const uint64_t* __restrict__ off, uint32_t* __restrict__ col) {
+  const uint32_t n = g.num_vertices();
+  const uint32_t lane = lane_id();
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t v = w0; v < n; v += nw) {
+    Seg sg = g.seg((uint32_t)v);
+    uint64_t o = off[v];
+    for (uint32_t i = lane; i < sg.len; i += 32) col[o + i] = __ldg(sg.p + i);
+  }
+}
+
+__global__ void set_last_u64_kernel(uint64_t* a, uint64_t i, uint64_t v) { a[i] = v; }
+
+}  // namespace
 
 unsigned grid_for(uint64_t work, int threads) {
   uint64_t b = (work + threads - 1) / threads;
@@ -211,6 +228,8 @@ unsigned grid_for(uint64_t work, int threads) {
   if (b == 0) b = 1;
   return (unsigned)b;
 }
+
+namespace {
 
 int bits_for(uint32_t n) {
   int lb = 1;
@@ -226,8 +245,8 @@ byo_status finish_csr(byo_graph* g, const uint32_t* rows, cudaStream_t s) {
   return BYO_OK;
 }
 
-template <typename OffT>
-byo_status build_buckets(byo_graph* g, cudaStream_t s) {
+template <typename G>
+byo_status build_buckets(byo_graph* g, G view, cudaStream_t s) {
   uint32_t n = g->n;
   int lb = bits_for(n > 1 ? n : 2);
   uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr;
@@ -235,11 +254,11 @@ byo_status build_buckets(byo_graph* g, cudaStream_t s) {
   BYO_RETURN_IF(tmp_alloc_t(&keys, n, s, "bucket keys"));
   byo_status st = tmp_alloc_t(&tmp, n, s, "bucket keys tmp");
   if (st == BYO_OK) st = tmp_alloc_t(&hist, kBuckets, s, "bucket histogram");
-  if (st == BYO_OK) st = dev_alloc_t(&g->vorder, n, "vertex order");
-  if (st == BYO_OK) st = dev_alloc_t(&g->d_bstart, kBuckets + 1, "bucket starts");
+  if (st == BYO_OK && !g->vorder) st = dev_alloc_t(&g->vorder, n, "vertex order");
+  if (st == BYO_OK && !g->d_bstart) st = dev_alloc_t(&g->d_bstart, kBuckets + 1, "bucket starts");
   if (st == BYO_OK) {
     cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kBuckets, s);
-    bucket_keys_kernel<OffT><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const OffT*>(g->off), n, lb, keys, hist); ::byo::note_launch();
+    bucket_keys_kernel<G><<<grid_for(n, 256), 256, 0, s>>>(view, lb, keys, hist); ::byo::note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_status(e, "bucket_keys_kernel");
   }
@@ -274,64 +293,37 @@ void graph_free(byo_graph* g) {
   bfs_free(g->bfs);
   pr_free(g->pr);
   tc_free(g->tc);
+  dyn_free(g->dyn);
+  if (g->member_base) cudaFree(g->member_base);
+  delete[] g->member_base_host;
+  dev_free(g->ms_seen);
+  dev_free(g->ms_ctl);
+  dev_free(g->ms_src);
   delete g;
 }
 
 byo_status build_csr(byo_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t k, bool sym, cudaStream_t s) {
   const uint32_t n = g->n;
-  const int lb = bits_for(n > 1 ? n : 2);
-  const uint64_t cnt = sym ? 2 * k : k;
-  uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr, *pos = nullptr;
-  uint32_t *flags = nullptr, *rows = nullptr, *bad = nullptr;
-  byo_status st = tmp_alloc_t(&bad, 4, s, "flag");
-  if (st == BYO_OK) st = tmp_alloc_t(&keys, cnt, s, "edge keys");
-  if (st == BYO_OK) st = tmp_alloc_t(&tmp, cnt, s, "edge keys tmp");
-  if (st == BYO_OK) {
-    cudaMemsetAsync(bad, 0, 16, s);
-    if (k) make_keys_kernel<<<grid_for(k, 256), 256, 0, s>>>(src, dst, k, n, lb, sym, keys, bad); ::byo::note_launch();
-    cudaError_t e = cudaGetLastError();
-    uint32_t hbad = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = cuda_status(e, "make_keys_kernel");
-    else if (hbad) {
-      set_error("byo_graph_build: a vertex id is >= n (%u)", n);
-      st = BYO_ERR_INVALID_ARG;
-    }
-  }
-  if (st == BYO_OK) st = radix_sort_u64(keys, tmp, cnt, 2 * lb, &sorted, s);
-  // reuse the other key buffer for the positions
-  if (st == BYO_OK) {
-    pos = sorted == keys ? tmp : keys;
-    st = tmp_alloc_t(&flags, cnt, s, "unique flags");
-  }
+  uint32_t *rows = nullptr, *cols = nullptr, *bad = nullptr;
   uint64_t m = 0;
-  if (st == BYO_OK) {
-    if (cnt) unique_flags_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(sorted, cnt, lb, flags); ::byo::note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) st = cuda_status(e, "unique_flags_kernel");
-  }
-  if (st == BYO_OK) st = scan_u32_to_u64(flags, pos, cnt, &m, s);
-  if (st == BYO_OK) {
-    g->m = m;
-    g->off64 = (g->flags & BYO_OFFSETS64) || m >= (1ull << 32);
-    st = dev_alloc(&g->off, (size_t)(n + 1) * (g->off64 ? 8 : 4) + 16, "CSR offsets");
-  }
+  BYO_RETURN_IF(sort_unique_pairs(n, src, dst, k, sym, s, &rows, &cols, &m));
+  g->m = m;
+  g->off64 = (g->flags & BYO_OFFSETS64) || m >= (1ull << 32);
+  byo_status st = dev_alloc(&g->off, (size_t)(n + 1) * (g->off64 ? 8 : 4) + 16, "CSR offsets");
   if (st == BYO_OK) st = dev_alloc_t(&g->col, m + 4, "CSR neighbours");
-  if (st == BYO_OK) st = tmp_alloc_t(&rows, m + 1, s, "CSR rows");
   if (st == BYO_OK) {
     cudaMemsetAsync(g->col + m, 0, 16, s);
-    if (cnt) compact_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(sorted, pos, flags, cnt, lb, g->col, rows); ::byo::note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) st = cuda_status(e, "compact_kernel");
+    if (m) cudaMemcpyAsync(g->col, cols, sizeof(uint32_t) * m, cudaMemcpyDeviceToDevice, s);
+    st = g->off64 ? finish_csr<uint64_t>(g, rows, s) : finish_csr<uint32_t>(g, rows, s);
   }
-  if (st == BYO_OK) st = g->off64 ? finish_csr<uint64_t>(g, rows, s) : finish_csr<uint32_t>(g, rows, s);
+  if (st == BYO_OK && !sym && m) st = tmp_alloc_t(&bad, 1, s, "flag");
   if (st == BYO_OK && !sym && m) {
     cudaMemsetAsync(bad, 0, 4, s);
     if (g->off64)
       symmetric_kernel<uint64_t><<<grid_for(m, 256), 256, 0, s>>>(static_cast<uint64_t*>(g->off), g->col, rows, m, bad);
     else
-      symmetric_kernel<uint32_t><<<grid_for(m, 256), 256, 0, s>>>(static_cast<uint32_t*>(g->off), g->col, rows, m, bad); ::byo::note_launch();
+      symmetric_kernel<uint32_t><<<grid_for(m, 256), 256, 0, s>>>(static_cast<uint32_t*>(g->off), g->col, rows, m, bad);
+    ::byo::note_launch();
     cudaError_t e = cudaGetLastError();
     uint32_t hbad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
@@ -342,12 +334,10 @@ byo_status build_csr(byo_graph* g, const uint32_t* src, const uint32_t* dst, uin
       st = BYO_ERR_NOT_SYMMETRIC;
     }
   }
-  tmp_free(keys, s);
-  tmp_free(tmp, s);
-  tmp_free(flags, s);
   tmp_free(rows, s);
+  tmp_free(cols, s);
   tmp_free(bad, s);
-  if (st == BYO_OK) st = g->off64 ? build_buckets<uint64_t>(g, s) : build_buckets<uint32_t>(g, s);
+  if (st == BYO_OK) st = rebuild_buckets(g, s);
   if (st == BYO_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = cuda_status(e, "byo_graph_build");
@@ -356,6 +346,78 @@ byo_status build_csr(byo_graph* g, const uint32_t* src, const uint32_t* dst, uin
 }
 
 }  // namespace
+
+byo_status sort_unique_pairs(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t k, bool sym,
+                             cudaStream_t s, uint32_t** rows_out, uint32_t** cols_out, uint64_t* count) {
+  *rows_out = *cols_out = nullptr;
+  *count = 0;
+  const int lb = bits_for(n > 1 ? n : 2);
+  const uint64_t cnt = sym ? 2 * k : k;
+  uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr, *pos = nullptr;
+  uint32_t *flags = nullptr, *rows = nullptr, *cols = nullptr, *bad = nullptr;
+  byo_status st = tmp_alloc_t(&bad, 4, s, "flag");
+  if (st == BYO_OK) st = tmp_alloc_t(&keys, cnt, s, "edge keys");
+  if (st == BYO_OK) st = tmp_alloc_t(&tmp, cnt, s, "edge keys tmp");
+  if (st == BYO_OK) {
+    cudaMemsetAsync(bad, 0, 16, s);
+    if (k) {
+      make_keys_kernel<<<grid_for(k, 256), 256, 0, s>>>(src, dst, k, n, lb, sym, keys, bad);
+      ::byo::note_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    uint32_t hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "make_keys_kernel");
+    else if (hbad) {
+      set_error("a vertex id is >= n (%u)", n);
+      st = BYO_ERR_INVALID_ARG;
+    }
+  }
+  if (st == BYO_OK) st = radix_sort_u64(keys, tmp, cnt, 2 * lb, &sorted, s);
+  if (st == BYO_OK) {
+    pos = sorted == keys ? tmp : keys;  // the other key buffer holds the positions
+    st = tmp_alloc_t(&flags, cnt, s, "unique flags");
+  }
+  uint64_t m = 0;
+  if (st == BYO_OK) {
+    if (cnt) {
+      unique_flags_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(sorted, cnt, lb, flags);
+      ::byo::note_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_status(e, "unique_flags_kernel");
+  }
+  if (st == BYO_OK) st = scan_u32_to_u64(flags, pos, cnt, &m, s);
+  if (st == BYO_OK) st = tmp_alloc_t(&rows, m + 4, s, "sorted rows");
+  if (st == BYO_OK) st = tmp_alloc_t(&cols, m + 4, s, "sorted cols");
+  if (st == BYO_OK) {
+    if (cnt) {
+      compact_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(sorted, pos, flags, cnt, lb, cols, rows);
+      ::byo::note_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_status(e, "compact_kernel");
+  }
+  tmp_free(keys, s);
+  tmp_free(tmp, s);
+  tmp_free(flags, s);
+  tmp_free(bad, s);
+  if (st != BYO_OK) {
+    tmp_free(rows, s);
+    tmp_free(cols, s);
+    return st;
+  }
+  *rows_out = rows;
+  *cols_out = cols;
+  *count = m;
+  return BYO_OK;
+}
+
+byo_status rebuild_buckets(byo_graph* g, cudaStream_t s) {
+  return with_view(g, [&](auto view) { return build_buckets(g, view, s); });
+}
+
 }  // namespace byo
 
 using namespace byo;
@@ -391,10 +453,6 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
     set_error("byo_graph_build: exactly one of BYO_CSR / BYO_DYNAMIC is required");
     return BYO_ERR_INVALID_ARG;
   }
-  if (flags & BYO_DYNAMIC) {
-    set_error("byo_graph_build: the dynamic container is not available in this build");
-    return BYO_ERR_UNSUPPORTED;
-  }
   if (n == 0xFFFFFFFFu) {
     set_error("byo_graph_build: n must be < 2^32 - 1 (0xFFFFFFFF is the INF marker)");
     return BYO_ERR_INVALID_ARG;
@@ -416,6 +474,7 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
   {
     ProfScope ps("csr_build", s);
     st = build_csr(g, src, dst, k, (flags & BYO_SYMMETRIZE) != 0, s);
+    if (st == BYO_OK && (flags & BYO_DYNAMIC)) st = dyn_from_csr(g, s);
   }
   if (st != BYO_OK) {
     cudaStreamSynchronize(s);
@@ -469,12 +528,11 @@ byo_status byo_degree(const byo_graph* g, const uint32_t* vs, uint64_t k, uint32
   uint32_t* bad = nullptr;
   BYO_RETURN_IF(tmp_alloc_t(&bad, 1, s, "flag"));
   cudaMemsetAsync(bad, 0, 4, s);
-  if (g->off64)
-    degree_kernel<uint64_t><<<grid_for(k, 256), 256, 0, s>>>(
-        CsrView<uint64_t>{g->n, g->m, static_cast<const uint64_t*>(g->off), g->col}, vs, k, out, bad);
-  else
-    degree_kernel<uint32_t><<<grid_for(k, 256), 256, 0, s>>>(
-        CsrView<uint32_t>{g->n, g->m, static_cast<const uint32_t*>(g->off), g->col}, vs, k, out, bad); ::byo::note_launch();
+  with_view(g, [&](auto view) {
+    degree_kernel<<<grid_for(k, 256), 256, 0, s>>>(view, vs, k, out, bad);
+    return BYO_OK;
+  });
+  ::byo::note_launch();
   cudaError_t e = cudaGetLastError();
   uint32_t hbad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
@@ -496,14 +554,27 @@ byo_status byo_graph_export_csr(const byo_graph* g, uint64_t* offsets, uint32_t*
     return BYO_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (g->off64)
-    export_off_kernel<uint64_t><<<grid_for(g->n + 1ull, 256), 256, 0, s>>>(static_cast<const uint64_t*>(g->off), g->n,
-                                                                           offsets);
-  else
-    export_off_kernel<uint32_t><<<grid_for(g->n + 1ull, 256), 256, 0, s>>>(static_cast<const uint32_t*>(g->off), g->n,
-                                                                           offsets); ::byo::note_launch();
-  BYO_CHECK_LAUNCH("export_off_kernel");
-  if (g->m) BYO_CUDA(cudaMemcpyAsync(col, g->col, sizeof(uint32_t) * g->m, cudaMemcpyDeviceToDevice, s));
+  // offsets = exclusive scan of the degrees, then one warp per vertex copies its list
+  uint32_t* deg = nullptr;
+  BYO_RETURN_IF(tmp_alloc_t(&deg, g->n + 1ull, s, "export degrees"));
+  byo_status st = with_view(g, [&](auto view) {
+    degrees_kernel<<<grid_for(g->n, 256), 256, 0, s>>>(view, deg);
+    ::byo::note_launch();
+    return BYO_OK;
+  });
+  if (st == BYO_OK) st = scan_u32_to_u64(deg, offsets, g->n, nullptr, s);
+  if (st == BYO_OK) {
+    set_last_u64_kernel<<<1, 1, 0, s>>>(offsets, g->n, g->m);
+    ::byo::note_launch();
+    st = with_view(g, [&](auto view) {
+      export_col_kernel<<<grid_for((uint64_t)g->n * 32, 256), 256, 0, s>>>(view, offsets, col);
+      ::byo::note_launch();
+      return BYO_OK;
+    });
+  }
+  tmp_free(deg, s);
+  BYO_RETURN_IF(st);
+  BYO_CHECK_LAUNCH("byo_graph_export_csr");
   return BYO_OK;
 }
 

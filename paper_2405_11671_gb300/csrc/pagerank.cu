@@ -18,6 +18,10 @@ namespace byo {
 
 struct PrWork {
   uint32_t n = 0;
+  float2* part = nullptr;      // per hub chunk: compensated partial (sum, error)
+  uint64_t part_cap = 0;
+  uint32_t* hub_ticket = nullptr;  // per hub: chunks finished this iteration
+  uint64_t ticket_cap = 0;
   float* c[2] = {nullptr, nullptr};
   double* partials = nullptr;  // 2 per block
   uint32_t max_blocks = 0;
@@ -29,6 +33,8 @@ void pr_free(PrWork* w) {
   if (!w) return;
   dev_free(w->c[0]);
   dev_free(w->c[1]);
+  dev_free(w->part);
+  dev_free(w->hub_ticket);
   dev_free(w->partials);
   dev_free(w->scal);
   dev_free(w->ticket);
@@ -138,10 +144,93 @@ __device__ __forceinline__ void pr_store(G& g, uint32_t v, uint32_t deg, Comp ac
   if (deg == 0) dang += (double)pn;
 }
 
+// Compensated sum of c[ids[k]] for k = first, first+stride, ... < len, with
+// eight independent id loads and eight independent gathers in flight per step.
+__device__ __forceinline__ void gather_sum(Comp& acc, const uint32_t* __restrict__ ids, uint32_t first, uint32_t len,
+                                           uint32_t stride, const float* __restrict__ c) {
+  uint32_t k = first;
+  for (; k + 7 * stride < len; k += 8 * stride) {
+    uint32_t u[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) u[j] = __ldg(ids + k + j * stride);
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = __ldg(c + u[j]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) neumaier_add(acc, x[j]);
+  }
+  for (; k < len; k += stride) neumaier_add(acc, __ldg(c + __ldg(ids + k)));
+}
+
+// Low-degree vertices (degree < small_lim) are processed in id order, 32 per
+// warp: the warp walks the concatenation of their neighbour lists 32 ids at a
+// time (coalesced id reads, 32 independent contribution gathers per step),
+// merges the per-lane values of each vertex with a segmented warp scan built
+// on the error-free TwoSum, and every lane keeps the compensated sum of its own
+// vertex.  Ranks and contributions of those vertices are stored coalesced.
 template <typename G>
-__global__ void __launch_bounds__(kPrThreads) pr_iter_kernel(G g, VBins bins, float damping,
-                                                             const float* __restrict__ c, float* __restrict__ cn,
-                                                             float* ranks, double* partials, double* scal,
+__device__ __forceinline__ void pr_stream_warp(const G& g, uint32_t v0, uint32_t small_lim, float damping,
+                                               float base, const float* __restrict__ c, float* __restrict__ cn,
+                                               float* ranks, double& res, double& dang) {
+  const uint32_t lane = lane_id();
+  const uint32_t n = g.num_vertices();
+  const uint32_t v = v0 + lane;
+  Seg s{nullptr, 0};
+  uint32_t deg = 0;
+  if (v < n) {
+    s = g.seg(v);
+    deg = s.len;
+  }
+  const uint32_t len = deg < small_lim ? deg : 0;
+  uint32_t incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  const uint32_t excl = incl - len;
+  Comp acc{0.f, 0.f};
+  for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+    const uint32_t e = e0 + lane;
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      int probe = owner + step;
+      uint32_t ex = __shfl_sync(0xFFFFFFFFu, excl, probe & 31);
+      if (probe < 32 && ex <= e) owner = probe;
+    }
+    const uint32_t oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
+    const uint32_t* op = reinterpret_cast<const uint32_t*>(
+        __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(s.p), owner));
+    Comp val{0.f, 0.f};
+    int key = 32;
+    if (e < total) {
+      val.s = __ldg(c + __ldg(op + (e - oex)));
+      key = owner;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      float ys = __shfl_up_sync(0xFFFFFFFFu, val.s, o);
+      float yc = __shfl_up_sync(0xFFFFFFFFu, val.c, o);
+      int yk = __shfl_up_sync(0xFFFFFFFFu, key, o);
+      if ((int)lane >= o && yk == key) val = comp_merge(Comp{ys, yc}, val);
+    }
+    // this lane's vertex: its ids in this chunk end at lane hi-1-e0
+    const uint32_t lo = excl > e0 ? excl : e0;
+    const uint32_t hi = (excl + len) < (e0 + 32) ? (excl + len) : (e0 + 32);
+    const int srcl = hi > lo ? (int)(hi - 1 - e0) : (int)lane;
+    Comp part{__shfl_sync(0xFFFFFFFFu, val.s, srcl), __shfl_sync(0xFFFFFFFFu, val.c, srcl)};
+    if (hi > lo) acc = comp_merge(acc, part);
+  }
+  if (v < n && deg < small_lim) pr_store(g, v, deg, acc, damping, base, ranks, cn, res, dang);
+}
+
+template <typename G>
+__global__ void __launch_bounds__(kPrThreads) pr_iter_kernel(G g, VBins bins, CtaChunks hubs, uint32_t small_lim,
+                                                             float damping, const float* __restrict__ c,
+                                                             float* __restrict__ cn, float* ranks, float2* part,
+                                                             uint32_t* hub_ticket, double* partials, double* scal,
                                                              uint32_t* ticket) {
   const uint32_t n = g.num_vertices();
   const float base = (float)__ldcg(scal + 2);
@@ -149,36 +238,57 @@ __global__ void __launch_bounds__(kPrThreads) pr_iter_kernel(G g, VBins bins, fl
   const uint32_t lane = lane_id();
   double res = 0.0, dang = 0.0;
   if (r.role == kRoleThread) {
-    for (uint64_t i = r.begin; i < r.end; i += r.stride) {
-      uint32_t v = __ldg(bins.vorder + i);
-      Seg s = g.seg(v);
-      Comp acc{0.f, 0.f};
-      for (uint32_t k = 0; k < s.len; ++k) neumaier_add(acc, __ldg(c + __ldg(s.p + k)));
-      pr_store(g, v, s.len, acc, damping, base, ranks, cn, res, dang);
-    }
+    const uint32_t wpb = blockDim.x >> 5;
+    const uint64_t wt = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
+    const uint64_t nw = (uint64_t)bins.nbT * wpb;
+    for (uint64_t v0 = wt * 32; v0 < n; v0 += nw * 32)
+      pr_stream_warp(g, (uint32_t)v0, small_lim, damping, base, c, cn, ranks, res, dang);
   } else if (r.role == kRoleWarp) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
       Comp acc{0.f, 0.f};
-      for (uint32_t k = lane; k < s.len; k += 32) neumaier_add(acc, __ldg(c + __ldg(s.p + k)));
+      gather_sum(acc, s.p, lane, s.len, 32, c);
       acc = warp_comp_sum(acc);
       if (lane == 0) pr_store(g, v, s.len, acc, damping, base, ranks, cn, res, dang);
     }
   } else {
+    // high degree: chunks spread over CTAs; the last chunk of a vertex to finish
+    // folds the chunk partials in chunk order and stores the vertex
     __shared__ Comp sh[kPrThreads / 32];
-    for (uint64_t i = r.begin; i < r.end; i += r.stride) {
-      uint32_t v = __ldg(bins.vorder + i);
+    for (uint64_t j = blockIdx.x - bins.nbT - bins.nbW; j < hubs.items; j += bins.nbC) {
+      ChunkItem it = chunk_item(hubs, j);
+      uint32_t v = __ldg(bins.vorder + it.vidx);
       Seg s = g.seg(v);
+      uint32_t lo, hi;
+      chunk_range(s.len, it.chunk, it.K, &lo, &hi);
       Comp acc{0.f, 0.f};
-      for (uint32_t k = threadIdx.x; k < s.len; k += blockDim.x) neumaier_add(acc, __ldg(c + __ldg(s.p + k)));
+      gather_sum(acc, s.p, lo + threadIdx.x, hi, blockDim.x, c);
       acc = warp_comp_sum(acc);
       if (lane == 0) sh[threadIdx.x >> 5] = acc;
       __syncthreads();
       if (threadIdx.x < 32) {
         Comp a = lane < (blockDim.x >> 5) ? sh[lane] : Comp{0.f, 0.f};
         a = warp_comp_sum(a);
-        if (threadIdx.x == 0) pr_store(g, v, s.len, a, damping, base, ranks, cn, res, dang);
+        if (threadIdx.x == 0) {
+          if (it.K == 1) {
+            pr_store(g, v, s.len, a, damping, base, ranks, cn, res, dang);
+          } else {
+            part[j] = make_float2(a.s, a.c);
+            __threadfence();
+            uint32_t* t = hub_ticket + (it.vidx - hubs.vbegin);
+            if (atomicAdd(t, 1u) == it.K - 1) {
+              __threadfence();
+              Comp tot{0.f, 0.f};
+              for (uint32_t q = 0; q < it.K; ++q) {
+                float2 pq = __ldcg(part + it.first + q);
+                tot = comp_merge(tot, Comp{pq.x, pq.y});
+              }
+              pr_store(g, v, s.len, tot, damping, base, ranks, cn, res, dang);
+              *t = 0;
+            }
+          }
+        }
       }
       __syncthreads();
     }
@@ -186,8 +296,8 @@ __global__ void __launch_bounds__(kPrThreads) pr_iter_kernel(G g, VBins bins, fl
   finish_reduction(res, dang, partials, scal, ticket, damping, n);
 }
 
-byo_status ensure_pr_work(byo_graph* g, uint32_t blocks) {
-  if (g->pr && g->pr->max_blocks >= blocks) return BYO_OK;
+byo_status ensure_pr_work(byo_graph* g, uint32_t blocks, uint64_t parts, uint64_t hubs) {
+  if (g->pr && g->pr->max_blocks >= blocks && g->pr->part_cap >= parts && g->pr->ticket_cap >= hubs) return BYO_OK;
   if (g->pr) {
     pr_free(g->pr);
     g->pr = nullptr;
@@ -202,6 +312,14 @@ byo_status ensure_pr_work(byo_graph* g, uint32_t blocks) {
   byo_status st = dev_alloc_t(&w->c[0], g->n, "PageRank contributions");
   if (st == BYO_OK) st = dev_alloc_t(&w->c[1], g->n, "PageRank contributions");
   if (st == BYO_OK) st = dev_alloc_t(&w->partials, 2ull * blocks, "PageRank partials");
+  w->part_cap = parts + 64;
+  w->ticket_cap = hubs + 64;
+  if (st == BYO_OK) st = dev_alloc_t(&w->part, w->part_cap, "PageRank hub partials");
+  if (st == BYO_OK) st = dev_alloc_t(&w->hub_ticket, w->ticket_cap, "PageRank hub tickets");
+  if (st == BYO_OK) {
+    cudaError_t e = cudaMemset(w->hub_ticket, 0, sizeof(uint32_t) * w->ticket_cap);
+    if (e != cudaSuccess) st = cuda_status(e, "cudaMemset");
+  }
   if (st == BYO_OK) st = dev_alloc_t(&w->scal, 4, "PageRank scalars");
   if (st == BYO_OK) st = dev_alloc_t(&w->ticket, 1, "PageRank ticket");
   if (st == BYO_OK) {
@@ -216,14 +334,25 @@ byo_status ensure_pr_work(byo_graph* g, uint32_t blocks) {
   return BYO_OK;
 }
 
-template <typename OffT>
-byo_status run_pr(byo_graph* g, float damping, uint32_t iters, float* ranks, double* host_residual,
+template <typename G>
+byo_status run_pr(byo_graph* g, G view, float damping, uint32_t iters, float* ranks, double* host_residual,
                   cudaStream_t s) {
-  CsrView<OffT> view{g->n, g->m, static_cast<const OffT*>(g->off), g->col};
-  VBins bins = make_vbins(g, 4, 10, kPrThreads);
+  constexpr int kSmallBucket = 5;  // degree < 32 goes to the id-ordered warp stream
+  VBins bins = make_vbins(g, kSmallBucket, 10, kPrThreads);
+  {
+    // the stream walks every id: size its blocks by n, not by the small-vertex count
+    uint64_t want = ((uint64_t)g->n + 32ull * (kPrThreads / 32) - 1) / (32ull * (kPrThreads / 32));
+    uint64_t cap = (uint64_t)sm_count() * 8;
+    bins.nbT = (uint32_t)(want < cap ? (want ? want : 1) : cap);
+  }
+  CtaChunks hubs = make_cta_chunks(g, 11, 11);  // degrees >= 1024, chunks of <= 2048 ids
+  {
+    uint64_t cap = (uint64_t)sm_count() * 8;
+    bins.nbC = (uint32_t)(hubs.items < cap ? hubs.items : cap);
+  }
   uint32_t grid = vbins_grid(bins);
   uint32_t init_grid = (uint32_t)sm_count() * 4;
-  BYO_RETURN_IF(ensure_pr_work(g, grid > init_grid ? grid : init_grid));
+  BYO_RETURN_IF(ensure_pr_work(g, grid > init_grid ? grid : init_grid, hubs.items, hubs.vcount));
   PrWork* w = g->pr;
   {
     ProfScope ps("pr_init", s);
@@ -232,8 +361,10 @@ byo_status run_pr(byo_graph* g, float damping, uint32_t iters, float* ranks, dou
   BYO_CHECK_LAUNCH("pr_init_kernel");
   for (uint32_t t = 0; t < iters; ++t) {
     ProfScope ps("pr_iter", s);
-    pr_iter_kernel<<<grid, kPrThreads, 0, s>>>(view, bins, damping, w->c[t & 1], w->c[(t + 1) & 1], ranks,
-                                               w->partials, w->scal, w->ticket); ::byo::note_launch();
+    pr_iter_kernel<<<grid, kPrThreads, 0, s>>>(view, bins, hubs, 1u << kSmallBucket, damping, w->c[t & 1],
+                                               w->c[(t + 1) & 1], ranks, w->part, w->hub_ticket, w->partials,
+                                               w->scal, w->ticket);
+    ::byo::note_launch();
     BYO_CHECK_LAUNCH("pr_iter_kernel");
   }
   if (host_residual) {
@@ -268,6 +399,5 @@ extern "C" byo_status byo_pagerank(const byo_graph* gc, float damping, uint32_t 
     return BYO_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return g->off64 ? run_pr<uint64_t>(g, damping, iters, ranks, host_residual, s)
-                  : run_pr<uint32_t>(g, damping, iters, ranks, host_residual, s);
+  return with_view(g, [&](auto view) { return run_pr(g, view, damping, iters, ranks, host_residual, s); });
 }

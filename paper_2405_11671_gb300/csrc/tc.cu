@@ -7,9 +7,10 @@
 // |N+(u) intersect N+(v)|.  For every u, N+(u) is staged in shared memory by a
 // TMA bulk copy (cp.async.bulk, completion on an mbarrier; no multicast), then
 // the ids of N+(v) for all v in N+(u) are walked 32 at a time by a warp
-// (edge-balanced across the warp) and looked up by binary search in shared
-// memory.  u with |N+(u)| <= kLightMax: one warp each (a private smem slice);
-// larger u: one CTA each, N+(u) staged in windows of kWindow ids.
+// (edge-balanced across the warp) and looked up in shared memory.  u with |N+(u)| <= kLightMax: one warp each; the staged N+(u) is
+// loaded into an open-addressing hash set in the warp's shared memory and each
+// id of N+(v) costs one or two probes.  Larger u: one CTA each, N+(u) staged
+// in windows of kWindow ids and searched by bisection.
 #include <stdlib.h>
 
 #include "byo_internal.cuh"
@@ -19,7 +20,7 @@
 
 namespace byo {
 
-constexpr uint32_t kLightMax = 1024;  // capacity of a warp's shared-memory slice (ids)
+constexpr uint32_t kLightMax = 256;   // capacity of a warp's shared-memory slice (ids)
 constexpr uint32_t kWindow = 16384;   // capacity of a CTA's shared-memory window (ids)
 constexpr int kTcThreads = 256;
 
@@ -36,6 +37,7 @@ static uint32_t env_cap(const char* name, uint32_t cap) {
 
 struct TcWork {
   uint32_t n = 0;
+  uint64_t half_cap = 0;        // capacity of dag_col (undirected edges)
   uint64_t* dag_off = nullptr;  // n + 1
   uint32_t* dag_col = nullptr;  // m/2 + 8
   uint32_t* outdeg = nullptr;   // n
@@ -239,13 +241,34 @@ __device__ __forceinline__ bool smem_contains(const uint32_t* a, uint32_t len, u
   return lo < len && a[lo] == x;
 }
 
-// The warp walks the concatenation of N+(v) for the 32 (or fewer) v of
-// vs[0..cnt) and counts the ids found in the sorted window a[0..alen) that lie
-// in [lo_id, hi_id].
+// Open-addressing hash set in shared memory (linear probing, empty = INF,
+// multiplicative hashing); the table has at least twice as many slots as keys.
+struct SmemHash {
+  const uint32_t* t;
+  uint32_t mask, shift;
+  __device__ __forceinline__ bool contains(uint32_t x) const {
+    uint32_t h = (x * 0x9E3779B1u) >> shift;
+    while (true) {
+      uint32_t y = t[h];
+      if (y == x) return true;
+      if (y == kInf) return false;
+      h = (h + 1) & mask;
+    }
+  }
+};
+
+struct SmemSorted {
+  const uint32_t* a;
+  uint32_t len;
+  __device__ __forceinline__ bool contains(uint32_t x) const { return smem_contains(a, len, x); }
+};
+
+// The warp walks the concatenation of N+(v) for the 32 (or fewer) v held by
+// its lanes and counts the ids w in [lo_id, hi_id] that the set contains.
+template <typename Set>
 __device__ __forceinline__ uint64_t warp_count_group(const uint64_t* __restrict__ dag_off,
                                                      const uint32_t* __restrict__ dag_col, uint32_t v, bool has_v,
-                                                     const uint32_t* a, uint32_t alen, uint32_t lo_id,
-                                                     uint32_t hi_id) {
+                                                     const Set& set, uint32_t lo_id, uint32_t hi_id) {
   const uint32_t lane = lane_id();
   uint64_t vb = 0;
   uint32_t len = 0;
@@ -275,20 +298,25 @@ __device__ __forceinline__ uint64_t warp_count_group(const uint64_t* __restrict_
     uint64_t ob = __shfl_sync(0xFFFFFFFFu, vb, owner);
     if (e < total) {
       uint32_t w = __ldg(dag_col + ob + (e - oex));
-      if (w >= lo_id && w <= hi_id && smem_contains(a, alen, w)) ++hits;
+      if (w >= lo_id && w <= hi_id && set.contains(w)) ++hits;
     }
   }
   return hits;
 }
 
+constexpr uint32_t kSlice = kLightMax + 8;  // staged N+(u) (+ alignment slack), ids
+constexpr uint32_t kTable = 2 * kLightMax;   // hash slots per warp
+constexpr size_t kLightSmem = (size_t)(kTcThreads / 32) * (kSlice + kTable) * sizeof(uint32_t);
+
 __global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __restrict__ dag_off,
                                                               const uint32_t* __restrict__ dag_col,
                                                               const uint32_t* __restrict__ light, uint32_t* ctr,
                                                               unsigned long long* count, uint64_t limit_ns) {
-  constexpr uint32_t kSlice = kLightMax + 8;
-  __shared__ __align__(16) uint32_t buf[kTcThreads / 32][kSlice];
+  extern __shared__ __align__(16) uint32_t smem[];
   __shared__ __align__(8) uint64_t bar[kTcThreads / 32];
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  uint32_t* buf = smem + (size_t)w * (kSlice + kTable);
+  uint32_t* table = buf + kSlice;
   const uint32_t nlight = __ldcg(ctr + 0);
   uint32_t* err = ctr + 3;
   if (lane == 0) mbar_init(&bar[w], 1);
@@ -304,21 +332,35 @@ __global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __
     uint64_t beg = dag_off[u], end = dag_off[u + 1];
     uint64_t a0 = beg & ~3ull, a1 = (end + 3) & ~3ull;
     uint32_t head = (uint32_t)(beg - a0), len = (uint32_t)(end - beg);
-    __syncwarp();
+    __syncwarp();  // every lane is done with the previous u's slice and table
     bool ok = true;
     if (lane == 0) {
-      bulk_load(&buf[w][0], dag_col + a0, (uint32_t)((a1 - a0) * 4), &bar[w]);
+      bulk_load(buf, dag_col + a0, (uint32_t)((a1 - a0) * 4), &bar[w]);
       ok = mbar_wait(&bar[w], phase, err, limit_ns);
     }
     if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) return;
     mbar_wait(&bar[w], phase, err, limit_ns);  // completed: every lane observes the phase
     phase ^= 1;
-    const uint32_t* list = &buf[w][head];
+    const uint32_t* list = buf + head;
+    // hash set of N+(u): 2^b >= 2 len slots
+    uint32_t bits = 32 - __clz(2 * len - 1);
+    if (bits < 5) bits = 5;
+    const uint32_t slots = 1u << bits;
+    for (uint32_t i = lane; i < slots; i += 32) table[i] = kInf;
+    __syncwarp();
+    for (uint32_t k = lane; k < len; k += 32) {
+      uint32_t x = list[k];
+      uint32_t h = (x * 0x9E3779B1u) >> (32 - bits);
+      while (atomicCAS(table + h, kInf, x) != kInf) h = (h + 1) & (slots - 1);
+    }
+    __syncwarp();
+    SmemHash set{table, slots - 1, 32 - bits};
+    const uint32_t lo_id = list[0], hi_id = list[len - 1];
     for (uint32_t k0 = 0; k0 < len; k0 += 32) {
       uint32_t k = k0 + lane;
       bool has = k < len;
       uint32_t v = has ? list[k] : 0;
-      hits += warp_count_group(dag_off, dag_col, v, has, list, len, 0u, 0xFFFFFFFFu);
+      hits += warp_count_group(dag_off, dag_col, v, has, set, lo_id, hi_id);
     }
   }
   uint64_t t = hits;
@@ -364,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __
         uint64_t k = k0 + lane;
         bool has = k < end;
         uint32_t v = has ? __ldg(dag_col + k) : 0;
-        hits += warp_count_group(dag_off, dag_col, v, has, list, wlen, lo_id, hi_id);
+        hits += warp_count_group(dag_off, dag_col, v, has, SmemSorted{list, wlen}, lo_id, hi_id);
       }
     }
   }
@@ -375,22 +417,27 @@ __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __
 }
 
 byo_status ensure_tc_work(byo_graph* g) {
-  if (g->tc) return BYO_OK;
+  if (g->tc && g->tc->half_cap >= g->m / 2) return BYO_OK;
+  if (g->tc) {  // the dynamic container grew
+    tc_free(g->tc);
+    g->tc = nullptr;
+  }
   TcWork* w = new (std::nothrow) TcWork();
   if (!w) {
     set_error("host allocation failed");
     return BYO_ERR_OUT_OF_MEMORY;
   }
   w->n = g->n;
+  w->half_cap = g->m / 2 + (g->dyn ? g->m / 8 : 0);  // headroom for later inserts
   byo_status st = dev_alloc_t(&w->dag_off, g->n + 1ull, "TC DAG offsets");
-  if (st == BYO_OK) st = dev_alloc_t(&w->dag_col, g->m / 2 + 8, "TC DAG neighbours");
+  if (st == BYO_OK) st = dev_alloc_t(&w->dag_col, w->half_cap + 8, "TC DAG neighbours");
   if (st == BYO_OK) st = dev_alloc_t(&w->outdeg, g->n, "TC out-degrees");
   if (st == BYO_OK) st = dev_alloc_t(&w->light, g->n, "TC light list");
   if (st == BYO_OK) st = dev_alloc_t(&w->heavy, g->n, "TC heavy list");
   if (st == BYO_OK) st = dev_alloc_t(&w->ctr, 4, "TC counters");
   if (st == BYO_OK) st = dev_alloc_t(&w->count, 1, "TC count");
   if (st == BYO_OK) {
-    cudaError_t e = cudaMemset(w->dag_col, 0, sizeof(uint32_t) * (g->m / 2 + 8));
+    cudaError_t e = cudaMemset(w->dag_col, 0, sizeof(uint32_t) * (w->half_cap + 8));
     if (e != cudaSuccess) st = cuda_status(e, "cudaMemset");
   }
   if (st != BYO_OK) {
@@ -401,11 +448,10 @@ byo_status ensure_tc_work(byo_graph* g) {
   return BYO_OK;
 }
 
-template <typename OffT>
-byo_status run_tc(byo_graph* g, uint64_t* host_count, cudaStream_t s) {
+template <typename G>
+byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, cudaStream_t s) {
   BYO_RETURN_IF(ensure_tc_work(g));
   TcWork* w = g->tc;
-  CsrView<OffT> view{g->n, g->m, static_cast<const OffT*>(g->off), g->col};
   VBins bins = make_vbins(g, 4, 10, kTcThreads);
   {
     ProfScope ps("tc_outdeg", s);
@@ -428,10 +474,11 @@ byo_status run_tc(byo_graph* g, uint64_t* host_count, cudaStream_t s) {
   BYO_CHECK_LAUNCH("tc_classify_kernel");
   uint64_t limit = timeout_ns();
   int per_sm = 0;
-  BYO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_light_kernel, kTcThreads, 0));
+  BYO_CUDA(cudaFuncSetAttribute(tc_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLightSmem));
+  BYO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_light_kernel, kTcThreads, kLightSmem));
   {
     ProfScope ps("tc_light", s);
-    tc_light_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, 0, s>>>(
+    tc_light_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kLightSmem, s>>>(
       w->dag_off, w->dag_col, w->light, w->ctr, w->count, limit); ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_light_kernel");
@@ -473,5 +520,5 @@ extern "C" byo_status byo_tc(const byo_graph* gc, uint64_t* host_count, void* st
   *host_count = 0;
   if (g->n == 0 || g->m == 0) return BYO_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return g->off64 ? run_tc<uint64_t>(g, host_count, s) : run_tc<uint32_t>(g, host_count, s);
+  return with_view(g, [&](auto view) { return run_tc(g, view, host_count, s); });
 }

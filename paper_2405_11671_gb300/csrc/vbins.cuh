@@ -70,3 +70,69 @@ __device__ __forceinline__ VRange vbins_range(const VBins& b) {
 }
 
 }  // namespace byo
+
+namespace byo {
+
+// The CTA bin split into chunks of at most 2^chunk_log neighbours, so that a
+// hub's neighbour list is spread over many CTAs instead of one.  Vertices of
+// bucket b (degrees < 2^b) get K_b = max(1, 2^(b - chunk_log)) work items each.
+struct CtaChunks {
+  int b0;                        // first bucket of the CTA bin
+  uint32_t chunk_log;
+  uint64_t pre[kBuckets + 1];    // work-item prefix over buckets (0 below b0)
+  uint64_t vstart[kBuckets + 1]; // vorder index where each bucket starts
+  uint64_t items;                // total work items
+  uint64_t vbegin;               // vorder index of the first CTA-bin vertex
+  uint64_t vcount;               // CTA-bin vertices
+};
+
+inline CtaChunks make_cta_chunks(const byo_graph* g, int b0, uint32_t chunk_log) {
+  CtaChunks c;
+  c.b0 = b0;
+  c.chunk_log = chunk_log;
+  c.pre[0] = 0;
+  for (int b = 0; b < kBuckets; ++b) {
+    uint64_t cnt = b >= b0 ? g->bstart[b + 1] - g->bstart[b] : 0;
+    uint64_t K = (uint32_t)b > chunk_log ? (1ull << (b - chunk_log)) : 1ull;
+    c.pre[b + 1] = c.pre[b] + cnt * K;
+  }
+  for (int b = 0; b <= kBuckets; ++b) c.vstart[b] = g->bstart[b];
+  c.items = c.pre[kBuckets];
+  c.vbegin = g->bstart[b0];
+  c.vcount = g->n - g->bstart[b0];
+  return c;
+}
+
+struct ChunkItem {
+  uint64_t vidx;   // vorder index of the vertex
+  uint64_t first;  // first work item of this vertex
+  uint32_t chunk, K;
+};
+
+__device__ __forceinline__ ChunkItem chunk_item(const CtaChunks& c, uint64_t j) {
+  int lo = c.b0, hi = kBuckets - 1;
+  while (lo < hi) {  // largest b with pre[b] <= j
+    int mid = (lo + hi + 1) >> 1;
+    if (c.pre[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  const int b = lo;
+  const uint64_t K = (uint32_t)b > c.chunk_log ? (1ull << (b - c.chunk_log)) : 1ull;
+  const uint64_t r = j - c.pre[b];
+  ChunkItem it;
+  it.vidx = c.vstart[b] + r / K;
+  it.first = c.pre[b] + (r / K) * K;
+  it.chunk = (uint32_t)(r % K);
+  it.K = (uint32_t)K;
+  return it;
+}
+
+// [lo, hi) of a vertex's neighbour list covered by one chunk
+__device__ __forceinline__ void chunk_range(uint32_t len, uint32_t chunk, uint32_t K, uint32_t* lo, uint32_t* hi) {
+  uint32_t per = (len + K - 1) / K;
+  uint32_t a = chunk * per;
+  *lo = a < len ? a : len;
+  *hi = a + per < len ? a + per : len;
+}
+
+}  // namespace byo

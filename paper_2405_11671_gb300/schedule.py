@@ -1,0 +1,193 @@
+"""Learned edgeMap schedule: training data, training and evaluation.
+
+The schedule network (``csrc/mlp.cu``, ``csrc/sched.cuh``) picks, for every BFS
+iteration, one of four result-identical actions from 12 frontier features:
+
+====== =========================================================
+action meaning
+====== =========================================================
+0      dense edgeMap (pull) over the frontier bit array
+1      sparse edgeMap (push), bins thread < 16, warp < 1024
+2      push, bins thread < 4, warp < 128
+3      push, bins thread < 64, warp < 4096
+====== =========================================================
+
+Training data are timings the engine records itself: every training graph is
+traversed once per action with that action forced at every level, and the
+per-iteration device times (``byo_bfs_trace``) give, for each level, the time
+of each action on the same frontier (BFS frontiers do not depend on the
+schedule).  A sample's label is the fastest action and its weight is the time
+the worst choice would lose, relative to the traversal's best total.  The
+network is trained by the library's own forward/backward/Adam kernels.
+
+``python -m paper_2405_11671_gb300.schedule train --out sched_mlp.json`` builds
+the training set from generated graphs (ER, RMAT, grids) and writes the FP32
+parameters that ``--sched learned`` loads.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+
+import numpy as np
+
+NUM_ACTIONS = 4
+NUM_FEATURES = 12
+# (mode, thr_thread, thr_warp) that force each action at every iteration
+FORCED = {0: ("pull", 16, 1024), 1: ("push", 16, 1024), 2: ("push", 4, 128), 3: ("push", 64, 4096)}
+DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "sched_mlp.json")
+
+
+def feature_vector(nf, mf, nu, mu, n, m, hist) -> np.ndarray:
+    """The 12 network inputs of one iteration; the same formula as the device
+    function that feeds the network inside the BFS loop."""
+    x = np.zeros(NUM_FEATURES, np.float32)
+    f = np.float32
+    x[0] = math.log2(1.0 + nf) / 32.0
+    x[1] = math.log2(1.0 + mf) / 40.0
+    x[2] = math.log2(1.0 + nu) / 32.0
+    x[3] = math.log2(1.0 + mu) / 40.0
+    x[4] = math.log2(1.0 + n) / 32.0
+    x[5] = math.log2(1.0 + m) / 40.0
+    x[6] = f(nf) / f(n if n else 1)
+    x[7] = mf / (mf + mu + 1.0)
+    inv = 1.0 / (nf if nf else 1)
+    for k in range(4):
+        x[8 + k] = hist[k] * inv
+    return x
+
+
+def trace_features(trace, n: int, m: int) -> np.ndarray:
+    return np.stack([feature_vector(r.frontier, r.frontier_edges, r.unvisited, r.unvisited_edges, n, m, list(r.hist))
+                     for r in trace]) if trace else np.zeros((0, NUM_FEATURES), np.float32)
+
+
+def forced_sched(byo, action: int):
+    mode, tt, tw = FORCED[action]
+    return byo.make_sched(byo.BYO_SCHED_PULL if mode == "pull" else byo.BYO_SCHED_PUSH, tt, tw)
+
+
+def time_actions(byo, g, sources, repeats: int = 2):
+    """Per-iteration device times of every forced action for each source.
+
+    Returns a list of (features [L, 12], times [L, NUM_ACTIONS] in ns)."""
+    n, m = byo.byo_num_vertices(g), byo.byo_num_edges(g)
+    out = []
+    for s in sources:
+        feats, times = None, []
+        for a in range(NUM_ACTIONS):
+            sp = forced_sched(byo, a)
+            best = None
+            for _ in range(repeats):
+                byo.byo_bfs(g, [int(s)], sched=sp, want_parents=False)
+                tr = byo.byo_bfs_trace(g)
+                t = np.array([r.t_ns for r in tr], np.float64)
+                best = t if best is None else np.minimum(best, t)
+                if feats is None:
+                    feats = trace_features(tr, n, m)
+            times.append(best)
+        out.append((feats, np.stack(times, axis=1)))
+    return out
+
+
+def samples_from_timings(tables):
+    """Labels = fastest action per iteration; weight = worst-case loss of that
+    iteration relative to the traversal's best total time."""
+    X, y, w = [], [], []
+    for feats, t in tables:
+        if len(t) == 0:
+            continue
+        best_total = float(t.min(axis=1).sum()) or 1.0
+        for i in range(len(t)):
+            X.append(feats[i])
+            y.append(int(np.argmin(t[i])))
+            w.append(float((t[i].max() - t[i].min()) / best_total) + 1e-3)
+    return (np.array(X, np.float32).reshape(-1, NUM_FEATURES), np.array(y, np.int32), np.array(w, np.float32))
+
+
+def regret(t, choices) -> float:
+    """Extra device time (ns) of per-iteration choices over the per-iteration best."""
+    t = np.asarray(t)
+    return float(sum(t[i, c] - t[i].min() for i, c in enumerate(choices)))
+
+
+def training_graphs(seed: int = 0xB10 + 50):
+    """Generated graphs of the three shapes at several sizes (never the benchmark graphs)."""
+    import graphgen
+    out = []
+    for sc in (14, 16, 18, 19):
+        out.append(("rmat%d" % sc, *graphgen.rmat_small(sc, 16, graphgen.stream(seed, sc))))
+    for sc, deg in ((15, 8), (17, 16), (18, 32)):
+        n = 1 << sc
+        out.append(("er%d" % sc, n, *graphgen.er(n, n * deg // 2, graphgen.stream(seed, 100 + sc))))
+    for side in (256, 512, 1024):
+        out.append(("grid%d" % side, *graphgen.grid_small(side, side, 0.1, 1e-4, graphgen.stream(seed, side))))
+    return out
+
+
+def build_training_set(byo, graphs, sources_per_graph: int = 3):
+    import torch
+
+    import graphgen
+    tables = []
+    for name, n, src, dst in graphs:
+        sd = torch.from_numpy(np.ascontiguousarray(src, np.uint32).view(np.int32)).cuda()
+        dd = torch.from_numpy(np.ascontiguousarray(dst, np.uint32).view(np.int32)).cuda()
+        with byo.Graph(n, sd, dd) as g:
+            srcs = graphgen.pick_sources(n, src, dst, sources_per_graph, 17)
+            tables += time_actions(byo, g.handle, srcs)
+    return tables
+
+
+def train(byo, X, y, w, seed: int = 1, epochs: int = 3000, lr: float = 3e-3):
+    import torch
+    m = byo.byo_mlp_create(seed)
+    loss = byo.byo_mlp_train(m, torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(w).cuda(),
+                             epochs=epochs, lr=lr)
+    return m, loss
+
+
+def save(byo, m, path: str, meta: dict | None = None):
+    params = byo.byo_mlp_get_params(m)
+    with open(path, "w") as f:
+        json.dump({"features": NUM_FEATURES, "hidden": [32, 32], "actions": NUM_ACTIONS,
+                   "params": [float(v) for v in params], "meta": meta or {}}, f)
+
+
+def load(byo, path: str = DEFAULT_PATH):
+    with open(path) as f:
+        d = json.load(f)
+    m = byo.byo_mlp_create(0)
+    byo.byo_mlp_set_params(m, np.array(d["params"], np.float32))
+    return m
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["train"])
+    ap.add_argument("--out", default=DEFAULT_PATH)
+    ap.add_argument("--epochs", type=int, default=3000)
+    args = ap.parse_args(argv)
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import paper_2405_11671_gb300 as byo
+    from paper_2405_11671_gb300 import build
+    build.build()
+    byo.load()
+    tables = build_training_set(byo, training_graphs())
+    X, y, w = samples_from_timings(tables)
+    m, loss = train(byo, X, y, w, epochs=args.epochs)
+    import torch
+    pred = byo.byo_mlp_predict(m, torch.from_numpy(X).cuda()).cpu().numpy()
+    r_learned = sum(regret(t, pred[o:o + len(t)]) for o, (_, t) in zip(np.cumsum([0] + [len(t) for _, t in tables]),
+                                                                     tables))
+    save(byo, m, args.out, {"samples": int(len(y)), "loss": loss, "train_regret_ns": r_learned,
+                             "label_counts": np.bincount(y, minlength=NUM_ACTIONS).tolist()})
+    print(json.dumps({"samples": int(len(y)), "loss": loss, "train_regret_ns": r_learned,
+                      "label_counts": np.bincount(y, minlength=NUM_ACTIONS).tolist(), "out": args.out}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+"""The dynamic blocked-adjacency container against the oracle's edge set.
+
+After every batch the container's contents (exported as CSR), m and the
+degrees must equal the oracle's bit for bit; after every round BFS levels
+(and parent validity), CC labels, triangle counts and PageRank (stated
+tolerance) computed over the dynamic container must match the oracle run on
+the oracle's own edge set.  Batches follow the dynamic-container workload:
+RMAT-distributed inserts and deletes of uniformly drawn earlier pairs, plus
+self-loops, duplicates and absent pairs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def byo():
+    from paper_2405_11671_gb300 import build
+    build.build()
+    import paper_2405_11671_gb300 as b
+    b.load()
+    return b
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def same_contents(byo, g, ref):
+    off, col = byo.byo_graph_export_csr(g.handle)
+    assert g.m == ref.m
+    assert np.array_equal(off.cpu().numpy().astype(np.uint64), ref.off)
+    assert np.array_equal(host(col), ref.col)
+    assert np.array_equal(host(byo.byo_degree(g.handle)).astype(np.uint64), np.diff(ref.off))
+
+
+def algorithms_match(byo, g, ref, sources):
+    lv, par = byo.byo_bfs(g.handle, sources)
+    for i, s in enumerate(sources):
+        want, _ = oracle.bfs(ref, s)
+        assert np.array_equal(host(lv[i]), want)
+        assert oracle.bfs_check_parents(ref, s, host(lv[i]), host(par[i])) == -1
+    assert np.array_equal(host(byo.byo_cc(g.handle)), oracle.cc(ref))
+    assert byo.byo_tc(g.handle) == oracle.tc(ref)
+    p, _ = byo.byo_pagerank(g.handle, 0.85, 20)
+    w, _ = oracle.pagerank(ref, 0.85, 20)
+    got = p.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - w) / w) <= 1e-5 and np.sum(np.abs(got - w)) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["tiny", "rmat12", "grid"])
+def test_dynamic_build_equals_csr(byo, name):
+    if name == "tiny":
+        n, src, dst = graphgen.workload("tiny")
+    elif name == "rmat12":
+        n, src, dst = graphgen.rmat_small(12, 16, 5)
+    else:
+        n, src, dst = graphgen.grid_small(50, 60, 0.1, 1e-3, 3)
+    ref = oracle.csr_build(n, src, dst)
+    g = byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    same_contents(byo, g, ref)
+    algorithms_match(byo, g, ref, [0] + graphgen.pick_sources(n, src, dst, 1, 3).tolist())
+    g.close()
+
+
+def test_dynamic_rounds_match_oracle(byo):
+    scale, seed = 13, 0xB14
+    n, src, dst = graphgen.rmat_small(scale, 8, seed)
+    g = byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    dg = oracle.DynGraph(n, src, dst)
+    pool_s, pool_d = [src], [dst]
+    for r in range(5):
+        ins_s, ins_d = graphgen.rmat(scale, 4000, graphgen.stream(seed, 100 + r))
+        # add self-loops and duplicates on purpose
+        ins_s = np.concatenate([ins_s, ins_s[:50], np.arange(10, dtype=np.uint32)])
+        ins_d = np.concatenate([ins_d, ins_d[:50], np.arange(10, dtype=np.uint32)])
+        byo.byo_insert_batch(g.handle, dev(ins_s), dev(ins_d))
+        dg.insert(ins_s, ins_d)
+        same_contents(byo, g, dg.csr())
+        pool_s.append(ins_s)
+        pool_d.append(ins_d)
+        ps, pd = np.concatenate(pool_s), np.concatenate(pool_d)
+        pick = graphgen.pick_indices(len(ps), 4000, graphgen.stream(seed, 200 + r))
+        del_s, del_d = ps[pick], pd[pick]
+        # absent pairs and reversed pairs too
+        del_s = np.concatenate([del_s, np.array([1, 2, 3], np.uint32), del_d[:20]])
+        del_d = np.concatenate([del_d, np.array([1, 5, 7], np.uint32), del_s[:20]])
+        byo.byo_delete_batch(g.handle, dev(del_s), dev(del_d))
+        dg.delete(del_s, del_d)
+        ref = dg.csr()
+        same_contents(byo, g, ref)
+        algorithms_match(byo, g, ref, graphgen.pick_sources(n, ps, pd, 2, r).tolist())
+    g.close()
+
+
+def test_hub_grows_through_classes_and_shrinks(byo):
+    n = 20000
+    g = byo.Graph(n, dev([1]), dev([2]), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    dg = oracle.DynGraph(n, [1], [2])
+    for hi in (5, 11, 12, 13, 40, 700, 5000, 19999):  # inline -> runs of growing class
+        leaves = np.arange(3, hi + 3, dtype=np.uint32) % n
+        hub = np.zeros(len(leaves), np.uint32)
+        byo.byo_insert_batch(g.handle, dev(hub), dev(leaves))
+        dg.insert(hub, leaves)
+        same_contents(byo, g, dg.csr())
+    for hi in (19999, 3000, 12, 2):  # and back down to inline
+        leaves = np.arange(hi + 3, n, dtype=np.uint32)
+        hub = np.zeros(len(leaves), np.uint32)
+        byo.byo_delete_batch(g.handle, dev(leaves), dev(hub))
+        dg.delete(leaves, hub)
+        same_contents(byo, g, dg.csr())
+    algorithms_match(byo, g, dg.csr(), [0, 1])
+    g.close()
+
+
+def test_insert_then_delete_restores(byo):
+    n, src, dst = graphgen.rmat_small(12, 8, 77)
+    g = byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    before = byo.byo_graph_export_csr(g.handle)
+    b_s, b_d = graphgen.er(n, 5000, 99)
+    base = oracle.csr_build(n, src, dst)
+    present = set(zip(np.repeat(np.arange(n), np.diff(base.off).astype(np.int64)).tolist(), base.col.tolist()))
+    keep = np.array([(a, b) not in present for a, b in zip(b_s.tolist(), b_d.tolist())])
+    b_s, b_d = b_s[keep], b_d[keep]
+    byo.byo_insert_batch(g.handle, dev(b_s), dev(b_d))
+    byo.byo_delete_batch(g.handle, dev(b_s), dev(b_d))
+    after = byo.byo_graph_export_csr(g.handle)
+    assert torch.equal(before[0], after[0]) and torch.equal(before[1], after[1])
+    g.close()
+
+
+def test_batch_errors(byo):
+    n, src, dst = graphgen.rmat_small(10, 4, 1)
+    g = byo.Graph(n, dev(src), dev(dst))
+    with pytest.raises(byo.ByoError) as e:
+        byo.byo_insert_batch(g.handle, dev([1]), dev([2]))
+    assert e.value.status == byo.BYO_ERR_UNSUPPORTED
+    g.close()
+    g = byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    with pytest.raises(byo.ByoError) as e:
+        byo.byo_insert_batch(g.handle, dev([1]), dev([n]))
+    assert e.value.status == byo.BYO_ERR_INVALID_ARG
+    byo.byo_insert_batch(g.handle, dev([]), dev([]))  # empty batch is a no-op
+    g.close()
