@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="byo", choices=["byo", "reference"])
     ap.add_argument("--workload", default="rmat25")
     ap.add_argument("--sources", type=int, default=8)
-    ap.add_argument("--sched", default="heuristic", choices=["heuristic", "push", "pull", "learned"])
+    ap.add_argument("--sched", default="heuristic", choices=["heuristic", "push", "pull", "learned", "solo"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -138,6 +138,8 @@ def ncu_traffic(kernel: str, workload: str):
 
 
 def sched_struct(byo, name, mlp=None):
+    if name == "solo":  # push by one CTA at every level
+        return byo.make_sched(byo.BYO_SCHED_FIXED, 16, 1024, 15.0, 18.0, None, 4)
     mode = {"heuristic": byo.BYO_SCHED_HEURISTIC, "push": byo.BYO_SCHED_PUSH, "pull": byo.BYO_SCHED_PULL,
             "learned": byo.BYO_SCHED_LEARNED}[name]
     return byo.make_sched(mode, 16, 1024, 15.0, 18.0, mlp)
@@ -390,7 +392,8 @@ def main():
     sched_cmp = None
     if args.schedules:
         sched_cmp = {}
-        cands = ["heuristic", "push", "pull"] + (["learned"] if load_mlp(byo) is not None else [])
+        cands = ["heuristic", "push", "pull", "solo"] + (["learned"] if os.path.exists(
+            os.path.join(ROOT, "paper_2405_11671_gb300", "sched_mlp.json")) else [])
         for name in cands:
             mm = load_mlp(byo) if name == "learned" else None
             spx = sched_struct(byo, name, mm)

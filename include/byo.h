@@ -112,8 +112,15 @@ typedef enum byo_sched_mode {
   BYO_SCHED_HEURISTIC = 0, /* Beamer-style direction switch with alpha/beta below */
   BYO_SCHED_LEARNED = 1,   /* the schedule network picks each iteration (needs mlp) */
   BYO_SCHED_PUSH = 2,      /* sparse edgeMap every iteration */
-  BYO_SCHED_PULL = 3       /* dense edgeMap every iteration */
+  BYO_SCHED_PULL = 3,      /* dense edgeMap every iteration */
+  BYO_SCHED_FIXED = 4      /* the action below at every iteration */
 } byo_sched_mode;
+
+/* Schedule actions: 0 dense (pull); 1 sparse (push) with the thr_thread /
+ * thr_warp bins below; 2 push with bins 4 / 128; 3 push with bins 64 / 4096;
+ * 4 push run by a single CTA for as many consecutive levels as the schedule
+ * keeps choosing it (no grid-wide barrier between those levels). */
+#define BYO_NUM_ACTIONS 5
 
 typedef struct byo_mlp byo_mlp;
 
@@ -124,16 +131,18 @@ typedef struct byo_sched {
   float alpha;         /* heuristic: push -> pull when frontier edges > unvisited edges / alpha */
   float beta;          /* heuristic: pull -> push when frontier vertices < n / beta */
   const byo_mlp* mlp;  /* LEARNED only */
+  uint32_t action;     /* FIXED only: 0 .. BYO_NUM_ACTIONS-1 */
 } byo_sched;
 
 /* ------------------------------------------------------------------------ */
 /* Schedule network (not in the paper: it only picks among equivalent       */
 /* execution paths, so results never depend on it).  A 12 -> 32 -> 32 -> 4  */
 /* ReLU MLP over the frontier features of one BFS iteration (the fields of   */
-/* byo_bfs_iter), outputs = scores of the 4 schedule actions.  Parameters    */
-/* are FP32, packed W1[32][12], b1[32], W2[32][32], b2[32], W3[4][32], b3[4]. */
+/* byo_bfs_iter), outputs = scores of the BYO_NUM_ACTIONS schedule actions.   */
+/* Parameters are FP32, packed W1[32][12], b1[32], W2[32][32], b2[32],        */
+/* W3[5][32], b3[5].                                                         */
 
-/* Number of FP32 parameters (1,604). */
+/* Number of FP32 parameters (1,637). */
 uint32_t byo_mlp_num_params(void);
 
 /* New network with He-uniform weights drawn from `seed` (biases zero). */
@@ -160,7 +169,7 @@ byo_status byo_mlp_train(byo_mlp* m, const float* X, const int32_t* y, const flo
 /* actions[i] = argmax of the network output for X[i] (device arrays). */
 byo_status byo_mlp_predict(const byo_mlp* m, const float* X, uint32_t B, int32_t* actions, void* stream);
 
-/* Defaults: HEURISTIC, thr_thread 16, thr_warp 1024, alpha 15, beta 18. */
+/* Defaults: HEURISTIC, thr_thread 16, thr_warp 1024, alpha 15, beta 18, action 1. */
 byo_sched byo_sched_default(void);
 
 /*
@@ -184,7 +193,7 @@ byo_status byo_bfs(const byo_graph* g, const uint32_t* host_sources, uint32_t nu
 typedef struct byo_bfs_iter {
   uint32_t level;           /* frontier level processed */
   uint32_t direction;       /* 0 = pull, 1 = push */
-  uint32_t action;          /* schedule action (0 = pull, 1..3 = push bin settings) */
+  uint32_t action;          /* schedule action (0 .. BYO_NUM_ACTIONS-1) */
   uint32_t frontier;        /* |F| */
   uint64_t frontier_edges;  /* sum of degrees over F */
   uint64_t edges_examined;  /* neighbour ids read in this iteration */
@@ -268,7 +277,7 @@ byo_status byo_msbfs(const byo_graph* g, const uint32_t* host_sources, uint32_t 
 /* allocates, so this call takes the CSR itself.                            */
 /*                                                                          */
 /* It runs the same persistent BFS kernel as byo_bfs for ONE source.  All    */
-/* scratch lives in a fixed file-scope device array of 9,308,160 bytes,    */
+/* scratch lives in a fixed file-scope device array of 9,324,800 bytes,    */
 /* sized for n <= BYO_NOALLOC_MAX_VERTICES; every GPU that loads the       */
 /* library holds it until the process exits.  The call makes no cudaMalloc, */
 /* cudaFree or other allocating call.                                       */

@@ -35,6 +35,8 @@ BYO_SCHED_HEURISTIC = 0
 BYO_SCHED_LEARNED = 1
 BYO_SCHED_PUSH = 2
 BYO_SCHED_PULL = 3
+BYO_SCHED_FIXED = 4
+BYO_NUM_ACTIONS = 5
 
 
 class ByoError(RuntimeError):
@@ -45,7 +47,8 @@ class ByoError(RuntimeError):
 
 class byo_sched(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("thr_thread", ctypes.c_uint32), ("thr_warp", ctypes.c_uint32),
-                ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("mlp", ctypes.c_void_p)]
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("mlp", ctypes.c_void_p),
+                ("action", ctypes.c_uint32)]
 
 
 class byo_bfs_iter(ctypes.Structure):
@@ -226,8 +229,8 @@ def byo_sched_default() -> byo_sched:
 
 
 def make_sched(mode: int = BYO_SCHED_HEURISTIC, thr_thread: int = 16, thr_warp: int = 1024, alpha: float = 15.0,
-               beta: float = 18.0, mlp: int | None = None) -> byo_sched:
-    return byo_sched(mode, thr_thread, thr_warp, alpha, beta, mlp)
+               beta: float = 18.0, mlp: int | None = None, action: int = 1) -> byo_sched:
+    return byo_sched(mode, thr_thread, thr_warp, alpha, beta, mlp, action)
 
 
 def byo_bfs(g: int, sources, levels: torch.Tensor | None = None, parents: torch.Tensor | None = None,

@@ -49,6 +49,10 @@ struct BfsCtl {
   unsigned long long cnt[3][kBuckets];  // appends per bucket, by level mod 3
   unsigned long long sdeg[3];           // sum of degrees of the frontier being built
   unsigned long long scanned[3];        // neighbour ids read while building it
+  // hand-over from a solo run of block 0 to the grid
+  uint32_t solo_L, solo_done, solo_prev, pad;
+  unsigned long long solo_nvis, solo_mvis;
+  unsigned long long solo_base[kBuckets];
 };
 
 struct BfsWork {
@@ -102,7 +106,7 @@ struct BfsShared {
   int dir, action, bt, bw, prev_dir;
   int fb_valid;
   uint64_t t_top;
-  float logits[kActions];
+  uint32_t t_level;  // level whose start time t_top is
 };
 
 __device__ __forceinline__ int find_bucket(const uint64_t* pre, int lo, int hi, uint64_t i) {
@@ -161,17 +165,23 @@ __device__ __forceinline__ uint32_t frontier_vertex(const BfsArgs<G>& a, const B
 }
 
 // ---------------------------------------------------------------- push
+// Who shares a push iteration: the whole grid, or one CTA alone (solo levels).
+struct Workers {
+  uint32_t cta, ctas;    // this CTA's rank and the number of CTAs
+  uint32_t warp, warps;  // this warp's rank and the number of warps
+};
+
 template <typename G, bool kParents>
-__device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, uint32_t L, int nxt, uint64_t& acc_deg,
-                           uint64_t& acc_scan) {
+__device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, const Workers& wk, uint32_t L, int nxt,
+                           uint64_t& acc_deg, uint64_t& acc_scan) {
   const uint32_t lane = lane_id();
-  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t gwarp = wk.warp;
+  const uint32_t nwarps = wk.warps;
   const int bt = S.bt, bw = S.bw;
 
   // CTA bin: chunks of high-degree vertices
   const uint64_t totC = S.preC[kBuckets] - S.preC[bw + 1];
-  for (uint64_t j = blockIdx.x; j < totC; j += gridDim.x) {
+  for (uint64_t j = wk.cta; j < totC; j += wk.ctas) {
     uint64_t jj = j + S.preC[bw + 1];
     int b = find_bucket(S.preC, bw + 1, kBuckets - 1, jj);
     uint64_t K = (b >= 12) ? (1ull << (b - 11)) : 1ull;  // chunks per vertex: 2^b / kChunk
@@ -359,6 +369,102 @@ __device__ __forceinline__ void flush_acc(unsigned long long* dst, uint64_t v) {
   if (lane_id() == 0 && v) atomicAdd(dst, (unsigned long long)v);
 }
 
+// Start of level L for the calling CTA: frontier counts and prefixes, the
+// trace, the schedule decision and the push bins.  `owner` (block 0) also
+// zeroes the counters of level L+2 and writes the trace.  Returns |F|.
+template <typename G>
+__device__ uint32_t level_top(const BfsArgs<G>& a, BfsShared& S, uint32_t L, bool owner) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t n = a.g.num_vertices();
+  const uint64_t m = a.g.num_edges();
+  BfsCtl* ctl = a.ctl;
+  const int cur = L % 3, old = (L + 2) % 3;
+  if (tid < (uint32_t)kBuckets) S.cnt[tid] = (uint32_t)ld_cg(&ctl->cnt[cur][tid]);
+  __syncthreads();
+  if (tid == 0) {
+    uint64_t now = globaltimer();
+    S.pre[0] = 0;
+    for (int b = 0; b < kBuckets; ++b) S.pre[b + 1] = S.pre[b] + S.cnt[b];
+    S.nf = (uint32_t)S.pre[kBuckets];
+    S.mf = ld_cg(&ctl->sdeg[cur]);
+    if (owner && L > 0 && L - 1 < kTraceCap && S.t_level == L - 1) {
+      byo_bfs_iter* r = a.trace + (L - 1);
+      r->t_ns = now - S.t_top;
+      r->edges_examined = ld_cg(&ctl->scanned[cur]);
+    }
+    if (S.t_level != L) {
+      S.t_top = now;
+      S.t_level = L;
+    }
+  }
+  __syncthreads();
+  if (S.nf == 0) return 0;
+  if (owner && tid < (uint32_t)kBuckets) ctl->cnt[old][tid] = 0;
+  if (owner && tid == 0) {
+    ctl->sdeg[old] = 0;
+    ctl->scanned[old] = 0;
+  }
+  if (tid < 32) {
+    SchedFeatures f;
+    f.nf = S.nf;
+    f.mf = S.mf;
+    f.nu = (uint64_t)n - S.nvis - S.nf;
+    f.mu = m - S.mvis - S.mf;
+    f.n = n;
+    f.m = m;
+    f.h[0] = (uint32_t)(S.pre[3]);
+    f.h[1] = (uint32_t)(S.pre[6] - S.pre[3]);
+    f.h[2] = (uint32_t)(S.pre[9] - S.pre[6]);
+    f.h[3] = (uint32_t)(S.pre[kBuckets] - S.pre[9]);
+    int action = sched_decide(a.sp, f, S.prev_dir);  // warp-collective
+    if (tid == 0) {
+      S.action = action;
+      S.dir = action == 0 ? 0 : 1;
+      sched_bins(a.sp, action, &S.bt, &S.bw);
+      if (owner && L < kTraceCap) {
+        byo_bfs_iter* r = a.trace + L;
+        r->level = L;
+        r->direction = (uint32_t)S.dir;
+        r->action = (uint32_t)action;
+        r->frontier = S.nf;
+        r->frontier_edges = S.mf;
+        r->unvisited = (uint32_t)f.nu;
+        r->unvisited_edges = f.mu;
+        for (int k = 0; k < 4; ++k) r->hist[k] = f.h[k];
+        r->reserved = 0;
+        r->edges_examined = 0;
+        r->t_ns = 0;
+      }
+      // CTA-bin work items: vertices * chunks per vertex
+      S.preC[0] = 0;
+      for (int b = 0; b < kBuckets; ++b) {
+        uint64_t K = (b >= 12) ? (1ull << (b - 11)) : 1ull;
+        S.preC[b + 1] = S.preC[b] + (b > S.bw ? (uint64_t)S.cnt[b] * K : 0ull);
+      }
+    }
+  }
+  __syncthreads();
+  return S.nf;
+}
+
+// End of a level for the calling CTA: its share of the next frontier's edge
+// and scan counts, then the level-local state moves on.
+template <typename G>
+__device__ __forceinline__ void level_end(const BfsArgs<G>& a, BfsShared& S, int nxt, uint64_t acc_deg,
+                                          uint64_t acc_scan) {
+  flush_acc(&a.ctl->sdeg[nxt], acc_deg);
+  flush_acc(&a.ctl->scanned[nxt], acc_scan);
+  __syncthreads();
+  if (threadIdx.x < (uint32_t)kBuckets) S.base[threadIdx.x] += S.cnt[threadIdx.x];
+  if (threadIdx.x == 0) {
+    S.nvis += S.nf;
+    S.mvis += S.mf;
+    S.prev_dir = S.dir;
+    S.fb_valid = S.dir == 0;
+  }
+  __syncthreads();
+}
+
 template <typename G, bool kParents>
 __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
   __shared__ BfsShared S;
@@ -367,6 +473,9 @@ __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
   const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint32_t n = a.g.num_vertices();
   BfsCtl* ctl = a.ctl;
+  const bool owner = blockIdx.x == 0;
+  const Workers grid_wk{blockIdx.x, gridDim.x, (uint32_t)(gtid >> 5), (uint32_t)(gthreads >> 5)};
+  const Workers solo_wk{0, 1, tid >> 5, blockDim.x >> 5};
 
   // ---- init: levels, parents, visited bits, counters
   for (uint64_t v = gtid; v < n; v += gthreads) {
@@ -374,7 +483,7 @@ __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
     if (kParents) a.parent[v] = kInf;
   }
   for (uint64_t w = gtid; w < a.nw; w += gthreads) a.vis[w] = 0;
-  if (blockIdx.x == 0) {
+  if (owner) {
     for (int i = tid; i < 3 * kBuckets; i += blockDim.x) (&ctl->cnt[0][0])[i] = 0;
     if (tid < 3) {
       ctl->sdeg[tid] = 0;
@@ -388,9 +497,10 @@ __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
     S.mvis = 0;
     S.prev_dir = 1;
     S.fb_valid = 0;
+    S.t_level = kInf;
   }
   if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
-  if (blockIdx.x == 0 && tid == 0) {
+  if (owner && tid == 0) {
     uint32_t s = a.src;
     uint32_t d = a.g.degree(s);
     int b = degree_bucket(d);
@@ -403,82 +513,67 @@ __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
   }
   if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
 
-  const uint64_t m = a.g.num_edges();
   const uint64_t t_begin = globaltimer();
-  for (uint32_t L = 0;; ++L) {
-    const int cur = L % 3, nxt = (L + 1) % 3, old = (L + 2) % 3;
+  uint32_t L = 0;
+  while (true) {
     // a BFS has at most n levels; the whole traversal is also time-bounded
     if (L > n || ld_cg(&ctl->err) != 0 || globaltimer() - t_begin > a.limit_ns) {
       if (tid == 0) atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_TIMEOUT);
       return;
     }
-    if (tid < (uint32_t)kBuckets) S.cnt[tid] = (uint32_t)ld_cg(&ctl->cnt[cur][tid]);
-    __syncthreads();
-    if (tid == 0) {
-      uint64_t now = globaltimer();
-      S.pre[0] = 0;
-      for (int b = 0; b < kBuckets; ++b) S.pre[b + 1] = S.pre[b] + S.cnt[b];
-      S.nf = (uint32_t)S.pre[kBuckets];
-      S.mf = ld_cg(&ctl->sdeg[cur]);
-      if (blockIdx.x == 0 && L > 0 && L - 1 < kTraceCap) {
-        byo_bfs_iter* r = a.trace + (L - 1);
-        r->t_ns = now - S.t_top;
-        r->edges_examined = ld_cg(&ctl->scanned[cur]);
-      }
-      S.t_top = now;
-    }
-    __syncthreads();
-    if (S.nf == 0) {
-      if (blockIdx.x == 0 && tid == 0) ctl->levels = L;
+    if (level_top(a, S, L, owner) == 0) {
+      if (owner && tid == 0) ctl->levels = L;
       break;
     }
-    if (blockIdx.x == 0 && tid < (uint32_t)kBuckets) ctl->cnt[old][tid] = 0;
-    if (blockIdx.x == 0 && tid == 0) {
-      ctl->sdeg[old] = 0;
-      ctl->scanned[old] = 0;
-    }
-    // ---- schedule: direction and bins for this iteration
-    if (tid < 32) {
-      SchedFeatures f;
-      f.nf = S.nf;
-      f.mf = S.mf;
-      f.nu = (uint64_t)n - S.nvis - S.nf;
-      f.mu = m - S.mvis - S.mf;
-      f.n = n;
-      f.m = m;
-      f.h[0] = (uint32_t)(S.pre[3]);
-      f.h[1] = (uint32_t)(S.pre[6] - S.pre[3]);
-      f.h[2] = (uint32_t)(S.pre[9] - S.pre[6]);
-      f.h[3] = (uint32_t)(S.pre[kBuckets] - S.pre[9]);
-      int action = sched_decide(a.sp, f, S.prev_dir);  // warp-collective
-      if (tid == 0) {
-        S.action = action;
-        S.dir = action == 0 ? 0 : 1;
-        sched_bins(a.sp, action, &S.bt, &S.bw);
-        if (blockIdx.x == 0 && L < kTraceCap) {
-          byo_bfs_iter* r = a.trace + L;
-          r->level = L;
-          r->direction = (uint32_t)S.dir;
-          r->action = (uint32_t)action;
-          r->frontier = S.nf;
-          r->frontier_edges = S.mf;
-          r->unvisited = (uint32_t)f.nu;
-          r->unvisited_edges = f.mu;
-          for (int k = 0; k < 4; ++k) r->hist[k] = f.h[k];
-          r->reserved = 0;
-          r->edges_examined = 0;
-          r->t_ns = 0;
-        }
-        // CTA-bin work items: vertices * chunks per vertex
-        S.preC[0] = 0;
-        for (int b = 0; b < kBuckets; ++b) {
-          uint64_t K = (b >= 12) ? (1ull << (b - 11)) : 1ull;
-          S.preC[b + 1] = S.preC[b] + (b > S.bw ? (uint64_t)S.cnt[b] * K : 0ull);
-        }
-      }
-    }
-    __syncthreads();
+    const int nxt = (L + 1) % 3;
     uint64_t acc_deg = 0, acc_scan = 0;
+    if (S.action == kActionSolo) {
+      // Levels with tiny frontiers: block 0 runs them alone with CTA barriers
+      // only, while the other CTAs wait at the grid barrier; it stops when the
+      // schedule asks for another action or the traversal ends, and hands the
+      // level-local state over through the control block.
+      if (owner) {
+        uint32_t Ls = L;
+        bool done = false;
+        while (true) {
+          const int nx = (Ls + 1) % 3;
+          uint64_t ad = 0, as = 0;
+          push_phase<G, kParents>(a, S, solo_wk, Ls, nx, ad, as);
+          level_end(a, S, nx, ad, as);
+          ++Ls;
+          if (Ls > n || globaltimer() - t_begin > a.limit_ns) {
+            if (tid == 0) atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_TIMEOUT);
+            break;
+          }
+          if (level_top(a, S, Ls, true) == 0) {
+            done = true;
+            break;
+          }
+          if (S.action != kActionSolo) break;
+        }
+        if (tid == 0) {
+          ctl->solo_L = Ls;
+          ctl->solo_done = done ? 1u : 0u;
+          ctl->solo_nvis = S.nvis;
+          ctl->solo_mvis = S.mvis;
+          ctl->solo_prev = (uint32_t)S.prev_dir;
+          if (done) ctl->levels = Ls;
+        }
+        if (tid < (uint32_t)kBuckets) ctl->solo_base[tid] = S.base[tid];
+      }
+      if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
+      if (ld_cg(&ctl->solo_done)) break;
+      L = ld_cg(&ctl->solo_L);
+      if (tid < (uint32_t)kBuckets) S.base[tid] = ld_cg(&ctl->solo_base[tid]);
+      if (tid == 0) {
+        S.nvis = ld_cg(&ctl->solo_nvis);
+        S.mvis = ld_cg(&ctl->solo_mvis);
+        S.prev_dir = (int)ld_cg(&ctl->solo_prev);
+        S.fb_valid = 0;
+      }
+      __syncthreads();
+      continue;
+    }
     if (S.dir == 0) {
       if (!S.fb_valid) {
         // queue -> bit-vector for this level
@@ -494,18 +589,10 @@ __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
       }
       pull_phase<G, kParents>(a, S, L, nxt, acc_deg, acc_scan);
     } else {
-      push_phase<G, kParents>(a, S, L, nxt, acc_deg, acc_scan);
+      push_phase<G, kParents>(a, S, grid_wk, L, nxt, acc_deg, acc_scan);
     }
-    flush_acc(&ctl->sdeg[nxt], acc_deg);
-    flush_acc(&ctl->scanned[nxt], acc_scan);
-    __syncthreads();
-    if (tid < (uint32_t)kBuckets) S.base[tid] += S.cnt[tid];
-    if (tid == 0) {
-      S.nvis += S.nf;
-      S.mvis += S.mf;
-      S.prev_dir = S.dir;
-      S.fb_valid = S.dir == 0;
-    }
+    level_end(a, S, nxt, acc_deg, acc_scan);
+    ++L;
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
   }
 }
@@ -667,7 +754,7 @@ constexpr size_t kNaQueue = kNaFb + na_align(8 * kNaWords);
 constexpr size_t kNaTrace = kNaQueue + na_align(4ull * kNoallocMaxVertices);
 constexpr size_t kNaBytes = kNaTrace + na_align(sizeof(byo_bfs_iter) * kTraceCap);
 
-// 9,308,160 bytes (8.9 MiB).  In host code this name is only a host-side stand-in for the
+// 9,324,800 bytes (8.9 MiB).  In host code this name is only a host-side stand-in for the
 // array; kernels get its device address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 

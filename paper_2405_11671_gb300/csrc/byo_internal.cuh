@@ -157,12 +157,19 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
 
 __device__ __forceinline__ int degree_bucket(uint32_t d) { return d == 0 ? 0 : 32 - __clz(d); }
 
-// Grid-wide barrier for a cooperative launch.  Sense by generation counter.
-// Every wait is bounded by `limit_ns`; on timeout the error word is set and
-// false is returned (the caller then leaves its loop and exits).
+// Grid-wide barrier for a cooperative launch, two levels deep: CTAs arrive
+// in groups of kBarGroup on their own counters (32 bytes apart), the last of
+// each group arrives at the root, and the last group releases everyone by
+// bumping the generation.  Every wait is bounded by `limit_ns`; on timeout the
+// error word is set and false is returned (the caller leaves its loop and exits).
+constexpr uint32_t kBarGroup = 16;
+constexpr uint32_t kBarMaxGroups = 512;  // up to 8192 CTAs
+
 struct GridBar {
-  uint32_t count;
+  uint32_t count;  // groups arrived
   uint32_t gen;
+  uint32_t pad[30];
+  uint32_t sub[kBarMaxGroups * 8];  // group counters, one per 32 bytes
 };
 
 __device__ __forceinline__ bool grid_barrier(GridBar* bar, uint32_t nblocks, uint32_t* err, uint64_t limit_ns) {
@@ -172,12 +179,22 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, uint32_t nblocks, uin
     uint32_t ok = 1;
     uint32_t g = ld_acquire(&bar->gen);
     __threadfence();
-    uint32_t arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == nblocks - 1) {
-      bar->count = 0;
+    const uint32_t grp = blockIdx.x / kBarGroup;
+    const uint32_t gsize = min(kBarGroup, nblocks - grp * kBarGroup);
+    const uint32_t ngroups = (nblocks + kBarGroup - 1) / kBarGroup;
+    uint32_t* sc = &bar->sub[grp * 8];
+    bool release = false;
+    if (atomicAdd(sc, 1u) == gsize - 1) {
+      *sc = 0;  // every member of the group has arrived and now waits on gen
       __threadfence();
-      st_release(&bar->gen, g + 1);
-    } else {
+      if (atomicAdd(&bar->count, 1u) == ngroups - 1) {
+        bar->count = 0;
+        __threadfence();
+        st_release(&bar->gen, g + 1);
+        release = true;
+      }
+    }
+    if (!release) {
       uint64_t t0 = globaltimer();
       uint32_t spins = 0;
       while (ld_acquire(&bar->gen) == g) {

@@ -434,6 +434,7 @@ byo_sched byo_sched_default(void) {
   s.alpha = 15.0f;
   s.beta = 18.0f;
   s.mlp = nullptr;
+  s.action = 1;
   return s;
 }
 

@@ -1,4 +1,4 @@
-// mlp.cu -- the schedule network: a 12 -> 32 -> 32 -> 4 ReLU MLP that maps the
+// mlp.cu -- the schedule network: a 12 -> 32 -> 32 -> 5 ReLU MLP that maps the
 // frontier features of one edgeMap iteration to a schedule action (not in the
 // paper; it only chooses between equivalent execution paths).  Forward and
 // backward passes, the weighted softmax cross-entropy loss and the Adam update
@@ -229,7 +229,7 @@ const float* mlp_device_params(const byo_mlp* m) { return m ? m->d_params : null
 
 byo_status sched_params(const byo_sched* s, SchedParams* out) {
   byo_sched d = s ? *s : byo_sched_default();
-  if (d.mode > BYO_SCHED_PULL) {
+  if (d.mode > BYO_SCHED_FIXED || (d.mode == BYO_SCHED_FIXED && d.action >= (uint32_t)kActions)) {
     set_error("byo_sched: unknown mode %u", d.mode);
     return BYO_ERR_INVALID_ARG;
   }
@@ -254,6 +254,7 @@ byo_status sched_params(const byo_sched* s, SchedParams* out) {
     return BYO_ERR_INVALID_ARG;
   }
   out->mode = (int)d.mode;
+  out->fixed_action = (int)d.action;
   out->bt = bt;
   out->bw = bw;
   out->alpha = d.alpha;

@@ -4,7 +4,7 @@
 //   HEURISTIC  Beamer-style switch: push -> pull when the frontier's edges
 //              exceed the unvisited edges / alpha; pull -> push when the
 //              frontier has fewer than n / beta vertices.
-//   LEARNED    a 12 -> 32 -> 32 -> 4 ReLU network over frontier features,
+//   LEARNED    a 12 -> 32 -> 32 -> 5 ReLU network over frontier features,
 //              evaluated by one warp of every CTA inside the persistent loop.
 //   PUSH/PULL  fixed.
 // Schedules never change results, only which kernel path runs.
@@ -16,11 +16,16 @@ namespace byo {
 
 constexpr int kFeatures = 12;
 constexpr int kHidden = 32;
-constexpr int kActions = 4;  // 0 pull; 1 push (thr_thread, thr_warp); 2 push (4, 128); 3 push (64, 4096)
+// 0 pull; 1 push (thr_thread, thr_warp); 2 push (4, 128); 3 push (64, 4096);
+// 4 push run by one CTA alone for as many consecutive levels as the schedule
+// keeps choosing it (no grid barrier between those levels)
+constexpr int kActions = 5;
+constexpr int kActionSolo = 4;
 constexpr int kMlpParams = kHidden * kFeatures + kHidden + kHidden * kHidden + kHidden + kActions * kHidden + kActions;
 
 struct SchedParams {
   int mode;
+  int fixed_action;
   int bt, bw;  // log2 of thr_thread / thr_warp
   float alpha, beta;
   const float* w;  // device MLP parameters (LEARNED)
@@ -67,6 +72,7 @@ __device__ __forceinline__ void sched_bins(const SchedParams& sp, int action, in
 
 // Warp-collective (all 32 lanes of one warp); returns the action on every lane.
 __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFeatures& f, int prev_dir) {
+  if (sp.mode == BYO_SCHED_FIXED) return sp.fixed_action;
   if (sp.mode == BYO_SCHED_PUSH) return 1;
   if (sp.mode == BYO_SCHED_PULL) return 0;
   if (sp.mode == BYO_SCHED_HEURISTIC || sp.w == nullptr) {

@@ -1,7 +1,7 @@
 """Learned edgeMap schedule: training data, training and evaluation.
 
 The schedule network (``csrc/mlp.cu``, ``csrc/sched.cuh``) picks, for every BFS
-iteration, one of four result-identical actions from 12 frontier features:
+iteration, one of five result-identical actions from 12 frontier features:
 
 ====== =========================================================
 action meaning
@@ -10,6 +10,7 @@ action meaning
 1      sparse edgeMap (push), bins thread < 16, warp < 1024
 2      push, bins thread < 4, warp < 128
 3      push, bins thread < 64, warp < 4096
+4      push by one CTA alone, no grid barrier between such levels
 ====== =========================================================
 
 Training data are timings the engine records itself: every training graph is
@@ -34,10 +35,8 @@ import sys
 
 import numpy as np
 
-NUM_ACTIONS = 4
+NUM_ACTIONS = 5
 NUM_FEATURES = 12
-# (mode, thr_thread, thr_warp) that force each action at every iteration
-FORCED = {0: ("pull", 16, 1024), 1: ("push", 16, 1024), 2: ("push", 4, 128), 3: ("push", 64, 4096)}
 DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "sched_mlp.json")
 
 
@@ -66,8 +65,7 @@ def trace_features(trace, n: int, m: int) -> np.ndarray:
 
 
 def forced_sched(byo, action: int):
-    mode, tt, tw = FORCED[action]
-    return byo.make_sched(byo.BYO_SCHED_PULL if mode == "pull" else byo.BYO_SCHED_PUSH, tt, tw)
+    return byo.make_sched(byo.BYO_SCHED_FIXED, 16, 1024, action=action)
 
 
 def time_actions(byo, g, sources, repeats: int = 2):

@@ -48,4 +48,5 @@ def test_binding_struct_layouts():
     from paper_2405_11671_gb300 import _byo
     assert ctypes.sizeof(_byo.byo_bfs_iter) == 72
     assert _byo.byo_bfs_iter.t_ns.offset == 64
-    assert ctypes.sizeof(_byo.byo_sched) == 32 and _byo.byo_sched.mlp.offset == 24
+    assert ctypes.sizeof(_byo.byo_sched) == 40 and _byo.byo_sched.mlp.offset == 24
+    assert _byo.byo_sched.action.offset == 32

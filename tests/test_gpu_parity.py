@@ -154,15 +154,24 @@ def test_empty_graph(byo):
 
 # ----------------------------------------------------------------------------- BFS
 
-SCHEDS = {"heuristic": (0, 16, 1024), "push": (2, 16, 1024), "pull": (3, 16, 1024),
-          "push_thread_only": (2, 1 << 31, 1 << 31), "push_cta_heavy": (2, 1, 2)}
+SCHEDS = {"heuristic": (0, 16, 1024, 1), "push": (2, 16, 1024, 1), "pull": (3, 16, 1024, 1),
+          "push_thread_only": (2, 1 << 31, 1 << 31, 1), "push_cta_heavy": (2, 1, 2, 1),
+          "solo": (4, 16, 1024, 4), "solo_cta_heavy": (4, 1, 2, 4), "push_small_bins": (4, 16, 1024, 2),
+          "learned_random": (1, 16, 1024, 1)}
+
+
+@pytest.fixture(scope="module")
+def random_net(byo):
+    m = byo.byo_mlp_create(12345)  # untrained: mixes all five actions
+    yield m
+    byo.byo_mlp_destroy(m)
 
 
 @pytest.mark.parametrize("sched", sorted(SCHEDS))
-def test_bfs_levels_and_parents(byo, case, sched):
+def test_bfs_levels_and_parents(byo, case, sched, random_net):
     name, n, src, dst, ref, g = case
-    mode, tt, tw = SCHEDS[sched]
-    sp = byo.make_sched(mode, tt, tw)
+    mode, tt, tw, act = SCHEDS[sched]
+    sp = byo.make_sched(mode, tt, tw, mlp=random_net if mode == byo.BYO_SCHED_LEARNED else None, action=act)
     srcs = _sources(n, src, dst, ref)
     lv, par = byo.byo_bfs(g.handle, srcs, sched=sp)
     for i, s in enumerate(srcs):
@@ -234,13 +243,13 @@ def test_triangle_count_cta_path_and_windows(byo, monkeypatch, light_max, window
 def _mlp_batch(B=333, seed=0):
     rng = np.random.default_rng(seed)
     X = rng.uniform(0, 1, (B, 12)).astype(np.float32)
-    y = rng.integers(0, 4, B).astype(np.int32)
+    y = rng.integers(0, 5, B).astype(np.int32)
     w = rng.uniform(0.2, 2.0, B).astype(np.float32)
     return X, y, w
 
 
 def _split(v):
-    sizes = [32 * 12, 32, 32 * 32, 32, 4 * 32, 4]
+    sizes = [32 * 12, 32, 32 * 32, 32, 5 * 32, 5]
     out, o = [], 0
     for s in sizes:
         out.append(v[o:o + s])
@@ -254,7 +263,7 @@ def test_mlp_gradient_matches_oracle(byo):
     X, y, w = _mlp_batch()
     loss, grad = byo.byo_mlp_loss_grad(m, torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(),
                                        torch.from_numpy(w).cuda())
-    L, g64, _ = oracle.mlp_loss(P.astype(np.float64), 12, 32, 32, 4, X.astype(np.float64), y, w.astype(np.float64))
+    L, g64, _ = oracle.mlp_loss(P.astype(np.float64), 12, 32, 32, 5, X.astype(np.float64), y, w.astype(np.float64))
     assert abs(loss - L) <= 1e-4 * max(1.0, abs(L))
     g32 = grad.cpu().numpy().astype(np.float64)
     for a, b in zip(_split(g32), _split(g64)):
@@ -273,7 +282,7 @@ def test_mlp_train_and_predict(byo):
     assert l1 < 0.5 * l0
     pred = byo.byo_mlp_predict(m, Xd).cpu().numpy()
     P = byo.byo_mlp_get_params(m).astype(np.float64)
-    _, _, logits = oracle.mlp_loss(P, 12, 32, 32, 4, X.astype(np.float64), y, None, want_grad=False)
+    _, _, logits = oracle.mlp_loss(P, 12, 32, 32, 5, X.astype(np.float64), y, None, want_grad=False)
     srt = np.sort(logits, axis=1)
     clear = (srt[:, -1] - srt[:, -2]) > 1e-3                      # skip near-ties (FP32 vs FP64)
     assert np.array_equal(pred[clear], np.argmax(logits, axis=1)[clear])
