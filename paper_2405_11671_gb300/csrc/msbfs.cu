@@ -323,7 +323,7 @@ extern "C" byo_status byo_msbfs(const byo_graph* gc, const uint32_t* host_source
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!g->ms_seen) {
     BYO_RETURN_IF(dev_alloc_t(&g->ms_seen, 3ull * g->n + 1, "MS-BFS words"));
-    BYO_RETURN_IF(dev_alloc_t(&g->ms_ctl, 1, "MS-BFS control"));
+    BYO_RETURN_IF(dev_alloc(&g->ms_ctl, sizeof(MsCtl), "MS-BFS control"));
     BYO_CUDA(cudaMemset(g->ms_ctl, 0, sizeof(MsCtl)));
   }
   if (g->ms_src_cap < gs.size()) {

@@ -9,8 +9,9 @@
 // the ids of N+(v) for all v in N+(u) are walked 32 at a time by a warp
 // (edge-balanced across the warp) and looked up in shared memory.  u with |N+(u)| <= kLightMax: one warp each; the staged N+(u) is
 // loaded into an open-addressing hash set in the warp's shared memory and each
-// id of N+(v) costs one or two probes.  Larger u: one CTA each, N+(u) staged
-// in windows of kWindow ids and searched by bisection.
+// id of N+(v) costs one or two probes.  Larger u: one CTA each (taken from a
+// work counter), N+(u) staged in windows of kWindow ids, each hashed the same
+// way into the CTA's shared memory.
 #include <stdlib.h>
 
 #include "byo_internal.cuh"
@@ -21,7 +22,7 @@
 namespace byo {
 
 constexpr uint32_t kLightMax = 256;   // capacity of a warp's shared-memory slice (ids)
-constexpr uint32_t kWindow = 16384;   // capacity of a CTA's shared-memory window (ids)
+constexpr uint32_t kWindow = 8192;    // capacity of a CTA's shared-memory window (ids)
 constexpr int kTcThreads = 256;
 
 // The light/heavy split and the window length can be lowered (never raised)
@@ -43,7 +44,7 @@ struct TcWork {
   uint32_t* outdeg = nullptr;   // n
   uint32_t* light = nullptr;    // n
   uint32_t* heavy = nullptr;    // n
-  uint32_t* ctr = nullptr;      // [0] light count, [1] heavy count, [2] light cursor, [3] error
+  uint32_t* ctr = nullptr;      // [0] light count, [1] heavy count, [2] light cursor, [3] error, [4] heavy cursor
   unsigned long long* count = nullptr;
 };
 
@@ -231,16 +232,6 @@ __global__ void tc_classify_kernel(const uint64_t* __restrict__ dag_off, uint32_
 }
 
 // ---------------------------------------------------------------- intersect
-__device__ __forceinline__ bool smem_contains(const uint32_t* a, uint32_t len, uint32_t x) {
-  uint32_t lo = 0, hi = len;
-  while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo < len && a[lo] == x;
-}
-
 // Open-addressing hash set in shared memory (linear probing, empty = INF,
 // multiplicative hashing); the table has at least twice as many slots as keys.
 struct SmemHash {
@@ -257,11 +248,6 @@ struct SmemHash {
   }
 };
 
-struct SmemSorted {
-  const uint32_t* a;
-  uint32_t len;
-  __device__ __forceinline__ bool contains(uint32_t x) const { return smem_contains(a, len, x); }
-};
 
 // The warp walks the concatenation of N+(v) for the 32 (or fewer) v held by
 // its lanes and counts the ids w in [lo_id, hi_id] that the set contains.
@@ -369,14 +355,19 @@ __global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __
   if (lane == 0 && t) atomicAdd(count, (unsigned long long)t);
 }
 
+constexpr uint32_t kHeavyTable = 2 * kWindow;
+constexpr size_t kHeavySmem = (size_t)(kWindow + 8 + kHeavyTable) * sizeof(uint32_t);
+
 __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __restrict__ dag_off,
                                                               const uint32_t* __restrict__ dag_col,
                                                               const uint32_t* __restrict__ heavy, uint32_t* ctr,
                                                               unsigned long long* count, uint32_t window,
                                                               uint64_t limit_ns) {
   extern __shared__ __align__(16) uint32_t win[];
+  uint32_t* table = win + kWindow + 8;
   __shared__ __align__(8) uint64_t bar;
   __shared__ bool ok_s;
+  __shared__ uint32_t idx_s;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t nheavy = __ldcg(ctr + 1);
   uint32_t* err = ctr + 3;
@@ -384,14 +375,18 @@ __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __
   __syncthreads();
   uint32_t phase = 0;
   uint64_t hits = 0;
-  for (uint32_t idx = blockIdx.x; idx < nheavy; idx += gridDim.x) {
+  while (true) {
+    if (threadIdx.x == 0) idx_s = atomicAdd(ctr + 4, 1u);
+    __syncthreads();
+    const uint32_t idx = idx_s;
+    if (idx >= nheavy) break;
     uint32_t u = __ldg(heavy + idx);
     uint64_t beg = dag_off[u], end = dag_off[u + 1];
     for (uint64_t wb = beg; wb < end; wb += window) {
       uint64_t we = wb + window < end ? wb + window : end;
       uint64_t a0 = wb & ~3ull, a1 = (we + 3) & ~3ull;
       uint32_t head = (uint32_t)(wb - a0), wlen = (uint32_t)(we - wb);
-      __syncthreads();
+      __syncthreads();  // every thread is done with the previous window and table
       if (threadIdx.x == 0) {
         bulk_load(win, dag_col + a0, (uint32_t)((a1 - a0) * 4), &bar);
         ok_s = mbar_wait(&bar, phase, err, limit_ns);
@@ -401,12 +396,24 @@ __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __
       mbar_wait(&bar, phase, err, limit_ns);  // completed: every thread observes the phase
       phase ^= 1;
       const uint32_t* list = win + head;
+      uint32_t bits = 32 - __clz(2 * wlen - 1);
+      if (bits < 5) bits = 5;
+      const uint32_t slots = 1u << bits;
+      for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) table[i] = kInf;
+      __syncthreads();
+      for (uint32_t k = threadIdx.x; k < wlen; k += blockDim.x) {
+        uint32_t x = list[k];
+        uint32_t h = (x * 0x9E3779B1u) >> (32 - bits);
+        while (atomicCAS(table + h, kInf, x) != kInf) h = (h + 1) & (slots - 1);
+      }
+      __syncthreads();
+      SmemHash set{table, slots - 1, 32 - bits};
       uint32_t lo_id = list[0], hi_id = list[wlen - 1];
       for (uint64_t k0 = beg + (uint64_t)w * 32; k0 < end; k0 += (uint64_t)nw * 32) {
         uint64_t k = k0 + lane;
         bool has = k < end;
         uint32_t v = has ? __ldg(dag_col + k) : 0;
-        hits += warp_count_group(dag_off, dag_col, v, has, SmemSorted{list, wlen}, lo_id, hi_id);
+        hits += warp_count_group(dag_off, dag_col, v, has, set, lo_id, hi_id);
       }
     }
   }
@@ -434,7 +441,7 @@ byo_status ensure_tc_work(byo_graph* g) {
   if (st == BYO_OK) st = dev_alloc_t(&w->outdeg, g->n, "TC out-degrees");
   if (st == BYO_OK) st = dev_alloc_t(&w->light, g->n, "TC light list");
   if (st == BYO_OK) st = dev_alloc_t(&w->heavy, g->n, "TC heavy list");
-  if (st == BYO_OK) st = dev_alloc_t(&w->ctr, 4, "TC counters");
+  if (st == BYO_OK) st = dev_alloc_t(&w->ctr, 8, "TC counters");
   if (st == BYO_OK) st = dev_alloc_t(&w->count, 1, "TC count");
   if (st == BYO_OK) {
     cudaError_t e = cudaMemset(w->dag_col, 0, sizeof(uint32_t) * (w->half_cap + 8));
@@ -466,7 +473,7 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, cudaStream_t s) {
     tc_fill_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->dag_off, w->dag_col); ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_fill_kernel");
-  BYO_CUDA(cudaMemsetAsync(w->ctr, 0, 4 * sizeof(uint32_t), s));
+  BYO_CUDA(cudaMemsetAsync(w->ctr, 0, 8 * sizeof(uint32_t), s));
   BYO_CUDA(cudaMemsetAsync(w->count, 0, sizeof(unsigned long long), s));
   unsigned grid = (unsigned)sm_count() * 4;
   tc_classify_kernel<<<grid, 256, 0, s>>>(w->dag_off, g->n, env_cap("BYO_TC_LIGHT_MAX", kLightMax), w->light,
@@ -482,7 +489,7 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, cudaStream_t s) {
       w->dag_off, w->dag_col, w->light, w->ctr, w->count, limit); ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_light_kernel");
-  size_t dyn = (kWindow + 8) * sizeof(uint32_t);
+  size_t dyn = kHeavySmem;
   BYO_CUDA(cudaFuncSetAttribute(tc_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   {
     ProfScope ps("tc_heavy", s);
