@@ -236,6 +236,76 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched workload
+
+def run_batched(args, byo, torch):
+    """256 graphs (half ER, half RMAT; n log-uniform in [2^10, 2^18], average
+    degree uniform in [4, 64]) in one container: one step = 64-source
+    multi-source BFS in every member + CC of the whole batch."""
+    import numpy as np
+
+    import graphgen
+    from paper_2405_11671_gb300 import autotune
+    params = graphgen.batched_params(256)
+    ns, ks, srcs_l, dsts_l, sources = [], [], [], [], []
+    for kind, n, k, sd in params:
+        s, d = graphgen.batched_member(kind, n, k, sd)
+        ns.append(n)
+        ks.append(k)
+        srcs_l.append(s)
+        dsts_l.append(d)
+        picked = graphgen.pick_sources(n, s, d, 64, sd + 1).tolist()
+        picked += [v % n for v in range(64 - len(picked))]
+        sources.append(picked[:64])
+    src, dst = np.concatenate(srcs_l), np.concatenate(dsts_l)
+    g = byo.byo_batch_build(ns, ks, dev_u32(torch, src), dev_u32(torch, dst))
+    N, m = byo.byo_num_vertices(g), byo.byo_num_edges(g)
+    levels = torch.empty((64, N), dtype=torch.int32, device="cuda")
+    labels = torch.empty(N, dtype=torch.int32, device="cuda")
+    tuned = autotune.tune_msbfs(byo, g, sources, 64, levels)
+    sp = byo.make_sched(byo.BYO_SCHED_HEURISTIC, 16, 1024, tuned["alpha"])
+    stream = torch.cuda.current_stream()
+
+    def step():
+        byo.byo_msbfs(g, sources, 64, levels, sched=sp)
+        byo.byo_cc(g, labels)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    byo.byo_profile_enable(True)
+    byo.byo_profile_reset()
+    l0 = byo.byo_kernel_launches()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    launches = byo.byo_kernel_launches() - l0
+    prof = byo.byo_profile_read()
+    byo.byo_profile_enable(False)
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / args.steps
+    deg = byo.byo_degree(g).to(torch.int64)
+    ms_edges = int(((levels != -1).to(torch.int64) * deg.unsqueeze(0)).sum().item()) // 2
+    edges = {"msbfs": ms_edges, "cc": m // 2}
+    tot = sum(v[1] for v in prof.values()) or 1.0
+    line = {"metric": METRIC, "value": round(sum(edges.values()) / (ms / 1e3) / 1e9, 3), "unit": "GTEPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
+            "config": {"workload": "batched256", "graphs": 256, "n": N, "m": m, "sources_per_graph": 64,
+                       "msbfs_alpha": tuned["alpha"], "autotune_ms": tuned["table_ms"]},
+            "edges_per_step": edges,
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot, 4)}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    byo.byo_graph_destroy(g)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -263,6 +333,9 @@ def main():
         dist.barrier()
     import paper_2405_11671_gb300 as byo
     byo.load()
+    if args.workload == "batched":
+        run_batched(args, byo, torch)
+        return
 
     def barrier():
         if dist:
@@ -392,7 +465,7 @@ def main():
     sched_cmp = None
     if args.schedules:
         sched_cmp = {}
-        cands = ["heuristic", "push", "pull", "solo"] + (["learned"] if os.path.exists(
+        cands = ["heuristic", "push", "pull"] + (["learned"] if os.path.exists(
             os.path.join(ROOT, "paper_2405_11671_gb300", "sched_mlp.json")) else [])
         for name in cands:
             mm = load_mlp(byo) if name == "learned" else None

@@ -261,10 +261,12 @@ byo_status byo_batch_member_base(const byo_graph* g, uint32_t i, uint32_t* host_
  * batch.  host_sources[i * num_sources + j] is source j of member i as a LOCAL
  * id (a plain graph is a batch of one).  levels[j * n + v] (device, n = total
  * vertices) = hop distance of global vertex v from source j of v's member, INF
- * if unreached.  Synchronises the stream.  Errors: INVALID_ARG, TIMEOUT, CUDA.
+ * if unreached.  sched (nullable): only alpha is used -- a level runs
+ * top-down while its frontier's edges * alpha < the edges not yet visited.
+ * Synchronises the stream.  Errors: INVALID_ARG, TIMEOUT, CUDA.
  */
 byo_status byo_msbfs(const byo_graph* g, const uint32_t* host_sources, uint32_t num_sources, uint32_t* levels,
-                     void* stream);
+                     const byo_sched* sched, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* BFS that allocates nothing (the paper has no counterpart; this is a       */

@@ -96,7 +96,7 @@ SIGNATURES = [
     ("byo_batch_build", _st, [_u32, ctypes.POINTER(_u32), ctypes.POINTER(_u64), _vp, _vp, _u32, _vp,
                                ctypes.POINTER(_vp)]),
     ("byo_batch_member_base", _st, [_vp, _u32, ctypes.POINTER(_u32)]),
-    ("byo_msbfs", _st, [_vp, ctypes.POINTER(_u32), _u32, _vp, _vp]),
+    ("byo_msbfs", _st, [_vp, ctypes.POINTER(_u32), _u32, _vp, ctypes.POINTER(byo_sched), _vp]),
     ("byo_bfs_noalloc", _st, [_u32, _u64, _vp, _vp, _u32, _vp, _vp, ctypes.POINTER(byo_sched), _vp]),
     ("byo_kernel_launches", _u64, []),
     ("byo_profile_enable", _st, [ctypes.c_int]),
@@ -356,13 +356,15 @@ def byo_batch_member_base(g: int, i: int) -> int:
     return v.value
 
 
-def byo_msbfs(g: int, sources, num_sources: int, levels: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+def byo_msbfs(g: int, sources, num_sources: int, levels: torch.Tensor | None = None,
+              sched: byo_sched | None = None, stream=None) -> torch.Tensor:
     """levels[num_sources, n]; sources = members x num_sources LOCAL ids (row-major)."""
     srcs = np.ascontiguousarray(np.asarray(sources, dtype=np.uint32).reshape(-1))
     n = byo_num_vertices(g)
     if levels is None:
         levels = torch.empty((num_sources, n), dtype=torch.int32, device="cuda")
-    _check(load().byo_msbfs(g, srcs.ctypes.data_as(ctypes.POINTER(_u32)), num_sources, levels.data_ptr(),
+    sp = ctypes.byref(sched) if sched is not None else None
+    _check(load().byo_msbfs(g, srcs.ctypes.data_as(ctypes.POINTER(_u32)), num_sources, levels.data_ptr(), sp,
                             _stream(stream)))
     return levels
 

@@ -298,7 +298,7 @@ extern "C" byo_status byo_batch_member_base(const byo_graph* g, uint32_t i, uint
 }
 
 extern "C" byo_status byo_msbfs(const byo_graph* gc, const uint32_t* host_sources, uint32_t num_sources,
-                                uint32_t* levels, void* stream) {
+                                uint32_t* levels, const byo_sched* sched, void* stream) {
   clear_error();
   BYO_RETURN_IF(check_graph(gc));
   byo_graph* g = const_cast<byo_graph*>(gc);
@@ -319,6 +319,11 @@ extern "C" byo_status byo_msbfs(const byo_graph* gc, const uint32_t* host_source
       }
       gs[(size_t)i * num_sources + j] = base + v;
     }
+  }
+  const float alpha = sched ? sched->alpha : 15.0f;
+  if (!(alpha > 0.0f)) {
+    set_error("byo_msbfs: alpha must be positive");
+    return BYO_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!g->ms_seen) {
@@ -349,7 +354,7 @@ extern "C" byo_status byo_msbfs(const byo_graph* gc, const uint32_t* host_source
     a.next = g->ms_seen + 2ull * g->n;
     a.ctl = ctl;
     a.limit_ns = timeout_ns();
-    a.alpha = 15.0f;
+    a.alpha = alpha;
     auto fn = msbfs_kernel<G>;
     int per_sm = 0;
     BYO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMsThreads, 0));
