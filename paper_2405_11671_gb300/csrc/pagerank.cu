@@ -191,37 +191,47 @@ __device__ __forceinline__ void pr_stream_warp(const G& g, uint32_t v0, uint32_t
   const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
   const uint32_t excl = incl - len;
   Comp acc{0.f, 0.f};
-  for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-    const uint32_t e = e0 + lane;
-    int owner = 0;
+  constexpr int kU = 4;  // chunks of 32 ids per step: kU independent gathers per lane in flight
+  for (uint32_t e00 = 0; e00 < total; e00 += 32 * kU) {
+    int key[kU];
+    uint32_t id[kU];
+    float x[kU];
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      int probe = owner + step;
-      uint32_t ex = __shfl_sync(0xFFFFFFFFu, excl, probe & 31);
-      if (probe < 32 && ex <= e) owner = probe;
-    }
-    const uint32_t oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
-    const uint32_t* op = reinterpret_cast<const uint32_t*>(
-        __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(s.p), owner));
-    Comp val{0.f, 0.f};
-    int key = 32;
-    if (e < total) {
-      val.s = __ldg(c + __ldg(op + (e - oex)));
-      key = owner;
+    for (int j = 0; j < kU; ++j) {
+      const uint32_t e = e00 + 32 * j + lane;
+      int owner = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        int probe = owner + step;
+        uint32_t ex = __shfl_sync(0xFFFFFFFFu, excl, probe & 31);
+        if (probe < 32 && ex <= e) owner = probe;
+      }
+      const uint32_t oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
+      const uint32_t* op = reinterpret_cast<const uint32_t*>(
+          __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(s.p), owner));
+      key[j] = e < total ? owner : 32;
+      id[j] = e < total ? __ldg(op + (e - oex)) : 0u;
     }
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      float ys = __shfl_up_sync(0xFFFFFFFFu, val.s, o);
-      float yc = __shfl_up_sync(0xFFFFFFFFu, val.c, o);
-      int yk = __shfl_up_sync(0xFFFFFFFFu, key, o);
-      if ((int)lane >= o && yk == key) val = comp_merge(Comp{ys, yc}, val);
+    for (int j = 0; j < kU; ++j) x[j] = key[j] < 32 ? __ldg(c + id[j]) : 0.f;
+    for (int j = 0; j < kU; ++j) {
+      const uint32_t e0 = e00 + 32 * j;
+      if (e0 >= total) break;  // warp-uniform
+      Comp val{x[j], 0.f};
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        float ys = __shfl_up_sync(0xFFFFFFFFu, val.s, o);
+        float yc = __shfl_up_sync(0xFFFFFFFFu, val.c, o);
+        int yk = __shfl_up_sync(0xFFFFFFFFu, key[j], o);
+        if ((int)lane >= o && yk == key[j]) val = comp_merge(Comp{ys, yc}, val);
+      }
+      // this lane's vertex: its ids in this chunk end at lane hi-1-e0
+      const uint32_t lo = excl > e0 ? excl : e0;
+      const uint32_t hi = (excl + len) < (e0 + 32) ? (excl + len) : (e0 + 32);
+      const int srcl = hi > lo ? (int)(hi - 1 - e0) : (int)lane;
+      Comp part{__shfl_sync(0xFFFFFFFFu, val.s, srcl), __shfl_sync(0xFFFFFFFFu, val.c, srcl)};
+      if (hi > lo) acc = comp_merge(acc, part);
     }
-    // this lane's vertex: its ids in this chunk end at lane hi-1-e0
-    const uint32_t lo = excl > e0 ? excl : e0;
-    const uint32_t hi = (excl + len) < (e0 + 32) ? (excl + len) : (e0 + 32);
-    const int srcl = hi > lo ? (int)(hi - 1 - e0) : (int)lane;
-    Comp part{__shfl_sync(0xFFFFFFFFu, val.s, srcl), __shfl_sync(0xFFFFFFFFu, val.c, srcl)};
-    if (hi > lo) acc = comp_merge(acc, part);
   }
   if (v < n && deg < small_lim) pr_store(g, v, deg, acc, damping, base, ranks, cn, res, dang);
 }

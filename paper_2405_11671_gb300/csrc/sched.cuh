@@ -21,6 +21,9 @@ constexpr int kHidden = 32;
 // keeps choosing it (no grid barrier between those levels)
 constexpr int kActions = 5;
 constexpr int kActionSolo = 4;
+// The network may choose the single-CTA action only for frontiers this small
+// (in edges); beyond it one CTA cannot beat the grid whatever the network says.
+constexpr uint64_t kSoloMaxEdges = 4096;
 constexpr int kMlpParams = kHidden * kFeatures + kHidden + kHidden * kHidden + kHidden + kActions * kHidden + kActions;
 
 struct SchedParams {
@@ -97,6 +100,7 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
 #pragma unroll
   for (int k = 0; k < kHidden; ++k) h2 = fmaf(__ldg(W2 + lane * kHidden + k), __shfl_sync(0xFFFFFFFFu, h1, k), h2);
   h2 = fmaxf(h2, 0.0f);
+  const bool solo_ok = f.mf <= kSoloMaxEdges;
   int best = 0;
   float bestz = 0.0f;
 #pragma unroll
@@ -105,7 +109,7 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
     float z = t + __ldg(b3 + c);
-    if (c == 0 || z > bestz) {
+    if ((c == 0 || z > bestz) && (c != kActionSolo || solo_ok)) {
       bestz = z;
       best = c;
     }

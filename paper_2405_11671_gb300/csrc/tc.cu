@@ -4,10 +4,12 @@
 // Filter: each edge is kept once, from the endpoint of lower rank, where
 // rank(v) = (degree(v), v) in lexicographic order; N+(v) stays sorted by id.
 // Count: the number of triangles is the sum over DAG edges u->v of
-// |N+(u) intersect N+(v)|.  For every u, N+(u) is staged in shared memory by a
-// TMA bulk copy (cp.async.bulk, completion on an mbarrier; no multicast), then
-// the ids of N+(v) for all v in N+(u) are walked 32 at a time by a warp
-// (edge-balanced across the warp) and looked up in shared memory.  u with |N+(u)| <= kLightMax: one warp each; the staged N+(u) is
+// |N+(u) intersect N+(v)|.  Each edge is intersected from the side with the
+// shorter out-list: N+(c) of a "centre" c is staged in shared memory by a TMA
+// bulk copy (cp.async.bulk, completion on an mbarrier; no multicast) and
+// hashed there, and the out-lists of its partners (out-neighbours p with
+// d+(p) <= d+(c), in-neighbours p with d+(p) < d+(c)) are walked 32 ids at a
+// time by a warp (edge-balanced across the warp) and probed.  u with |N+(u)| <= kLightMax: one warp each; the staged N+(u) is
 // loaded into an open-addressing hash set in the warp's shared memory and each
 // id of N+(v) costs one or two probes.  Larger u: one CTA each (taken from a
 // work counter), N+(u) staged in windows of kWindow ids, each hashed the same
@@ -38,13 +40,17 @@ static uint32_t env_cap(const char* name, uint32_t cap) {
 
 struct TcWork {
   uint32_t n = 0;
-  uint64_t half_cap = 0;        // capacity of dag_col (undirected edges)
-  uint64_t* dag_off = nullptr;  // n + 1
-  uint32_t* dag_col = nullptr;  // m/2 + 8
+  uint64_t half_cap = 0;        // capacity of dag_col / in_col (undirected edges)
+  uint64_t* dag_off = nullptr;  // n + 1: N+ offsets
+  uint32_t* dag_col = nullptr;  // half_cap + 8
+  uint64_t* in_off = nullptr;   // n + 1: N- offsets
+  uint32_t* in_col = nullptr;   // half_cap + 8
   uint32_t* outdeg = nullptr;   // n
-  uint32_t* light = nullptr;    // n
-  uint32_t* heavy = nullptr;    // n
-  uint32_t* ctr = nullptr;      // [0] light count, [1] heavy count, [2] light cursor, [3] error, [4] heavy cursor
+  uint32_t* cnt_l = nullptr;    // n: in-degrees, then light task counts
+  uint32_t* cnt_h = nullptr;    // n: heavy task counts
+  uint64_t* pos_l = nullptr;    // n + 1
+  uint64_t* pos_h = nullptr;    // n + 1
+  uint32_t* ctr = nullptr;      // [2] light cursor, [3] error, [4] heavy cursor
   unsigned long long* count = nullptr;
 };
 
@@ -52,9 +58,13 @@ void tc_free(TcWork* w) {
   if (!w) return;
   dev_free(w->dag_off);
   dev_free(w->dag_col);
+  dev_free(w->in_off);
+  dev_free(w->in_col);
   dev_free(w->outdeg);
-  dev_free(w->light);
-  dev_free(w->heavy);
+  dev_free(w->cnt_l);
+  dev_free(w->cnt_h);
+  dev_free(w->pos_l);
+  dev_free(w->pos_h);
   dev_free(w->ctr);
   dev_free(w->count);
   delete w;
@@ -153,57 +163,71 @@ __global__ void __launch_bounds__(kTcThreads) tc_outdeg_kernel(G g, VBins bins, 
   }
 }
 
+// N+(v) (higher-rank neighbours) into dag_col and N-(v) (lower-rank ones)
+// into in_col, both in stored (ascending id) order: one pass over the list.
 template <typename G>
 __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, const uint64_t* __restrict__ dag_off,
-                                                             uint32_t* __restrict__ dag_col) {
+                                                             uint32_t* __restrict__ dag_col,
+                                                             const uint64_t* __restrict__ in_off,
+                                                             uint32_t* __restrict__ in_col) {
   VRange r = vbins_range(bins);
   const uint32_t lane = lane_id();
   if (r.role == kRoleThread) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
-      uint64_t o = dag_off[v];
+      uint64_t o = dag_off[v], q = in_off[v];
       for (uint32_t k = 0; k < s.len; ++k) {
         uint32_t u = __ldg(s.p + k);
         if (rank_lt(g, v, s.len, u)) dag_col[o++] = u;
+        else in_col[q++] = u;
       }
     }
   } else if (r.role == kRoleWarp) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
-      uint64_t o = dag_off[v];
+      uint64_t o = dag_off[v], q = in_off[v];
       for (uint32_t base = 0; base < s.len; base += 32) {
         uint32_t k = base + lane;
         uint32_t u = k < s.len ? __ldg(s.p + k) : 0;
         bool keep = k < s.len && rank_lt(g, v, s.len, u);
-        uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        bool back = k < s.len && !keep;
+        uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep), bbk = __ballot_sync(0xFFFFFFFFu, back);
         if (keep) dag_col[o + __popc(bal & lanemask_lt())] = u;
+        if (back) in_col[q + __popc(bbk & lanemask_lt())] = u;
         o += __popc(bal);
+        q += __popc(bbk);
       }
     }
   } else {
-    __shared__ uint32_t wcnt[kTcThreads / 32];
-    __shared__ uint32_t wpre[kTcThreads / 32 + 1];
+    __shared__ uint32_t wcnt[2][kTcThreads / 32];
+    __shared__ uint32_t wpre[2][kTcThreads / 32 + 1];
     const uint32_t nw = blockDim.x >> 5, w = threadIdx.x >> 5;
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
-      uint64_t o = dag_off[v];
+      uint64_t o = dag_off[v], q = in_off[v];
       for (uint32_t base = 0; base < s.len; base += blockDim.x) {
         uint32_t k = base + threadIdx.x;
         uint32_t u = k < s.len ? __ldg(s.p + k) : 0;
         bool keep = k < s.len && rank_lt(g, v, s.len, u);
-        uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-        if (lane == 0) wcnt[w] = __popc(bal);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          wpre[0] = 0;
-          for (uint32_t j = 0; j < nw; ++j) wpre[j + 1] = wpre[j] + wcnt[j];
+        bool back = k < s.len && !keep;
+        uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep), bbk = __ballot_sync(0xFFFFFFFFu, back);
+        if (lane == 0) {
+          wcnt[0][w] = __popc(bal);
+          wcnt[1][w] = __popc(bbk);
         }
         __syncthreads();
-        if (keep) dag_col[o + wpre[w] + __popc(bal & lanemask_lt())] = u;
-        o += wpre[nw];
+        if (threadIdx.x < 2) {
+          wpre[threadIdx.x][0] = 0;
+          for (uint32_t j = 0; j < nw; ++j) wpre[threadIdx.x][j + 1] = wpre[threadIdx.x][j] + wcnt[threadIdx.x][j];
+        }
+        __syncthreads();
+        if (keep) dag_col[o + wpre[0][w] + __popc(bal & lanemask_lt())] = u;
+        if (back) in_col[q + wpre[1][w] + __popc(bbk & lanemask_lt())] = u;
+        o += wpre[0][nw];
+        q += wpre[1][nw];
         __syncthreads();
       }
     }
@@ -212,28 +236,57 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
 
 __global__ void tc_set_last_kernel(uint64_t* dag_off, uint32_t n, uint64_t total) { dag_off[n] = total; }
 
-__global__ void tc_classify_kernel(const uint64_t* __restrict__ dag_off, uint32_t n, uint32_t light_max,
-                                   uint32_t* light, uint32_t* heavy, uint32_t* ctr) {
-  const uint32_t lane = lane_id();
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t u = base + threadIdx.x;
-    uint64_t od = u < n ? dag_off[u + 1] - dag_off[u] : 0;
-    bool l = od >= 2 && od <= light_max;
-    bool h = od > light_max;
-    uint32_t bl = __ballot_sync(0xFFFFFFFFu, l), bh = __ballot_sync(0xFFFFFFFFu, h);
-    uint32_t pl = 0, ph = 0;
-    if (lane == 0 && bl) pl = atomicAdd(ctr + 0, __popc(bl));
-    if (lane == 0 && bh) ph = atomicAdd(ctr + 1, __popc(bh));
-    pl = __shfl_sync(0xFFFFFFFFu, pl, 0);
-    ph = __shfl_sync(0xFFFFFFFFu, ph, 0);
-    if (l) light[pl + __popc(bl & lanemask_lt())] = (uint32_t)u;
-    if (h) heavy[ph + __popc(bh & lanemask_lt())] = (uint32_t)u;
+// in-degree in the DAG = degree - out-degree
+template <typename G>
+__global__ void tc_indeg_kernel(G g, const uint32_t* __restrict__ outdeg, uint32_t* indeg) {
+  const uint32_t n = g.num_vertices();
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+    indeg[v] = g.degree((uint32_t)v) - outdeg[v];
+}
+
+// Work items.  Every DAG edge a->b is intersected from the side with the
+// shorter out-list: at centre a (walk N+(b), probe N+(a)) when d+(b) <= d+(a),
+// else at centre b (walk N+(a), probe N+(b)).  A task is one centre c (whose
+// N+(c) is hashed) and a chunk of at most kPartners partners: kind 0 takes
+// partners from N+(c), kind 1 from N-(c).  Tasks of centres with d+(c) <=
+// light_max go to the warp kernel, the others to the CTA kernel.
+constexpr uint32_t kPartners = 512;
+
+struct TcTask {
+  uint32_t c, kind, lo, hi;
+};
+
+__device__ __forceinline__ uint32_t chunks(uint32_t len) { return (len + kPartners - 1) / kPartners; }
+
+__global__ void tc_task_count_kernel(const uint64_t* __restrict__ dag_off, const uint64_t* __restrict__ in_off,
+                                     uint32_t n, uint32_t light_max, uint32_t* cnt_light, uint32_t* cnt_heavy) {
+  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t dp = (uint32_t)(dag_off[c + 1] - dag_off[c]);
+    uint32_t dm = (uint32_t)(in_off[c + 1] - in_off[c]);
+    uint32_t t = (dp >= 2 ? chunks(dp) : 0) + (dp >= 1 ? chunks(dm) : 0);
+    cnt_light[c] = dp <= light_max ? t : 0;
+    cnt_heavy[c] = dp <= light_max ? 0 : t;
+  }
+}
+
+__global__ void tc_task_fill_kernel(const uint64_t* __restrict__ dag_off, const uint64_t* __restrict__ in_off,
+                                    uint32_t n, uint32_t light_max, const uint64_t* __restrict__ pos_light,
+                                    const uint64_t* __restrict__ pos_heavy, TcTask* light, TcTask* heavy) {
+  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t dp = (uint32_t)(dag_off[c + 1] - dag_off[c]);
+    uint32_t dm = (uint32_t)(in_off[c + 1] - in_off[c]);
+    TcTask* out = dp <= light_max ? light + pos_light[c] : heavy + pos_heavy[c];
+    if (dp >= 2)
+      for (uint32_t lo = 0; lo < dp; lo += kPartners) *out++ = TcTask{(uint32_t)c, 0u, lo, min(dp, lo + kPartners)};
+    if (dp >= 1)
+      for (uint32_t lo = 0; lo < dm; lo += kPartners) *out++ = TcTask{(uint32_t)c, 1u, lo, min(dm, lo + kPartners)};
   }
 }
 
 // ---------------------------------------------------------------- intersect
 // Open-addressing hash set in shared memory (linear probing, empty = INF,
-// multiplicative hashing); the table has at least twice as many slots as keys.
+// multiplicative hashing); the table has at least twice (warp kernel: four
+// times) as many slots as keys, so that most absent ids cost one probe.
 struct SmemHash {
   const uint32_t* t;
   uint32_t mask, shift;
@@ -249,19 +302,13 @@ struct SmemHash {
 };
 
 
-// The warp walks the concatenation of N+(v) for the 32 (or fewer) v held by
-// its lanes and counts the ids w in [lo_id, hi_id] that the set contains.
+// The warp walks the concatenation of the lists dag_col[vb .. vb+len) held by
+// its lanes (len = 0 for lanes without a partner) and counts the ids w in
+// [lo_id, hi_id] that the set contains.
 template <typename Set>
-__device__ __forceinline__ uint64_t warp_count_group(const uint64_t* __restrict__ dag_off,
-                                                     const uint32_t* __restrict__ dag_col, uint32_t v, bool has_v,
+__device__ __forceinline__ uint64_t warp_count_group(const uint32_t* __restrict__ dag_col, uint64_t vb, uint32_t len,
                                                      const Set& set, uint32_t lo_id, uint32_t hi_id) {
   const uint32_t lane = lane_id();
-  uint64_t vb = 0;
-  uint32_t len = 0;
-  if (has_v) {
-    vb = dag_off[v];
-    len = (uint32_t)(dag_off[v + 1] - vb);
-  }
   uint32_t incl = len;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -290,69 +337,97 @@ __device__ __forceinline__ uint64_t warp_count_group(const uint64_t* __restrict_
   return hits;
 }
 
+// A lane's partner p: its out-list, kept only on the side that walks the
+// shorter list (kind 0: d+(p) <= d+(c); kind 1: d+(p) < d+(c)).
+__device__ __forceinline__ void partner_list(const uint64_t* __restrict__ dag_off, bool has, uint32_t p, uint32_t kind,
+                                             uint32_t dc, uint64_t* vb, uint32_t* len) {
+  *vb = 0;
+  *len = 0;
+  if (!has) return;
+  uint64_t b = dag_off[p];
+  uint32_t d = (uint32_t)(dag_off[p + 1] - b);
+  if (kind == 0 ? d <= dc : d < dc) {
+    *vb = b;
+    *len = d;
+  }
+}
+
 constexpr uint32_t kSlice = kLightMax + 8;  // staged N+(u) (+ alignment slack), ids
-constexpr uint32_t kTable = 2 * kLightMax;   // hash slots per warp
+constexpr uint32_t kTable = 4 * kLightMax;   // hash slots per warp (load factor <= 1/4)
 constexpr size_t kLightSmem = (size_t)(kTcThreads / 32) * (kSlice + kTable) * sizeof(uint32_t);
 
 __global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __restrict__ dag_off,
                                                               const uint32_t* __restrict__ dag_col,
-                                                              const uint32_t* __restrict__ light, uint32_t* ctr,
-                                                              unsigned long long* count, uint64_t limit_ns) {
+                                                              const uint64_t* __restrict__ in_off,
+                                                              const uint32_t* __restrict__ in_col,
+                                                              const TcTask* __restrict__ tasks, uint64_t ntasks,
+                                                              uint32_t* ctr, unsigned long long* count,
+                                                              uint64_t limit_ns) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ __align__(8) uint64_t bar[kTcThreads / 32];
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   uint32_t* buf = smem + (size_t)w * (kSlice + kTable);
   uint32_t* table = buf + kSlice;
-  const uint32_t nlight = __ldcg(ctr + 0);
   uint32_t* err = ctr + 3;
   if (lane == 0) mbar_init(&bar[w], 1);
   __syncwarp();
   uint32_t phase = 0;
+  uint32_t have = kInf;  // centre whose N+ is staged and hashed in this warp's slice
+  uint32_t head = 0, dc = 0, bits = 5;
   uint64_t hits = 0;
   while (true) {
     uint32_t idx = 0;
     if (lane == 0) idx = atomicAdd(ctr + 2, 1u);
     idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
-    if (idx >= nlight) break;
-    uint32_t u = __ldg(light + idx);
-    uint64_t beg = dag_off[u], end = dag_off[u + 1];
-    uint64_t a0 = beg & ~3ull, a1 = (end + 3) & ~3ull;
-    uint32_t head = (uint32_t)(beg - a0), len = (uint32_t)(end - beg);
-    __syncwarp();  // every lane is done with the previous u's slice and table
-    bool ok = true;
-    if (lane == 0) {
-      bulk_load(buf, dag_col + a0, (uint32_t)((a1 - a0) * 4), &bar[w]);
-      ok = mbar_wait(&bar[w], phase, err, limit_ns);
+    if (idx >= ntasks) break;
+    const TcTask t = tasks[idx];
+    const uint32_t c = t.c;
+    if (c != have) {
+      uint64_t beg = dag_off[c], end = dag_off[c + 1];
+      uint64_t a0 = beg & ~3ull, a1 = (end + 3) & ~3ull;
+      head = (uint32_t)(beg - a0);
+      dc = (uint32_t)(end - beg);
+      __syncwarp();  // every lane is done with the previous slice and table
+      bool ok = true;
+      if (lane == 0) {
+        bulk_load(buf, dag_col + a0, (uint32_t)((a1 - a0) * 4), &bar[w]);
+        ok = mbar_wait(&bar[w], phase, err, limit_ns);
+      }
+      if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) return;
+      mbar_wait(&bar[w], phase, err, limit_ns);  // completed: every lane observes the phase
+      phase ^= 1;
+      // hash set of N+(c): 2^bits >= 4 d+(c) slots (few probes for absent ids)
+      bits = 32 - __clz(4 * dc - 1);
+      if (bits < 5) bits = 5;
+      const uint32_t slots = 1u << bits;
+      for (uint32_t i = lane; i < slots; i += 32) table[i] = kInf;
+      __syncwarp();
+      for (uint32_t k = lane; k < dc; k += 32) {
+        uint32_t x = buf[head + k];
+        uint32_t h = (x * 0x9E3779B1u) >> (32 - bits);
+        while (atomicCAS(table + h, kInf, x) != kInf) h = (h + 1) & (slots - 1);
+      }
+      __syncwarp();
+      have = c;
     }
-    if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) return;
-    mbar_wait(&bar[w], phase, err, limit_ns);  // completed: every lane observes the phase
-    phase ^= 1;
     const uint32_t* list = buf + head;
-    // hash set of N+(u): 2^b >= 2 len slots
-    uint32_t bits = 32 - __clz(2 * len - 1);
-    if (bits < 5) bits = 5;
-    const uint32_t slots = 1u << bits;
-    for (uint32_t i = lane; i < slots; i += 32) table[i] = kInf;
-    __syncwarp();
-    for (uint32_t k = lane; k < len; k += 32) {
-      uint32_t x = list[k];
-      uint32_t h = (x * 0x9E3779B1u) >> (32 - bits);
-      while (atomicCAS(table + h, kInf, x) != kInf) h = (h + 1) & (slots - 1);
-    }
-    __syncwarp();
-    SmemHash set{table, slots - 1, 32 - bits};
-    const uint32_t lo_id = list[0], hi_id = list[len - 1];
-    for (uint32_t k0 = 0; k0 < len; k0 += 32) {
+    SmemHash set{table, (1u << bits) - 1, 32 - bits};
+    const uint32_t lo_id = list[0], hi_id = list[dc - 1];
+    const uint32_t* partners = t.kind == 0 ? list : in_col + in_off[c];
+    for (uint32_t k0 = t.lo; k0 < t.hi; k0 += 32) {
       uint32_t k = k0 + lane;
-      bool has = k < len;
-      uint32_t v = has ? list[k] : 0;
-      hits += warp_count_group(dag_off, dag_col, v, has, set, lo_id, hi_id);
+      bool has = k < t.hi;
+      uint32_t p = has ? partners[k] : 0;
+      uint64_t vb;
+      uint32_t len;
+      partner_list(dag_off, has, p, t.kind, dc, &vb, &len);
+      hits += warp_count_group(dag_col, vb, len, set, lo_id, hi_id);
     }
   }
-  uint64_t t = hits;
+  uint64_t sum = hits;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, o);
-  if (lane == 0 && t) atomicAdd(count, (unsigned long long)t);
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+  if (lane == 0 && sum) atomicAdd(count, (unsigned long long)sum);
 }
 
 constexpr uint32_t kHeavyTable = 2 * kWindow;
@@ -360,16 +435,17 @@ constexpr size_t kHeavySmem = (size_t)(kWindow + 8 + kHeavyTable) * sizeof(uint3
 
 __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __restrict__ dag_off,
                                                               const uint32_t* __restrict__ dag_col,
-                                                              const uint32_t* __restrict__ heavy, uint32_t* ctr,
-                                                              unsigned long long* count, uint32_t window,
-                                                              uint64_t limit_ns) {
+                                                              const uint64_t* __restrict__ in_off,
+                                                              const uint32_t* __restrict__ in_col,
+                                                              const TcTask* __restrict__ tasks, uint64_t ntasks,
+                                                              uint32_t* ctr, unsigned long long* count,
+                                                              uint32_t window, uint64_t limit_ns) {
   extern __shared__ __align__(16) uint32_t win[];
   uint32_t* table = win + kWindow + 8;
   __shared__ __align__(8) uint64_t bar;
   __shared__ bool ok_s;
   __shared__ uint32_t idx_s;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t nheavy = __ldcg(ctr + 1);
   uint32_t* err = ctr + 3;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
@@ -379,9 +455,12 @@ __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __
     if (threadIdx.x == 0) idx_s = atomicAdd(ctr + 4, 1u);
     __syncthreads();
     const uint32_t idx = idx_s;
-    if (idx >= nheavy) break;
-    uint32_t u = __ldg(heavy + idx);
-    uint64_t beg = dag_off[u], end = dag_off[u + 1];
+    if (idx >= ntasks) break;
+    const TcTask t = tasks[idx];
+    const uint32_t c = t.c;
+    const uint64_t beg = dag_off[c], end = dag_off[c + 1];
+    const uint32_t dc = (uint32_t)(end - beg);
+    const uint32_t* partners = t.kind == 0 ? dag_col + beg : in_col + in_off[c];
     for (uint64_t wb = beg; wb < end; wb += window) {
       uint64_t we = wb + window < end ? wb + window : end;
       uint64_t a0 = wb & ~3ull, a1 = (we + 3) & ~3ull;
@@ -408,19 +487,22 @@ __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __
       }
       __syncthreads();
       SmemHash set{table, slots - 1, 32 - bits};
-      uint32_t lo_id = list[0], hi_id = list[wlen - 1];
-      for (uint64_t k0 = beg + (uint64_t)w * 32; k0 < end; k0 += (uint64_t)nw * 32) {
-        uint64_t k = k0 + lane;
-        bool has = k < end;
-        uint32_t v = has ? __ldg(dag_col + k) : 0;
-        hits += warp_count_group(dag_off, dag_col, v, has, set, lo_id, hi_id);
+      const uint32_t lo_id = list[0], hi_id = list[wlen - 1];
+      for (uint32_t k0 = t.lo + w * 32; k0 < t.hi; k0 += nw * 32) {
+        uint32_t k = k0 + lane;
+        bool has = k < t.hi;
+        uint32_t p = has ? __ldg(partners + k) : 0;
+        uint64_t vb;
+        uint32_t len;
+        partner_list(dag_off, has, p, t.kind, dc, &vb, &len);
+        hits += warp_count_group(dag_col, vb, len, set, lo_id, hi_id);
       }
     }
   }
-  uint64_t t = hits;
+  uint64_t sum = hits;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, o);
-  if (lane == 0 && t) atomicAdd(count, (unsigned long long)t);
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+  if (lane == 0 && sum) atomicAdd(count, (unsigned long long)sum);
 }
 
 byo_status ensure_tc_work(byo_graph* g) {
@@ -438,9 +520,13 @@ byo_status ensure_tc_work(byo_graph* g) {
   w->half_cap = g->m / 2 + (g->dyn ? g->m / 8 : 0);  // headroom for later inserts
   byo_status st = dev_alloc_t(&w->dag_off, g->n + 1ull, "TC DAG offsets");
   if (st == BYO_OK) st = dev_alloc_t(&w->dag_col, w->half_cap + 8, "TC DAG neighbours");
+  if (st == BYO_OK) st = dev_alloc_t(&w->in_off, g->n + 1ull, "TC DAG in-offsets");
+  if (st == BYO_OK) st = dev_alloc_t(&w->in_col, w->half_cap + 8, "TC DAG in-neighbours");
   if (st == BYO_OK) st = dev_alloc_t(&w->outdeg, g->n, "TC out-degrees");
-  if (st == BYO_OK) st = dev_alloc_t(&w->light, g->n, "TC light list");
-  if (st == BYO_OK) st = dev_alloc_t(&w->heavy, g->n, "TC heavy list");
+  if (st == BYO_OK) st = dev_alloc_t(&w->cnt_l, g->n, "TC task counts");
+  if (st == BYO_OK) st = dev_alloc_t(&w->cnt_h, g->n, "TC task counts");
+  if (st == BYO_OK) st = dev_alloc_t(&w->pos_l, g->n + 1ull, "TC task offsets");
+  if (st == BYO_OK) st = dev_alloc_t(&w->pos_h, g->n + 1ull, "TC task offsets");
   if (st == BYO_OK) st = dev_alloc_t(&w->ctr, 8, "TC counters");
   if (st == BYO_OK) st = dev_alloc_t(&w->count, 1, "TC count");
   if (st == BYO_OK) {
@@ -459,50 +545,87 @@ template <typename G>
 byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, cudaStream_t s) {
   BYO_RETURN_IF(ensure_tc_work(g));
   TcWork* w = g->tc;
+  const uint32_t n = g->n;
+  const uint64_t half = g->m / 2;
   VBins bins = make_vbins(g, 4, 10, kTcThreads);
   {
     ProfScope ps("tc_outdeg", s);
-    tc_outdeg_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->outdeg); ::byo::note_launch();
+    tc_outdeg_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->outdeg);
+    ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_outdeg_kernel");
-  BYO_RETURN_IF(scan_u32_to_u64(w->outdeg, w->dag_off, g->n, nullptr, s));
-  tc_set_last_kernel<<<1, 1, 0, s>>>(w->dag_off, g->n, g->m / 2); ::byo::note_launch();
-  BYO_CHECK_LAUNCH("tc_set_last_kernel");
+  BYO_RETURN_IF(scan_u32_to_u64(w->outdeg, w->dag_off, n, nullptr, s));
+  tc_set_last_kernel<<<1, 1, 0, s>>>(w->dag_off, n, half);
+  tc_indeg_kernel<<<grid_for(n, 256), 256, 0, s>>>(view, w->outdeg, w->cnt_l);
+  ::byo::note_launch(2);
+  BYO_CHECK_LAUNCH("tc_indeg_kernel");
+  BYO_RETURN_IF(scan_u32_to_u64(w->cnt_l, w->in_off, n, nullptr, s));
+  tc_set_last_kernel<<<1, 1, 0, s>>>(w->in_off, n, half);
+  ::byo::note_launch();
   {
     ProfScope ps("tc_fill", s);
-    tc_fill_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->dag_off, w->dag_col); ::byo::note_launch();
+    tc_fill_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->dag_off, w->dag_col, w->in_off, w->in_col);
+    ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_fill_kernel");
-  BYO_CUDA(cudaMemsetAsync(w->ctr, 0, 8 * sizeof(uint32_t), s));
-  BYO_CUDA(cudaMemsetAsync(w->count, 0, sizeof(unsigned long long), s));
-  unsigned grid = (unsigned)sm_count() * 4;
-  tc_classify_kernel<<<grid, 256, 0, s>>>(w->dag_off, g->n, env_cap("BYO_TC_LIGHT_MAX", kLightMax), w->light,
-                                          w->heavy, w->ctr); ::byo::note_launch();
-  BYO_CHECK_LAUNCH("tc_classify_kernel");
-  uint64_t limit = timeout_ns();
-  int per_sm = 0;
-  BYO_CUDA(cudaFuncSetAttribute(tc_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLightSmem));
-  BYO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_light_kernel, kTcThreads, kLightSmem));
-  {
-    ProfScope ps("tc_light", s);
-    tc_light_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kLightSmem, s>>>(
-      w->dag_off, w->dag_col, w->light, w->ctr, w->count, limit); ::byo::note_launch();
+  // tasks
+  const uint32_t light_max = env_cap("BYO_TC_LIGHT_MAX", kLightMax);
+  tc_task_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, n, light_max, w->cnt_l, w->cnt_h);
+  ::byo::note_launch();
+  BYO_CHECK_LAUNCH("tc_task_count_kernel");
+  uint64_t nl = 0, nh = 0;
+  BYO_RETURN_IF(scan_u32_to_u64(w->cnt_l, w->pos_l, n, &nl, s));
+  BYO_RETURN_IF(scan_u32_to_u64(w->cnt_h, w->pos_h, n, &nh, s));
+  TcTask *tl = nullptr, *th = nullptr;
+  byo_status st = tmp_alloc_t(&tl, nl + 1, s, "TC light tasks");
+  if (st == BYO_OK) st = tmp_alloc_t(&th, nh + 1, s, "TC heavy tasks");
+  if (st == BYO_OK) {
+    tc_task_fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, n, light_max, w->pos_l, w->pos_h, tl,
+                                                         th);
+    ::byo::note_launch();
+    cudaMemsetAsync(w->ctr, 0, 8 * sizeof(uint32_t), s);
+    cudaMemsetAsync(w->count, 0, sizeof(unsigned long long), s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_status(e, "tc_task_fill_kernel");
   }
-  BYO_CHECK_LAUNCH("tc_light_kernel");
-  size_t dyn = kHeavySmem;
-  BYO_CUDA(cudaFuncSetAttribute(tc_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-  {
-    ProfScope ps("tc_heavy", s);
-    tc_heavy_kernel<<<(unsigned)sm_count() * 2, kTcThreads, dyn, s>>>(w->dag_off, w->dag_col, w->heavy, w->ctr,
-                                                                    w->count, env_cap("BYO_TC_WINDOW", kWindow),
-                                                                    limit); ::byo::note_launch();
+  const uint64_t limit = timeout_ns();
+  if (st == BYO_OK && nl) {
+    int per_sm = 0;
+    cudaError_t e = cudaFuncSetAttribute(tc_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLightSmem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_light_kernel, kTcThreads, kLightSmem);
+    if (e == cudaSuccess) {
+      ProfScope ps("tc_light", s);
+      tc_light_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kLightSmem, s>>>(
+          w->dag_off, w->dag_col, w->in_off, w->in_col, tl, nl, w->ctr, w->count, limit);
+      ::byo::note_launch();
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = cuda_status(e, "tc_light_kernel");
   }
-  BYO_CHECK_LAUNCH("tc_heavy_kernel");
+  if (st == BYO_OK && nh) {
+    cudaError_t e = cudaFuncSetAttribute(tc_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeavySmem);
+    if (e == cudaSuccess) {
+      ProfScope ps("tc_heavy", s);
+      tc_heavy_kernel<<<(unsigned)sm_count() * 2, kTcThreads, kHeavySmem, s>>>(
+          w->dag_off, w->dag_col, w->in_off, w->in_col, th, nh, w->ctr, w->count, env_cap("BYO_TC_WINDOW", kWindow),
+          limit);
+      ::byo::note_launch();
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = cuda_status(e, "tc_heavy_kernel");
+  }
   uint32_t err = 0;
   unsigned long long c = 0;
-  BYO_CUDA(cudaMemcpyAsync(&c, w->count, sizeof(c), cudaMemcpyDeviceToHost, s));
-  BYO_CUDA(cudaMemcpyAsync(&err, w->ctr + 3, sizeof(err), cudaMemcpyDeviceToHost, s));
-  BYO_CUDA(cudaStreamSynchronize(s));
+  if (st == BYO_OK) {
+    cudaError_t e = cudaMemcpyAsync(&c, w->count, sizeof(c), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, w->ctr + 3, sizeof(err), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "byo_tc");
+  }
+  tmp_free(tl, s);
+  tmp_free(th, s);
+  BYO_RETURN_IF(st);
   if (err) {
     set_error("byo_tc: a TMA completion wait exceeded BYO_TIMEOUT_MS");
     return BYO_ERR_TIMEOUT;

@@ -71,11 +71,12 @@ def forced_sched(byo, action: int):
 def time_actions(byo, g, sources, repeats: int = 2):
     """Per-iteration device times of every forced action for each source.
 
-    Returns a list of (features [L, 12], times [L, NUM_ACTIONS] in ns)."""
+    Returns a list of (features [L, 12], times [L, NUM_ACTIONS] in ns,
+    frontier edges [L])."""
     n, m = byo.byo_num_vertices(g), byo.byo_num_edges(g)
     out = []
     for s in sources:
-        feats, times = None, []
+        feats, times, mf = None, [], None
         for a in range(NUM_ACTIONS):
             sp = forced_sched(byo, a)
             best = None
@@ -86,23 +87,36 @@ def time_actions(byo, g, sources, repeats: int = 2):
                 best = t if best is None else np.minimum(best, t)
                 if feats is None:
                     feats = trace_features(tr, n, m)
+                    mf = np.array([r.frontier_edges for r in tr], np.float64)
             times.append(best)
-        out.append((feats, np.stack(times, axis=1)))
+        out.append((feats, np.stack(times, axis=1), mf))
     return out
 
 
+def allowed(feats_row, t_row, mf):
+    """Per-level times with the single-CTA action masked where the device
+    would not let the network take it."""
+    t = np.array(t_row, np.float64)
+    if mf > SOLO_MAX_EDGES:
+        t[4] = np.inf
+    return t
+
+
 def samples_from_timings(tables):
-    """Labels = fastest action per iteration; weight = worst-case loss of that
-    iteration relative to the traversal's best total time."""
+    """Labels = fastest allowed action per iteration; weight = worst-case loss
+    of that iteration (over allowed actions) relative to the traversal's best
+    total time."""
     X, y, w = [], [], []
-    for feats, t in tables:
+    for feats, t, mf in tables:
         if len(t) == 0:
             continue
+        t = np.stack([allowed(feats[i], t[i], mf[i]) for i in range(len(t))])
         best_total = float(t.min(axis=1).sum()) or 1.0
         for i in range(len(t)):
             X.append(feats[i])
             y.append(int(np.argmin(t[i])))
-            w.append(float((t[i].max() - t[i].min()) / best_total) + 1e-3)
+            fin = t[i][np.isfinite(t[i])]
+            w.append(float((fin.max() - fin.min()) / best_total) + 1e-3)
     return (np.array(X, np.float32).reshape(-1, NUM_FEATURES), np.array(y, np.int32), np.array(w, np.float32))
 
 
@@ -112,16 +126,19 @@ def regret(t, choices) -> float:
     return float(sum(t[i, c] - t[i].min() for i, c in enumerate(choices)))
 
 
+SOLO_MAX_EDGES = 4096  # the device only lets the network pick action 4 below this
+
+
 def training_graphs(seed: int = 0xB10 + 50):
     """Generated graphs of the three shapes at several sizes (never the benchmark graphs)."""
     import graphgen
     out = []
-    for sc in (14, 16, 18, 19):
+    for sc in (14, 16, 18, 20, 21):
         out.append(("rmat%d" % sc, *graphgen.rmat_small(sc, 16, graphgen.stream(seed, sc))))
-    for sc, deg in ((15, 8), (17, 16), (18, 32)):
+    for sc, deg in ((15, 8), (17, 16), (19, 32)):
         n = 1 << sc
         out.append(("er%d" % sc, n, *graphgen.er(n, n * deg // 2, graphgen.stream(seed, 100 + sc))))
-    for side in (256, 512, 1024):
+    for side in (256, 512, 1024, 2048):
         out.append(("grid%d" % side, *graphgen.grid_small(side, side, 0.1, 1e-4, graphgen.stream(seed, side))))
     return out
 
@@ -179,8 +196,8 @@ def main(argv=None):
     m, loss = train(byo, X, y, w, epochs=args.epochs)
     import torch
     pred = byo.byo_mlp_predict(m, torch.from_numpy(X).cuda()).cpu().numpy()
-    r_learned = sum(regret(t, pred[o:o + len(t)]) for o, (_, t) in zip(np.cumsum([0] + [len(t) for _, t in tables]),
-                                                                     tables))
+    r_learned = sum(regret(t, pred[o:o + len(t)]) for o, (_, t, _) in zip(np.cumsum([0] + [len(t) for _, t, _ in tables]),
+                                                                        tables))
     save(byo, m, args.out, {"samples": int(len(y)), "loss": loss, "train_regret_ns": r_learned,
                              "label_counts": np.bincount(y, minlength=NUM_ACTIONS).tolist()})
     print(json.dumps({"samples": int(len(y)), "loss": loss, "train_regret_ns": r_learned,
