@@ -239,6 +239,12 @@ byo_status byo_pagerank(const byo_graph* g, float damping, uint32_t iters, float
  */
 byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
 
+/* Runs byo_tc and reports its intersection work (host_work3, host array of 3):
+ * [0] sum_c d+(c)^2 and [1] sum_c d-(c) d+(c) -- together the out-list ids a
+ * merge of both lists of every DAG edge reads -- and [2] the ids this library
+ * walks (sum over DAG edges of the shorter out-list).  Synchronises. */
+byo_status byo_tc_work(const byo_graph* g, uint64_t* host_work3, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Many graphs at once.  byo_batch_build stores num_graphs graphs as one      */
 /* container over their disjoint union: member i owns the global ids          */

@@ -85,6 +85,7 @@ SIGNATURES = [
     ("byo_cc", _st, [_vp, _vp, _vp]),
     ("byo_pagerank", _st, [_vp, ctypes.c_float, _u32, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     ("byo_tc", _st, [_vp, ctypes.POINTER(_u64), _vp]),
+    ("byo_tc_work", _st, [_vp, ctypes.POINTER(_u64), _vp]),
     ("byo_mlp_num_params", _u32, []),
     ("byo_mlp_create", _st, [_u64, ctypes.POINTER(_vp)]),
     ("byo_mlp_destroy", _st, [_vp]),
@@ -279,6 +280,13 @@ def byo_tc(g: int, stream=None) -> int:
     c = _u64()
     _check(load().byo_tc(g, ctypes.byref(c), _stream(stream)))
     return c.value
+
+
+def byo_tc_work(g: int, stream=None):
+    """(sum d+^2, sum d- d+, walked ids) of the triangle-count DAG."""
+    w = (_u64 * 3)()
+    _check(load().byo_tc_work(g, w, _stream(stream)))
+    return int(w[0]), int(w[1]), int(w[2])
 
 
 # ----------------------------------------------------------------------------- schedule network

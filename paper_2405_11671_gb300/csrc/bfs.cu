@@ -465,9 +465,228 @@ __device__ __forceinline__ void level_end(const BfsArgs<G>& a, BfsShared& S, int
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- solo levels
+// While the frontier stays small, block 0 keeps it in shared memory as
+// (list pointer, id, degree) entries and runs level after level without
+// touching the global queue or counters: per level it walks the frontier's
+// concatenated lists, claims neighbours with one atomicOr each on the visited
+// bits, writes level/parent and appends the winners (with their own list
+// location, fetched once) to the next shared-memory list.  That leaves about
+// three dependent memory round trips per level.  If a level's winners do not
+// fit, the excess spills to the global queue and the grid takes over.
+constexpr uint32_t kSoloCap = 1024;
+
+struct SoloEntry {
+  const uint32_t* p;
+  uint32_t v, len;
+};
+
+struct SoloShared {
+  SoloEntry list[2][kSoloCap];
+  uint32_t pre[kSoloCap + 1];
+  uint32_t wsum[kBfsThreads / 32];
+  uint32_t n_next, spilled;
+  unsigned long long mf_next;
+  uint32_t h_next[4];
+  uint32_t h_cur[4];
+};
+
+__device__ __forceinline__ int deg_class(uint32_t d) { return d < 4 ? 0 : (d < 32 ? 1 : (d < 256 ? 2 : 3)); }
+
+// Q.pre[0..cnt] = exclusive prefix of list[i].len (cnt <= kSoloCap); CTA-wide.
+__device__ void solo_prefix(SoloShared& Q, const SoloEntry* list, uint32_t cnt) {
+  constexpr uint32_t kPer = kSoloCap / kBfsThreads;  // 4 entries per thread
+  const uint32_t tid = threadIdx.x, lane = lane_id();
+  uint32_t v[kPer], sum = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kPer; ++j) {
+    uint32_t i = tid * kPer + j;
+    v[j] = i < cnt ? list[i].len : 0;
+    sum += v[j];
+  }
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if ((int)lane >= o) inc += y;
+  }
+  if (lane == 31) Q.wsum[tid >> 5] = inc;
+  __syncthreads();
+  uint32_t off = 0;
+  for (uint32_t w = 0; w < (tid >> 5); ++w) off += Q.wsum[w];
+  uint32_t run = off + inc - sum;
+#pragma unroll
+  for (uint32_t j = 0; j < kPer; ++j) {
+    uint32_t i = tid * kPer + j;
+    if (i < cnt) Q.pre[i] = run;
+    run += v[j];
+  }
+  if (tid == blockDim.x - 1) {
+    uint32_t tot = 0;
+    for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) tot += Q.wsum[w];
+    Q.pre[cnt] = tot;
+  }
+  __syncthreads();
+}
+
+// Block 0 only.  Entry: level L's frontier (|F| <= kSoloCap) is in the global
+// queue described by S.  Exit: the frontier of the returned level is in the
+// global queue again (or the traversal is done), S.base/nvis/mvis describe it.
+template <typename G, bool kParents>
+__device__ void fast_solo(const BfsArgs<G>& a, BfsShared& S, SoloShared& Q, uint32_t& L, bool& done,
+                          uint64_t t_begin) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t n = a.g.num_vertices();
+  const uint64_t m = a.g.num_edges();
+  BfsCtl* ctl = a.ctl;
+  uint32_t cur = 0;
+  uint32_t nA = S.nf;
+  unsigned long long mfA = S.mf;
+  for (uint32_t i = tid; i < nA; i += blockDim.x) {
+    int b = find_bucket(S.pre, 0, kBuckets - 1, i);
+    uint32_t v = frontier_vertex(a, S, b, i - S.pre[b]);
+    Seg sg = a.g.seg(v);
+    Q.list[0][i] = SoloEntry{sg.p, v, sg.len};
+  }
+  __syncthreads();
+  // level L's global entries are consumed: later appends start after them
+  if (tid < (uint32_t)kBuckets) S.base[tid] += S.cnt[tid];
+  if (tid == 0) {
+    Q.h_cur[0] = (uint32_t)S.pre[3];
+    Q.h_cur[1] = (uint32_t)(S.pre[6] - S.pre[3]);
+    Q.h_cur[2] = (uint32_t)(S.pre[9] - S.pre[6]);
+    Q.h_cur[3] = (uint32_t)(S.pre[kBuckets] - S.pre[9]);
+  }
+  done = false;
+  while (true) {
+    const int nx = (L + 1) % 3;
+    const SoloEntry* A = Q.list[cur];
+    SoloEntry* B = Q.list[cur ^ 1];
+    solo_prefix(Q, A, nA);
+    const uint32_t TE = Q.pre[nA];
+    if (tid < (uint32_t)kBuckets) ctl->cnt[nx][tid] = 0;
+    if (tid == 0) {
+      Q.n_next = 0;
+      Q.spilled = 0;
+      Q.mf_next = 0;
+      for (int k = 0; k < 4; ++k) Q.h_next[k] = 0;
+    }
+    __syncthreads();
+    for (uint32_t e = tid; e < TE; e += blockDim.x) {
+      uint32_t lo = 0, hi = nA - 1;  // owner: largest i with pre[i] <= e
+      while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (Q.pre[mid] <= e) lo = mid;
+        else hi = mid - 1;
+      }
+      const SoloEntry u = A[lo];
+      const uint32_t w = __ldg(u.p + (e - Q.pre[lo]));
+      const uint32_t bit = 1u << (w & 31);
+      if (atomicOr(a.vis + (w >> 5), bit) & bit) continue;
+      a.level[w] = L + 1;
+      if (kParents) a.parent[w] = u.v;
+      const Seg sg = a.g.seg(w);
+      const uint32_t slot = atomicAdd(&Q.n_next, 1u);
+      if (slot < kSoloCap) {
+        B[slot] = SoloEntry{sg.p, w, sg.len};
+      } else {
+        const int b = degree_bucket(sg.len);
+        const unsigned long long pos = atomicAdd(&ctl->cnt[nx][b], 1ull);
+        const uint64_t at = S.bstart[b] + S.base[b] + pos;
+        if (at < S.bstart[b + 1]) a.queue[at] = w;
+        else atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is claimed once
+        Q.spilled = 1;
+      }
+      atomicAdd(&Q.mf_next, (unsigned long long)sg.len);
+      atomicAdd(&Q.h_next[deg_class(sg.len)], 1u);
+    }
+    __syncthreads();
+    const uint32_t nB = Q.n_next;
+    const unsigned long long mfB = Q.mf_next;
+    if (tid == 0) {
+      uint64_t now = globaltimer();
+      if (L < kTraceCap) {
+        byo_bfs_iter* r = a.trace + L;
+        r->level = L;
+        r->direction = 1;
+        r->action = (uint32_t)kActionSolo;
+        r->frontier = nA;
+        r->frontier_edges = mfA;
+        r->edges_examined = TE;
+        r->unvisited = (uint32_t)((uint64_t)n - S.nvis - nA);
+        r->unvisited_edges = m - S.mvis - mfA;
+        for (int k = 0; k < 4; ++k) r->hist[k] = Q.h_cur[k];
+        r->reserved = 0;
+        r->t_ns = now - S.t_top;
+      }
+      S.t_top = now;
+      S.nvis += nA;
+      S.mvis += mfA;
+      S.prev_dir = 1;
+      S.dir = 1;
+    }
+    __syncthreads();
+    ++L;
+    S.t_level = L;
+    if (nB == 0) {
+      done = true;
+      return;
+    }
+    bool stay = !Q.spilled && L <= n && globaltimer() - t_begin <= a.limit_ns;
+    if (stay && tid < 32) {
+      SchedFeatures f;
+      f.nf = nB;
+      f.mf = mfB;
+      f.nu = (uint64_t)n - S.nvis - nB;
+      f.mu = m - S.mvis - mfB;
+      f.n = n;
+      f.m = m;
+      for (int k = 0; k < 4; ++k) f.h[k] = Q.h_next[k];
+      int act = sched_decide(a.sp, f, 1);  // warp-collective
+      if (tid == 0) S.action = act;
+    }
+    __syncthreads();
+    if (stay && S.action == kActionSolo) {
+      if (tid < 4) Q.h_cur[tid] = Q.h_next[tid];
+      cur ^= 1;
+      nA = nB;
+      mfA = mfB;
+      continue;
+    }
+    // hand the new frontier (level L) back to the global queue
+    const uint32_t kept = nB < kSoloCap ? nB : kSoloCap;
+    for (uint32_t i = tid; i < kept; i += blockDim.x) {
+      const SoloEntry e = B[i];
+      const int b = degree_bucket(e.len);
+      const unsigned long long pos = atomicAdd(&ctl->cnt[L % 3][b], 1ull);
+      const uint64_t at = S.bstart[b] + S.base[b] + pos;
+      if (at < S.bstart[b + 1]) a.queue[at] = e.v;
+      else atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);
+    }
+    if (tid == 0) {
+      ctl->sdeg[L % 3] = mfB;
+      ctl->scanned[L % 3] = TE;
+    }
+    // the counters of the next two levels start from zero
+    if (tid < (uint32_t)kBuckets) {
+      ctl->cnt[(L + 1) % 3][tid] = 0;
+      ctl->cnt[(L + 2) % 3][tid] = 0;
+    }
+    if (tid == 0) {
+      ctl->sdeg[(L + 1) % 3] = 0;
+      ctl->scanned[(L + 1) % 3] = 0;
+      ctl->sdeg[(L + 2) % 3] = 0;
+      ctl->scanned[(L + 2) % 3] = 0;
+    }
+    __syncthreads();
+    return;
+  }
+}
+
 template <typename G, bool kParents>
 __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
   __shared__ BfsShared S;
+  __shared__ SoloShared Q;
   const uint32_t tid = threadIdx.x;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
   const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
@@ -532,7 +751,20 @@ __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
       // only, while the other CTAs wait at the grid barrier; it stops when the
       // schedule asks for another action or the traversal ends, and hands the
       // level-local state over through the control block.
-      if (owner) {
+      if (owner && S.nf <= kSoloCap) {
+        uint32_t Ls = L;
+        bool done = false;
+        fast_solo<G, kParents>(a, S, Q, Ls, done, t_begin);
+        if (tid == 0) {
+          ctl->solo_L = Ls;
+          ctl->solo_done = done ? 1u : 0u;
+          ctl->solo_nvis = S.nvis;
+          ctl->solo_mvis = S.mvis;
+          ctl->solo_prev = 1u;
+          if (done) ctl->levels = Ls;
+        }
+        if (tid < (uint32_t)kBuckets) ctl->solo_base[tid] = S.base[tid];
+      } else if (owner) {
         uint32_t Ls = L;
         bool done = false;
         while (true) {

@@ -4,8 +4,10 @@
 //   HEURISTIC  Beamer-style switch: push -> pull when the frontier's edges
 //              exceed the unvisited edges / alpha; pull -> push when the
 //              frontier has fewer than n / beta vertices.
-//   LEARNED    a 12 -> 32 -> 32 -> 5 ReLU network over frontier features,
-//              evaluated by one warp of every CTA inside the persistent loop.
+//   LEARNED    the Beamer rule picks the direction; on push levels a
+//              12 -> 32 -> 32 -> 5 ReLU network over the frontier features
+//              picks the push variant (bins or single-CTA), evaluated by one
+//              warp of every CTA inside the persistent loop.
 //   PUSH/PULL  fixed.
 // Schedules never change results, only which kernel path runs.
 #pragma once
@@ -78,10 +80,9 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
   if (sp.mode == BYO_SCHED_FIXED) return sp.fixed_action;
   if (sp.mode == BYO_SCHED_PUSH) return 1;
   if (sp.mode == BYO_SCHED_PULL) return 0;
-  if (sp.mode == BYO_SCHED_HEURISTIC || sp.w == nullptr) {
-    if (prev_dir == 1) return (double)f.mf > (double)f.mu / (double)sp.alpha ? 0 : 1;
-    return (double)f.nf < (double)f.n / (double)sp.beta ? 1 : 0;
-  }
+  const int beamer = prev_dir == 1 ? ((double)f.mf > (double)f.mu / (double)sp.alpha ? 0 : 1)
+                                    : ((double)f.nf < (double)f.n / (double)sp.beta ? 1 : 0);
+  if (sp.mode == BYO_SCHED_HEURISTIC || sp.w == nullptr || beamer == 0) return beamer;
   // LEARNED: lane j owns hidden unit j of both layers
   const uint32_t lane = lane_id();
   float x[kFeatures];
@@ -101,15 +102,15 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
   for (int k = 0; k < kHidden; ++k) h2 = fmaf(__ldg(W2 + lane * kHidden + k), __shfl_sync(0xFFFFFFFFu, h1, k), h2);
   h2 = fmaxf(h2, 0.0f);
   const bool solo_ok = f.mf <= kSoloMaxEdges;
-  int best = 0;
+  int best = 1;
   float bestz = 0.0f;
 #pragma unroll
-  for (int c = 0; c < kActions; ++c) {
+  for (int c = 1; c < kActions; ++c) {  // a push variant: the direction is Beamer's
     float t = __ldg(W3 + c * kHidden + lane) * h2;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
     float z = t + __ldg(b3 + c);
-    if ((c == 0 || z > bestz) && (c != kActionSolo || solo_ok)) {
+    if ((c == 1 || z > bestz) && (c != kActionSolo || solo_ok)) {
       bestz = z;
       best = c;
     }

@@ -24,7 +24,7 @@
 namespace byo {
 
 constexpr uint32_t kLightMax = 256;   // capacity of a warp's shared-memory slice (ids)
-constexpr uint32_t kWindow = 8192;    // capacity of a CTA's shared-memory window (ids)
+constexpr uint32_t kWindow = 4096;    // capacity of a CTA's shared-memory window (ids)
 constexpr int kTcThreads = 256;
 
 // The light/heavy split and the window length can be lowered (never raised)
@@ -52,6 +52,8 @@ struct TcWork {
   uint64_t* pos_h = nullptr;    // n + 1
   uint32_t* ctr = nullptr;      // [2] light cursor, [3] error, [4] heavy cursor
   unsigned long long* count = nullptr;
+  unsigned long long* work = nullptr;  // [0] sum d+(c)^2, [1] sum d-(c) d+(c), [2] sum over edges of the shorter out-list
+  unsigned long long host_work[3] = {0, 0, 0};
 };
 
 void tc_free(TcWork* w) {
@@ -67,6 +69,7 @@ void tc_free(TcWork* w) {
   dev_free(w->pos_h);
   dev_free(w->ctr);
   dev_free(w->count);
+  dev_free(w->work);
   delete w;
 }
 
@@ -257,6 +260,36 @@ struct TcTask {
 };
 
 __device__ __forceinline__ uint32_t chunks(uint32_t len) { return (len + kPartners - 1) / kPartners; }
+
+// Intersection work of the DAG: the out-list lengths every method must read
+// (sum over edges a->b of d+(a) + d+(b) = sum_c d+(c)^2 + d-(c) d+(c)) and the
+// ids this implementation walks (sum over edges of min(d+(a), d+(b))).
+__global__ void tc_work_kernel(const uint64_t* __restrict__ dag_off, const uint64_t* __restrict__ in_off,
+                               const uint32_t* __restrict__ in_col, uint32_t n, unsigned long long* work) {
+  unsigned long long sq = 0, io = 0, mn = 0;
+  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long dp = dag_off[c + 1] - dag_off[c];
+    const uint64_t b = in_off[c], e = in_off[c + 1];
+    sq += dp * dp;
+    io += (e - b) * dp;
+    for (uint64_t i = b; i < e; ++i) {  // in-neighbour a of c: edge a->c
+      const uint32_t a = in_col[i];
+      const unsigned long long da = dag_off[a + 1] - dag_off[a];
+      mn += da < dp ? da : dp;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sq += __shfl_down_sync(0xFFFFFFFFu, sq, o);
+    io += __shfl_down_sync(0xFFFFFFFFu, io, o);
+    mn += __shfl_down_sync(0xFFFFFFFFu, mn, o);
+  }
+  if (lane_id() == 0) {
+    atomicAdd(work + 0, sq);
+    atomicAdd(work + 1, io);
+    atomicAdd(work + 2, mn);
+  }
+}
 
 __global__ void tc_task_count_kernel(const uint64_t* __restrict__ dag_off, const uint64_t* __restrict__ in_off,
                                      uint32_t n, uint32_t light_max, uint32_t* cnt_light, uint32_t* cnt_heavy) {
@@ -529,6 +562,7 @@ byo_status ensure_tc_work(byo_graph* g) {
   if (st == BYO_OK) st = dev_alloc_t(&w->pos_h, g->n + 1ull, "TC task offsets");
   if (st == BYO_OK) st = dev_alloc_t(&w->ctr, 8, "TC counters");
   if (st == BYO_OK) st = dev_alloc_t(&w->count, 1, "TC count");
+  if (st == BYO_OK) st = dev_alloc_t(&w->work, 4, "TC work counters");
   if (st == BYO_OK) {
     cudaError_t e = cudaMemset(w->dag_col, 0, sizeof(uint32_t) * (w->half_cap + 8));
     if (e != cudaSuccess) st = cuda_status(e, "cudaMemset");
@@ -542,7 +576,7 @@ byo_status ensure_tc_work(byo_graph* g) {
 }
 
 template <typename G>
-byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, cudaStream_t s) {
+byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cudaStream_t s) {
   BYO_RETURN_IF(ensure_tc_work(g));
   TcWork* w = g->tc;
   const uint32_t n = g->n;
@@ -568,6 +602,12 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, cudaStream_t s) {
     ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_fill_kernel");
+  if (want_work) {
+    cudaMemsetAsync(w->work, 0, 4 * sizeof(unsigned long long), s);
+    tc_work_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, w->in_col, n, w->work);
+    ::byo::note_launch();
+    BYO_CUDA(cudaMemcpyAsync(w->host_work, w->work, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  }
   // tasks
   const uint32_t light_max = env_cap("BYO_TC_LIGHT_MAX", kLightMax);
   tc_task_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, n, light_max, w->cnt_l, w->cnt_h);
@@ -604,10 +644,13 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, cudaStream_t s) {
     if (e != cudaSuccess) st = cuda_status(e, "tc_light_kernel");
   }
   if (st == BYO_OK && nh) {
+    int per_sm = 0;
     cudaError_t e = cudaFuncSetAttribute(tc_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeavySmem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_heavy_kernel, kTcThreads, kHeavySmem);
     if (e == cudaSuccess) {
       ProfScope ps("tc_heavy", s);
-      tc_heavy_kernel<<<(unsigned)sm_count() * 2, kTcThreads, kHeavySmem, s>>>(
+      tc_heavy_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kHeavySmem, s>>>(
           w->dag_off, w->dag_col, w->in_off, w->in_col, th, nh, w->ctr, w->count, env_cap("BYO_TC_WINDOW", kWindow),
           limit);
       ::byo::note_launch();
@@ -650,5 +693,22 @@ extern "C" byo_status byo_tc(const byo_graph* gc, uint64_t* host_count, void* st
   *host_count = 0;
   if (g->n == 0 || g->m == 0) return BYO_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return with_view(g, [&](auto view) { return run_tc(g, view, host_count, s); });
+  return with_view(g, [&](auto view) { return run_tc(g, view, host_count, false, s); });
+}
+
+extern "C" byo_status byo_tc_work(const byo_graph* gc, uint64_t* host_work3, void* stream) {
+  clear_error();
+  BYO_RETURN_IF(check_graph(gc));
+  if (!host_work3) {
+    set_error("byo_tc_work: NULL output");
+    return BYO_ERR_INVALID_ARG;
+  }
+  byo_graph* g = const_cast<byo_graph*>(gc);
+  host_work3[0] = host_work3[1] = host_work3[2] = 0;
+  if (g->n == 0 || g->m == 0) return BYO_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint64_t count = 0;
+  BYO_RETURN_IF(with_view(g, [&](auto view) { return run_tc(g, view, &count, true, s); }));
+  for (int i = 0; i < 3; ++i) host_work3[i] = g->tc->host_work[i];
+  return BYO_OK;
 }

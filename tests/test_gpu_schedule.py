@@ -57,7 +57,7 @@ def test_learned_schedule_regret(byo, shape):
         heur = byo.make_sched(byo.BYO_SCHED_HEURISTIC)
         learned = byo.make_sched(byo.BYO_SCHED_LEARNED, mlp=net)
         r_h = r_l = best = t_h = t_l = 0.0
-        for s, (_, t, _) in zip(srcs, tables):
+        for s, (_, t, _, _) in zip(srcs, tables):
             lv_h, _ = byo.byo_bfs(g.handle, [s], sched=heur, want_parents=False)
             ch = [r.action for r in byo.byo_bfs_trace(g.handle)]
             lv_l, _ = byo.byo_bfs(g.handle, [s], sched=learned, want_parents=False)
