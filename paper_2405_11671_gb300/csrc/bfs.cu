@@ -572,33 +572,54 @@ __device__ void fast_solo(const BfsArgs<G>& a, BfsShared& S, SoloShared& Q, uint
       for (int k = 0; k < 4; ++k) Q.h_next[k] = 0;
     }
     __syncthreads();
-    for (uint32_t e = tid; e < TE; e += blockDim.x) {
-      uint32_t lo = 0, hi = nA - 1;  // owner: largest i with pre[i] <= e
-      while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (Q.pre[mid] <= e) lo = mid;
-        else hi = mid - 1;
+    // four edges per thread per step: their id loads, then their claims, are
+    // independent, so four memory round trips overlap
+    constexpr uint32_t kU = 4;
+    for (uint32_t e0 = 0; e0 < TE; e0 += kU * blockDim.x) {
+      uint32_t wv[kU], uv[kU];
+      bool ok[kU];
+#pragma unroll
+      for (uint32_t j = 0; j < kU; ++j) {
+        const uint32_t e = e0 + j * blockDim.x + tid;
+        ok[j] = e < TE;
+        wv[j] = 0;
+        uv[j] = 0;
+        if (ok[j]) {
+          uint32_t lo = 0, hi = nA - 1;  // owner: largest i with pre[i] <= e
+          while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) >> 1;
+            if (Q.pre[mid] <= e) lo = mid;
+            else hi = mid - 1;
+          }
+          const SoloEntry u = A[lo];
+          uv[j] = u.v;
+          wv[j] = __ldg(u.p + (e - Q.pre[lo]));
+        }
       }
-      const SoloEntry u = A[lo];
-      const uint32_t w = __ldg(u.p + (e - Q.pre[lo]));
-      const uint32_t bit = 1u << (w & 31);
-      if (atomicOr(a.vis + (w >> 5), bit) & bit) continue;
-      a.level[w] = L + 1;
-      if (kParents) a.parent[w] = u.v;
-      const Seg sg = a.g.seg(w);
-      const uint32_t slot = atomicAdd(&Q.n_next, 1u);
-      if (slot < kSoloCap) {
-        B[slot] = SoloEntry{sg.p, w, sg.len};
-      } else {
-        const int b = degree_bucket(sg.len);
-        const unsigned long long pos = atomicAdd(&ctl->cnt[nx][b], 1ull);
-        const uint64_t at = S.bstart[b] + S.base[b] + pos;
-        if (at < S.bstart[b + 1]) a.queue[at] = w;
-        else atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is claimed once
-        Q.spilled = 1;
+      uint32_t old[kU];
+#pragma unroll
+      for (uint32_t j = 0; j < kU; ++j) old[j] = ok[j] ? atomicOr(a.vis + (wv[j] >> 5), 1u << (wv[j] & 31)) : ~0u;
+#pragma unroll
+      for (uint32_t j = 0; j < kU; ++j) {
+        const uint32_t w = wv[j];
+        if (!ok[j] || (old[j] & (1u << (w & 31)))) continue;
+        a.level[w] = L + 1;
+        if (kParents) a.parent[w] = uv[j];
+        const Seg sg = a.g.seg(w);
+        const uint32_t slot = atomicAdd(&Q.n_next, 1u);
+        if (slot < kSoloCap) {
+          B[slot] = SoloEntry{sg.p, w, sg.len};
+        } else {
+          const int b = degree_bucket(sg.len);
+          const unsigned long long pos = atomicAdd(&ctl->cnt[nx][b], 1ull);
+          const uint64_t at = S.bstart[b] + S.base[b] + pos;
+          if (at < S.bstart[b + 1]) a.queue[at] = w;
+          else atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is claimed once
+          Q.spilled = 1;
+        }
+        atomicAdd(&Q.mf_next, (unsigned long long)sg.len);
+        atomicAdd(&Q.h_next[deg_class(sg.len)], 1u);
       }
-      atomicAdd(&Q.mf_next, (unsigned long long)sg.len);
-      atomicAdd(&Q.h_next[deg_class(sg.len)], 1u);
     }
     __syncthreads();
     const uint32_t nB = Q.n_next;

@@ -25,7 +25,7 @@ constexpr int kActions = 5;
 constexpr int kActionSolo = 4;
 // The network may choose the single-CTA action only for frontiers this small
 // (in edges); beyond it one CTA cannot beat the grid whatever the network says.
-constexpr uint64_t kSoloMaxEdges = 4096;
+constexpr uint64_t kSoloMaxEdges = 16384;
 constexpr int kMlpParams = kHidden * kFeatures + kHidden + kHidden * kHidden + kHidden + kActions * kHidden + kActions;
 
 struct SchedParams {

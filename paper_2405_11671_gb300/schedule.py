@@ -119,8 +119,9 @@ def beamer_pushes(stats, alpha: float = 15.0, beta: float = 18.0):
 
 def samples_from_timings(tables):
     """Samples = levels the Beamer rule pushes; label = fastest allowed push
-    variant; weight = worst-case loss of that level (over the allowed push
-    variants) relative to the traversal's best total time."""
+    variant; weight = log of the worst / best allowed push variant's time on
+    that level (scale-free, so the many short levels of a deep traversal count
+    as much as the few long levels of a shallow one), clipped to [0.01, 3]."""
     X, y, w = [], [], []
     for feats, t, mf, stats in tables:
         if len(t) == 0:
@@ -135,7 +136,7 @@ def samples_from_timings(tables):
             X.append(feats[i])
             y.append(int(np.argmin(t[i])))
             fin = t[i][np.isfinite(t[i])]
-            w.append(float((fin.max() - fin.min()) / best_total) + 1e-3)
+            w.append(float(np.clip(np.log(fin.max() / max(fin.min(), 1.0)), 0.01, 3.0)))
     return (np.array(X, np.float32).reshape(-1, NUM_FEATURES), np.array(y, np.int32), np.array(w, np.float32))
 
 
@@ -145,7 +146,7 @@ def regret(t, choices) -> float:
     return float(sum(t[i, c] - t[i].min() for i, c in enumerate(choices)))
 
 
-SOLO_MAX_EDGES = 4096  # the device only lets the network pick action 4 below this
+SOLO_MAX_EDGES = 16384  # the device only lets the network pick action 4 below this
 
 
 def training_graphs(seed: int = 0xB10 + 50):
@@ -176,7 +177,7 @@ def build_training_set(byo, graphs, sources_per_graph: int = 3):
     return tables
 
 
-def train(byo, X, y, w, seed: int = 1, epochs: int = 3000, lr: float = 3e-3):
+def train(byo, X, y, w, seed: int = 1, epochs: int = 6000, lr: float = 3e-3):
     import torch
     m = byo.byo_mlp_create(seed)
     loss = byo.byo_mlp_train(m, torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(w).cuda(),
@@ -203,7 +204,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("cmd", choices=["train"])
     ap.add_argument("--out", default=DEFAULT_PATH)
-    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--epochs", type=int, default=6000)
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import paper_2405_11671_gb300 as byo
@@ -215,10 +216,10 @@ def main(argv=None):
     m, loss = train(byo, X, y, w, epochs=args.epochs)
     import torch
     pred = byo.byo_mlp_predict(m, torch.from_numpy(X).cuda()).cpu().numpy()
-    r_learned = 0.0
-    save(byo, m, args.out, {"samples": int(len(y)), "loss": loss, "train_regret_ns": r_learned,
+    acc = float(np.mean(pred == y)) if len(y) else 0.0
+    save(byo, m, args.out, {"samples": int(len(y)), "loss": loss, "train_accuracy": acc,
                              "label_counts": np.bincount(y, minlength=NUM_ACTIONS).tolist()})
-    print(json.dumps({"samples": int(len(y)), "loss": loss, "train_regret_ns": r_learned,
+    print(json.dumps({"samples": int(len(y)), "loss": loss, "train_accuracy": acc,
                       "label_counts": np.bincount(y, minlength=NUM_ACTIONS).tolist(), "out": args.out}))
 
 
