@@ -110,6 +110,24 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- helpers
 
+def reduce_over_ranks(dist, x: float, op: str, device: str) -> float:
+    """MAX or SUM of a per-rank float over the process group (identity alone)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_value(dist, edges_per_step: float, ms_per_step: float, device: str) -> tuple[float, float]:
+    """Whole-job GTEPS of independent replicas: edges of all ranks over the
+    slowest rank's step time.  Returns (GTEPS, max ms per step)."""
+    ms = reduce_over_ranks(dist, ms_per_step, "max", device)
+    edges = reduce_over_ranks(dist, edges_per_step, "sum", device)
+    return edges / (ms / 1e3) / 1e9, ms
+
+
 def dev_u32(torch, a):
     import numpy as np
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
@@ -306,6 +324,88 @@ def run_batched(args, byo, torch):
     byo.byo_graph_destroy(g)
 
 
+# ----------------------------------------------------------------------------- dynamic workload
+
+def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
+    """RMAT-24 (ef 16) in the dynamic container, then `rounds` rounds of one
+    insert batch of RMAT pairs and one delete batch of uniformly drawn earlier
+    pairs, each followed by BFS (one source) + CC + PageRank.  Reported: batch
+    update throughput (pairs/s, before symmetrisation), the algorithms' time on
+    the dynamic container, and a full GPU CSR rebuild of the same edge set."""
+    import numpy as np
+
+    import graphgen
+    seed = graphgen.SEEDS["rmat24"]
+    n, src, dst = graphgen.workload("rmat24")
+    g = byo.Graph(n, dev_u32(torch, src), dev_u32(torch, dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    pool_s, pool_d = [src], [dst]
+    s0 = int(graphgen.pick_sources(n, src, dst, 1, seed + 1)[0])
+    levels = torch.empty((1, n), dtype=torch.int32, device="cuda")
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    ranks = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    ins_ms, del_ms, alg_ms, csr_alg_ms, rebuild_ms = [], [], [], [], []
+    for r in range(rounds):
+        ins_s, ins_d = graphgen.rmat(24, batch, graphgen.stream(seed, 100 + r))
+        ps, pd = np.concatenate(pool_s), np.concatenate(pool_d)
+        pick = graphgen.pick_indices(len(ps), batch, graphgen.stream(seed, 200 + r))
+        del_s, del_d = ps[pick], pd[pick]
+        di, dd_ = dev_u32(torch, ins_s), dev_u32(torch, ins_d)
+        ds, dd = dev_u32(torch, del_s), dev_u32(torch, del_d)
+        torch.cuda.synchronize()
+        a, b, c = ev(), ev(), ev()
+        a.record(stream)
+        byo.byo_insert_batch(g.handle, di, dd_)
+        b.record(stream)
+        byo.byo_delete_batch(g.handle, ds, dd)
+        c.record(stream)
+        torch.cuda.synchronize()
+        ins_ms.append(a.elapsed_time(b))
+        del_ms.append(b.elapsed_time(c))
+        pool_s.append(ins_s)
+        pool_d.append(ins_d)
+        a, b = ev(), ev()
+        a.record(stream)
+        byo.byo_bfs(g.handle, [s0], levels, None, None, want_parents=False)
+        byo.byo_cc(g.handle, labels)
+        byo.byo_pagerank(g.handle, DAMPING, PR_ITERS, ranks, want_residual=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        alg_ms.append(a.elapsed_time(b))
+        # the same edge set rebuilt as a static CSR, and the same algorithms on it
+        off, col = byo.byo_graph_export_csr(g.handle)
+        rows = torch.repeat_interleave(torch.arange(n, device="cuda", dtype=torch.int32), off.diff())
+        a, b = ev(), ev()
+        a.record(stream)
+        gc = byo.Graph(n, rows, col, byo.BYO_CSR)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rebuild_ms.append(a.elapsed_time(b))
+        a, b = ev(), ev()
+        a.record(stream)
+        byo.byo_bfs(gc.handle, [s0], levels, None, None, want_parents=False)
+        byo.byo_cc(gc.handle, labels)
+        byo.byo_pagerank(gc.handle, DAMPING, PR_ITERS, ranks, want_residual=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        csr_alg_ms.append(a.elapsed_time(b))
+        gc.close()
+        del rows, off, col
+    med = statistics.median
+    line = {"metric": "dynamic container: batch updates/s and algorithm time vs CSR", "workload": "rmat24-dynamic",
+            "n": n, "m_final": g.m, "rounds": rounds, "batch_pairs": batch,
+            "insert_ms_median": round(med(ins_ms), 3), "delete_ms_median": round(med(del_ms), 3),
+            "insert_pairs_per_s": round(batch / (med(ins_ms) / 1e3), 1),
+            "delete_pairs_per_s": round(batch / (med(del_ms) / 1e3), 1),
+            "bfs_cc_pr_ms_dynamic": round(med(alg_ms), 3), "bfs_cc_pr_ms_csr": round(med(csr_alg_ms), 3),
+            "dynamic_over_csr": round(med(alg_ms) / med(csr_alg_ms), 3),
+            "csr_rebuild_ms_median": round(med(rebuild_ms), 3),
+            "update_round_vs_rebuild": round((med(ins_ms) + med(del_ms)) / med(rebuild_ms), 3)}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -333,8 +433,15 @@ def main():
         dist.barrier()
     import paper_2405_11671_gb300 as byo
     byo.load()
+    # all work on one non-default stream (PageRank's iterations then run as a
+    # captured CUDA graph)
+    work_stream = torch.cuda.Stream()
+    torch.cuda.set_stream(work_stream)
     if args.workload == "batched":
         run_batched(args, byo, torch)
+        return
+    if args.workload == "dynamic":
+        run_dynamic(args, byo, torch)
         return
 
     def barrier():
@@ -342,18 +449,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(dist, x, "max", "cuda")
 
     # ---- inputs (seeded, synthetic; replicas use the same graph)
     n, src, dst = graphgen.workload(args.workload)
@@ -424,7 +520,7 @@ def main():
     byo.byo_profile_enable(False)
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    step_ms = max_over_ranks(total_ms / args.steps)
+    local_ms = total_ms / args.steps
     algo_ms = {a: statistics.mean(x.elapsed_time(y) for x, y in ev[a]) for a in algos}
 
     # ---- edges per step (from the parity-checked outputs)
@@ -433,7 +529,7 @@ def main():
     bfs_edges = int((reached.to(torch.int64) * deg.unsqueeze(0)).sum().item()) // 2
     edges = {"bfs": bfs_edges, "cc": m // 2, "pr": PR_ITERS * m, "tc": m}
     step_edges = sum(edges.values())
-    value = sum_over_ranks(step_edges) / (step_ms / 1e3) / 1e9
+    value, step_ms = replica_value(dist, step_edges, local_ms, "cuda")
     per_algo = {a: {"ms": round(algo_ms[a], 4), "gteps": round(edges[a] / (algo_ms[a] / 1e3) / 1e9, 3)}
                 for a in algos}
 
@@ -532,8 +628,8 @@ def main():
             del sd, dd
         b.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps)
-        e2e = {"value": round(sum_over_ranks(step_edges) / (e2e_ms / 1e3) / 1e9, 3), "unit": "GTEPS",
+        e2e_v, e2e_ms = replica_value(dist, step_edges, a.elapsed_time(b) / e2e_steps, "cuda")
+        e2e = {"value": round(e2e_v, 3), "unit": "GTEPS",
                "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(src_h.numel() * 8),
                "d2h_bytes_per_step": int(lv_h.numel() * 4 + lab_h.numel() * 4 + rk_h.numel() * 4 + 8)}
     else:

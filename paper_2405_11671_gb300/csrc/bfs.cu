@@ -708,6 +708,8 @@ template <typename G, bool kParents>
 __global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
   __shared__ BfsShared S;
   __shared__ SoloShared Q;
+  __shared__ float wsm[kMlpParams];
+  sched_stage_weights(a.sp, wsm);
   const uint32_t tid = threadIdx.x;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
   const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;

@@ -84,6 +84,7 @@ struct DynStore;
 struct byo_graph {
   uint32_t n = 0;
   uint64_t m = 0;
+  uint64_t version = 0;  // bumped whenever the structure changes (cached launch plans depend on it)
   uint32_t flags = 0;
   bool off64 = false;
   int device = 0;

@@ -415,6 +415,7 @@ byo_status sort_unique_pairs(uint32_t n, const uint32_t* src, const uint32_t* ds
 }
 
 byo_status rebuild_buckets(byo_graph* g, cudaStream_t s) {
+  ++g->version;
   return with_view(g, [&](auto view) { return build_buckets(g, view, s); });
 }
 

@@ -51,6 +51,7 @@ cudaEvent_t take_event() {
 }  // namespace
 
 void note_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+bool profiling_on() { return g_on.load(std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s), a_(nullptr) {
   if (!g_on.load(std::memory_order_relaxed)) return;

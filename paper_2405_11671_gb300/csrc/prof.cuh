@@ -7,6 +7,7 @@
 namespace byo {
 
 void note_launch(uint64_t k = 1);
+bool profiling_on();
 
 // Records an event on `s` at construction and at destruction when profiling
 // is on; the pair is attributed to `name` (a string literal).

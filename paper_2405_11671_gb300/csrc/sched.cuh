@@ -4,10 +4,13 @@
 //   HEURISTIC  Beamer-style switch: push -> pull when the frontier's edges
 //              exceed the unvisited edges / alpha; pull -> push when the
 //              frontier has fewer than n / beta vertices.
-//   LEARNED    the Beamer rule picks the direction; on push levels a
-//              12 -> 32 -> 32 -> 5 ReLU network over the frontier features
-//              picks the push variant (bins or single-CTA), evaluated by one
-//              warp of every CTA inside the persistent loop.
+//   LEARNED    a 12 -> 32 -> 32 -> 5 ReLU network over the frontier
+//              features picks the action (evaluated by one warp of every CTA
+//              inside the persistent loop) among those the level allows: any
+//              push variant; pull only where the Beamer tests would pull
+//              (frontier edges > unvisited edges / alpha, or |F| >= n / beta),
+//              so that a misprediction never pulls a small frontier; the
+//              single-CTA push only for small frontiers.
 //   PUSH/PULL  fixed.
 // Schedules never change results, only which kernel path runs.
 #pragma once
@@ -26,6 +29,7 @@ constexpr int kActionSolo = 4;
 // The network may choose the single-CTA action only for frontiers this small
 // (in edges); beyond it one CTA cannot beat the grid whatever the network says.
 constexpr uint64_t kSoloMaxEdges = 16384;
+constexpr uint32_t kSoloMaxVertices = 1024;  // the shared-memory frontier of a solo run
 constexpr int kMlpParams = kHidden * kFeatures + kHidden + kHidden * kHidden + kHidden + kActions * kHidden + kActions;
 
 struct SchedParams {
@@ -33,8 +37,27 @@ struct SchedParams {
   int fixed_action;
   int bt, bw;  // log2 of thr_thread / thr_warp
   float alpha, beta;
-  const float* w;  // device MLP parameters (LEARNED)
+  const float* w;  // MLP parameters (LEARNED): global on the host side, the CTA's staged copy in kernels
 };
+
+// A CTA's shared-memory copy of the network, read once per launch so that
+// the per-level inference costs shared-memory latency.  The weight matrices
+// are stored transposed (input-major: element [i][j] of W at i * rows + j),
+// so that the 32 lanes, one per hidden unit, read 32 consecutive words
+// (no bank conflicts).  Every caller of sched_decide in LEARNED mode stages
+// the network first.
+__device__ __forceinline__ void sched_stage_weights(SchedParams& sp, float* smem_w) {
+  if (sp.mode != BYO_SCHED_LEARNED || sp.w == nullptr) return;
+  constexpr int o1 = kHidden * kFeatures, o2 = o1 + kHidden, o3 = o2 + kHidden * kHidden;
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
+    int d = i;
+    if (i < o1) d = (i % kFeatures) * kHidden + i / kFeatures;                  // W1 [32 x 12]
+    else if (i >= o2 && i < o3) d = o2 + ((i - o2) % kHidden) * kHidden + (i - o2) / kHidden;  // W2 [32 x 32]
+    smem_w[d] = __ldg(sp.w + i);
+  }
+  __syncthreads();
+  sp.w = smem_w;
+}
 
 struct SchedFeatures {
   uint32_t nf;
@@ -75,6 +98,11 @@ __device__ __forceinline__ void sched_bins(const SchedParams& sp, int action, in
   }
 }
 
+// Whether the learned schedule may pull: where either Beamer test would.
+__device__ __forceinline__ bool sched_pull_allowed(const SchedParams& sp, const SchedFeatures& f) {
+  return (double)f.mf > (double)f.mu / (double)sp.alpha || (double)f.nf >= (double)f.n / (double)sp.beta;
+}
+
 // Warp-collective (all 32 lanes of one warp); returns the action on every lane.
 __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFeatures& f, int prev_dir) {
   if (sp.mode == BYO_SCHED_FIXED) return sp.fixed_action;
@@ -82,7 +110,7 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
   if (sp.mode == BYO_SCHED_PULL) return 0;
   const int beamer = prev_dir == 1 ? ((double)f.mf > (double)f.mu / (double)sp.alpha ? 0 : 1)
                                     : ((double)f.nf < (double)f.n / (double)sp.beta ? 1 : 0);
-  if (sp.mode == BYO_SCHED_HEURISTIC || sp.w == nullptr || beamer == 0) return beamer;
+  if (sp.mode == BYO_SCHED_HEURISTIC || sp.w == nullptr) return beamer;
   // LEARNED: lane j owns hidden unit j of both layers
   const uint32_t lane = lane_id();
   float x[kFeatures];
@@ -93,24 +121,26 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
   const float* b2 = W2 + kHidden * kHidden;
   const float* W3 = b2 + kHidden;
   const float* b3 = W3 + kActions * kHidden;
-  float h1 = __ldg(b1 + lane);
+  float h1 = b1[lane];
 #pragma unroll
-  for (int i = 0; i < kFeatures; ++i) h1 = fmaf(__ldg(W1 + lane * kFeatures + i), x[i], h1);
+  for (int i = 0; i < kFeatures; ++i) h1 = fmaf(W1[i * kHidden + lane], x[i], h1);  // staged transposed
   h1 = fmaxf(h1, 0.0f);
-  float h2 = __ldg(b2 + lane);
+  float h2 = b2[lane];
 #pragma unroll
-  for (int k = 0; k < kHidden; ++k) h2 = fmaf(__ldg(W2 + lane * kHidden + k), __shfl_sync(0xFFFFFFFFu, h1, k), h2);
+  for (int k = 0; k < kHidden; ++k) h2 = fmaf(W2[k * kHidden + lane], __shfl_sync(0xFFFFFFFFu, h1, k), h2);
   h2 = fmaxf(h2, 0.0f);
-  const bool solo_ok = f.mf <= kSoloMaxEdges;
-  int best = 1;
+  const bool solo_ok = f.mf <= kSoloMaxEdges && f.nf <= kSoloMaxVertices;
+  const bool pull_ok = sched_pull_allowed(sp, f);
+  int best = -1;  // action 1 is always allowed
   float bestz = 0.0f;
 #pragma unroll
-  for (int c = 1; c < kActions; ++c) {  // a push variant: the direction is Beamer's
-    float t = __ldg(W3 + c * kHidden + lane) * h2;
+  for (int c = 0; c < kActions; ++c) {
+    float t = W3[c * kHidden + lane] * h2;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-    float z = t + __ldg(b3 + c);
-    if ((c == 1 || z > bestz) && (c != kActionSolo || solo_ok)) {
+    const float z = t + b3[c];
+    const bool ok = c == 0 ? pull_ok : (c == kActionSolo ? solo_ok : true);
+    if (ok && (best < 0 || z > bestz)) {
       bestz = z;
       best = c;
     }

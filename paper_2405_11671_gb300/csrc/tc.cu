@@ -2,24 +2,30 @@
 // builds a smaller DAG first, then neighbour sets are intersected).
 //
 // Filter: each edge is kept once, from the endpoint of lower rank, where
-// rank(v) = (degree(v), v) in lexicographic order; N+(v) stays sorted by id.
+// rank(v) = (degree(v), v) in lexicographic order.  The DAG is stored in rank
+// space: vertex v becomes its position in that order (a radix sort of the
+// (degree, id) keys), so that N+(r) holds only ids above r and the out-lists
+// of high-degree vertices fall in the short range of top ranks.
 // Count: the number of triangles is the sum over DAG edges u->v of
-// |N+(u) intersect N+(v)|.  Each edge is intersected from the side with the
-// shorter out-list: N+(c) of a "centre" c is staged in shared memory by a TMA
-// bulk copy (cp.async.bulk, completion on an mbarrier; no multicast) and
-// hashed there, and the out-lists of its partners (out-neighbours p with
-// d+(p) <= d+(c), in-neighbours p with d+(p) < d+(c)) are walked 32 ids at a
-// time by a warp (edge-balanced across the warp) and probed.  u with |N+(u)| <= kLightMax: one warp each; the staged N+(u) is
-// loaded into an open-addressing hash set in the warp's shared memory and each
-// id of N+(v) costs one or two probes.  Larger u: one CTA each (taken from a
-// work counter), N+(u) staged in windows of kWindow ids, each hashed the same
-// way into the CTA's shared memory.
+// |N+(u) intersect N+(v)| (the count does not depend on the labels).  Each
+// edge is intersected from the side with the shorter out-list: N+(c) of a
+// "centre" c is put into a shared-memory set and the out-lists of its
+// partners (out-neighbours p with d+(p) <= d+(c), in-neighbours p with d+(p) <
+// d+(c)) are walked 32 ids at a time by a warp (edge-balanced across the warp)
+// and probed.  Centres with |N+(c)| <= kLightMax: one warp each; N+(c) is
+// staged by a TMA bulk copy (cp.async.bulk, completion on an mbarrier; no
+// multicast) and loaded into an open-addressing hash set in the warp's shared
+// memory.  Larger centres: one CTA each (taken from a work counter); when the
+// rank range above c fits the CTA's shared memory, N+(c) becomes a bitmap of
+// that range (one probe per id, no collisions), otherwise it is staged in
+// windows of kWindow ids, each hashed into the CTA's shared memory.
 #include <stdlib.h>
 
 #include "byo_internal.cuh"
 #include "prof.cuh"
 #include "container.cuh"
 #include "vbins.cuh"
+#include "rank.cuh"
 
 namespace byo {
 
@@ -27,9 +33,10 @@ constexpr uint32_t kLightMax = 256;   // capacity of a warp's shared-memory slic
 constexpr uint32_t kWindow = 4096;    // capacity of a CTA's shared-memory window (ids)
 constexpr int kTcThreads = 256;
 
-// The light/heavy split and the window length can be lowered (never raised)
-// with BYO_TC_LIGHT_MAX / BYO_TC_WINDOW, so that small test graphs exercise
-// the CTA path and multi-window intersections.
+// The light/heavy split, the window length and the bitmap range can be
+// lowered (never raised) with BYO_TC_LIGHT_MAX / BYO_TC_WINDOW /
+// BYO_TC_BITMAP_BITS, so that small test graphs exercise the CTA path, the
+// hashed windows and multi-window intersections.
 static uint32_t env_cap(const char* name, uint32_t cap) {
   const char* e = getenv(name);
   if (!e || !*e) return cap;
@@ -45,7 +52,8 @@ struct TcWork {
   uint32_t* dag_col = nullptr;  // half_cap + 8
   uint64_t* in_off = nullptr;   // n + 1: N- offsets
   uint32_t* in_col = nullptr;   // half_cap + 8
-  uint32_t* outdeg = nullptr;   // n
+  uint32_t* outdeg = nullptr;   // n (rank-indexed)
+  uint32_t* rank = nullptr;     // n: vertex id -> position in (degree, id) order
   uint32_t* cnt_l = nullptr;    // n: in-degrees, then light task counts
   uint32_t* cnt_h = nullptr;    // n: heavy task counts
   uint64_t* pos_l = nullptr;    // n + 1
@@ -63,6 +71,7 @@ void tc_free(TcWork* w) {
   dev_free(w->in_off);
   dev_free(w->in_col);
   dev_free(w->outdeg);
+  dev_free(w->rank);
   dev_free(w->cnt_l);
   dev_free(w->cnt_h);
   dev_free(w->pos_l);
@@ -119,57 +128,64 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_
 }
 
 // ---------------------------------------------------------------- filter
+// Out-degree d+(v) = |{u in N(v): rank(u) > rank(v)}| and in-degree d-(v) =
+// deg(v) - d+(v), both stored at rank(v).
 template <typename G>
-__device__ __forceinline__ bool rank_lt(const G& g, uint32_t a, uint32_t da, uint32_t b) {
-  uint32_t db = g.degree(b);
-  return da < db || (da == db && a < b);
-}
-
-template <typename G>
-__global__ void __launch_bounds__(kTcThreads) tc_outdeg_kernel(G g, VBins bins, uint32_t* outdeg) {
+__global__ void __launch_bounds__(kTcThreads) tc_outdeg_kernel(G g, VBins bins, const uint32_t* __restrict__ rank,
+                                                               uint32_t* outdeg, uint32_t* indeg) {
   VRange r = vbins_range(bins);
   const uint32_t lane = lane_id();
   if (r.role == kRoleThread) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
+      const uint32_t rv = __ldg(rank + v);
       uint32_t c = 0;
-      for (uint32_t k = 0; k < s.len; ++k) c += rank_lt(g, v, s.len, __ldg(s.p + k));
-      outdeg[v] = c;
+      for (uint32_t k = 0; k < s.len; ++k) c += __ldg(rank + __ldg(s.p + k)) > rv;
+      outdeg[rv] = c;
+      indeg[rv] = s.len - c;
     }
   } else if (r.role == kRoleWarp) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
+      const uint32_t rv = __ldg(rank + v);
       uint32_t c = 0;
-      for (uint32_t k = lane; k < s.len; k += 32) c += rank_lt(g, v, s.len, __ldg(s.p + k));
+      for (uint32_t k = lane; k < s.len; k += 32) c += __ldg(rank + __ldg(s.p + k)) > rv;
       c = __reduce_add_sync(0xFFFFFFFFu, c);
-      if (lane == 0) outdeg[v] = c;
+      if (lane == 0) {
+        outdeg[rv] = c;
+        indeg[rv] = s.len - c;
+      }
     }
   } else {
     __shared__ uint32_t part[kTcThreads / 32];
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
+      const uint32_t rv = __ldg(rank + v);
       uint32_t c = 0;
-      for (uint32_t k = threadIdx.x; k < s.len; k += blockDim.x) c += rank_lt(g, v, s.len, __ldg(s.p + k));
+      for (uint32_t k = threadIdx.x; k < s.len; k += blockDim.x) c += __ldg(rank + __ldg(s.p + k)) > rv;
       c = __reduce_add_sync(0xFFFFFFFFu, c);
       if (lane == 0) part[threadIdx.x >> 5] = c;
       __syncthreads();
       if (threadIdx.x == 0) {
         uint32_t t = 0;
         for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) t += part[w];
-        outdeg[v] = t;
+        outdeg[rv] = t;
+        indeg[rv] = s.len - t;
       }
       __syncthreads();
     }
   }
 }
 
-// N+(v) (higher-rank neighbours) into dag_col and N-(v) (lower-rank ones)
-// into in_col, both in stored (ascending id) order: one pass over the list.
+// N+(rank v) (ranks of the higher-rank neighbours) into dag_col and N-(rank v)
+// (ranks of the lower-rank ones) into in_col, both in v's stored neighbour
+// order: one pass over the list.
 template <typename G>
-__global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, const uint64_t* __restrict__ dag_off,
+__global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, const uint32_t* __restrict__ rank,
+                                                             const uint64_t* __restrict__ dag_off,
                                                              uint32_t* __restrict__ dag_col,
                                                              const uint64_t* __restrict__ in_off,
                                                              uint32_t* __restrict__ in_col) {
@@ -179,26 +195,28 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
-      uint64_t o = dag_off[v], q = in_off[v];
+      const uint32_t rv = __ldg(rank + v);
+      uint64_t o = dag_off[rv], q = in_off[rv];
       for (uint32_t k = 0; k < s.len; ++k) {
-        uint32_t u = __ldg(s.p + k);
-        if (rank_lt(g, v, s.len, u)) dag_col[o++] = u;
-        else in_col[q++] = u;
+        uint32_t ru = __ldg(rank + __ldg(s.p + k));
+        if (ru > rv) dag_col[o++] = ru;
+        else in_col[q++] = ru;
       }
     }
   } else if (r.role == kRoleWarp) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
-      uint64_t o = dag_off[v], q = in_off[v];
+      const uint32_t rv = __ldg(rank + v);
+      uint64_t o = dag_off[rv], q = in_off[rv];
       for (uint32_t base = 0; base < s.len; base += 32) {
         uint32_t k = base + lane;
-        uint32_t u = k < s.len ? __ldg(s.p + k) : 0;
-        bool keep = k < s.len && rank_lt(g, v, s.len, u);
+        uint32_t ru = k < s.len ? __ldg(rank + __ldg(s.p + k)) : 0;
+        bool keep = k < s.len && ru > rv;
         bool back = k < s.len && !keep;
         uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep), bbk = __ballot_sync(0xFFFFFFFFu, back);
-        if (keep) dag_col[o + __popc(bal & lanemask_lt())] = u;
-        if (back) in_col[q + __popc(bbk & lanemask_lt())] = u;
+        if (keep) dag_col[o + __popc(bal & lanemask_lt())] = ru;
+        if (back) in_col[q + __popc(bbk & lanemask_lt())] = ru;
         o += __popc(bal);
         q += __popc(bbk);
       }
@@ -210,11 +228,12 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
-      uint64_t o = dag_off[v], q = in_off[v];
+      const uint32_t rv = __ldg(rank + v);
+      uint64_t o = dag_off[rv], q = in_off[rv];
       for (uint32_t base = 0; base < s.len; base += blockDim.x) {
         uint32_t k = base + threadIdx.x;
-        uint32_t u = k < s.len ? __ldg(s.p + k) : 0;
-        bool keep = k < s.len && rank_lt(g, v, s.len, u);
+        uint32_t ru = k < s.len ? __ldg(rank + __ldg(s.p + k)) : 0;
+        bool keep = k < s.len && ru > rv;
         bool back = k < s.len && !keep;
         uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep), bbk = __ballot_sync(0xFFFFFFFFu, back);
         if (lane == 0) {
@@ -227,8 +246,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
           for (uint32_t j = 0; j < nw; ++j) wpre[threadIdx.x][j + 1] = wpre[threadIdx.x][j] + wcnt[threadIdx.x][j];
         }
         __syncthreads();
-        if (keep) dag_col[o + wpre[0][w] + __popc(bal & lanemask_lt())] = u;
-        if (back) in_col[q + wpre[1][w] + __popc(bbk & lanemask_lt())] = u;
+        if (keep) dag_col[o + wpre[0][w] + __popc(bal & lanemask_lt())] = ru;
+        if (back) in_col[q + wpre[1][w] + __popc(bbk & lanemask_lt())] = ru;
         o += wpre[0][nw];
         q += wpre[1][nw];
         __syncthreads();
@@ -238,14 +257,6 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
 }
 
 __global__ void tc_set_last_kernel(uint64_t* dag_off, uint32_t n, uint64_t total) { dag_off[n] = total; }
-
-// in-degree in the DAG = degree - out-degree
-template <typename G>
-__global__ void tc_indeg_kernel(G g, const uint32_t* __restrict__ outdeg, uint32_t* indeg) {
-  const uint32_t n = g.num_vertices();
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
-    indeg[v] = g.degree((uint32_t)v) - outdeg[v];
-}
 
 // Work items.  Every DAG edge a->b is intersected from the side with the
 // shorter out-list: at centre a (walk N+(b), probe N+(a)) when d+(b) <= d+(a),
@@ -318,12 +329,14 @@ __global__ void tc_task_fill_kernel(const uint64_t* __restrict__ dag_off, const 
 
 // ---------------------------------------------------------------- intersect
 // Open-addressing hash set in shared memory (linear probing, empty = INF,
-// multiplicative hashing); the table has at least twice (warp kernel: four
-// times) as many slots as keys, so that most absent ids cost one probe.
+// multiplicative hashing) over ids in [lo, hi]; the table has at least twice
+// (warp kernel: four times) as many slots as keys, so that most absent ids
+// cost one probe.
 struct SmemHash {
   const uint32_t* t;
-  uint32_t mask, shift;
+  uint32_t mask, shift, lo, hi;
   __device__ __forceinline__ bool contains(uint32_t x) const {
+    if (x < lo || x > hi) return false;
     uint32_t h = (x * 0x9E3779B1u) >> shift;
     while (true) {
       uint32_t y = t[h];
@@ -334,25 +347,55 @@ struct SmemHash {
   }
 };
 
+// Bitmap over the rank range [base, base + nbits) in shared memory.
+struct SmemBits {
+  const uint32_t* b;
+  uint32_t base, nbits;
+  __device__ __forceinline__ bool contains(uint32_t x) const {
+    const uint32_t i = x - base;  // wraps for x < base
+    return i < nbits && ((b[i >> 5] >> (i & 31)) & 1u);
+  }
+};
 
-// The warp walks the concatenation of the lists dag_col[vb .. vb+len) held by
-// its lanes (len = 0 for lanes without a partner) and counts the ids w in
-// [lo_id, hi_id] that the set contains.
+// The warp walks the lists dag_col[vb .. vb+len) held by its lanes (len = 0
+// for lanes without a partner) and counts the ids the set contains.  Lists of
+// 32 ids or more are walked one at a time by the whole warp (coalesced, four
+// loads in flight per lane, no bookkeeping per id); the shorter ones are
+// concatenated and walked 32 ids at a time, each lane finding the list its id
+// belongs to by a 5-step search over the lanes' prefix sums.
 template <typename Set>
 __device__ __forceinline__ uint64_t warp_count_group(const uint32_t* __restrict__ dag_col, uint64_t vb, uint32_t len,
-                                                     const Set& set, uint32_t lo_id, uint32_t hi_id) {
+                                                     const Set& set) {
   const uint32_t lane = lane_id();
-  uint32_t incl = len;
+  uint64_t hits = 0;
+  uint32_t longs = __ballot_sync(0xFFFFFFFFu, len >= 32);
+  while (longs) {
+    const int l = __ffs(longs) - 1;
+    longs &= longs - 1;
+    const uint64_t b = __shfl_sync(0xFFFFFFFFu, vb, l);
+    const uint32_t ln = __shfl_sync(0xFFFFFFFFu, len, l);
+    const uint32_t* p = dag_col + b;
+    uint32_t k = lane;
+    for (; k + 96 < ln; k += 128) {
+      const uint32_t w0 = __ldg(p + k), w1 = __ldg(p + k + 32), w2 = __ldg(p + k + 64), w3 = __ldg(p + k + 96);
+      hits += set.contains(w0);
+      hits += set.contains(w1);
+      hits += set.contains(w2);
+      hits += set.contains(w3);
+    }
+    for (; k < ln; k += 32) hits += set.contains(__ldg(p + k));
+  }
+  const uint32_t slen = len >= 32 ? 0 : len;
+  uint32_t incl = slen;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
     if ((int)lane >= o) incl += y;
   }
-  uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-  uint32_t excl = incl - len;
-  uint64_t hits = 0;
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  const uint32_t excl = incl - slen;
   for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-    uint32_t e = e0 + lane;
+    const uint32_t e = e0 + lane;
     int owner = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
@@ -360,12 +403,9 @@ __device__ __forceinline__ uint64_t warp_count_group(const uint32_t* __restrict_
       uint32_t ex = __shfl_sync(0xFFFFFFFFu, excl, probe & 31);
       if (probe < 32 && ex <= e) owner = probe;
     }
-    uint32_t oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
-    uint64_t ob = __shfl_sync(0xFFFFFFFFu, vb, owner);
-    if (e < total) {
-      uint32_t w = __ldg(dag_col + ob + (e - oex));
-      if (w >= lo_id && w <= hi_id && set.contains(w)) ++hits;
-    }
+    const uint32_t oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
+    const uint64_t ob = __shfl_sync(0xFFFFFFFFu, vb, owner);
+    if (e < total && set.contains(__ldg(dag_col + ob + (e - oex)))) ++hits;
   }
   return hits;
 }
@@ -385,11 +425,31 @@ __device__ __forceinline__ void partner_list(const uint64_t* __restrict__ dag_of
   }
 }
 
+// Walks the partners [t.lo, t.hi) of a task with `warps` warps (this one is
+// warp `w`) and counts the ids of their out-lists that `set` contains.
+template <typename Set>
+__device__ __forceinline__ uint64_t walk_partners(const uint64_t* __restrict__ dag_off,
+                                                  const uint32_t* __restrict__ dag_col, const uint32_t* partners,
+                                                  const TcTask& t, uint32_t dc, uint32_t w, uint32_t warps,
+                                                  const Set& set) {
+  uint64_t hits = 0;
+  for (uint32_t k0 = t.lo + w * 32; k0 < t.hi; k0 += warps * 32) {
+    const uint32_t k = k0 + lane_id();
+    const bool has = k < t.hi;
+    const uint32_t p = has ? __ldg(partners + k) : 0;
+    uint64_t vb;
+    uint32_t len;
+    partner_list(dag_off, has, p, t.kind, dc, &vb, &len);
+    hits += warp_count_group(dag_col, vb, len, set);
+  }
+  return hits;
+}
+
 constexpr uint32_t kSlice = kLightMax + 8;  // staged N+(u) (+ alignment slack), ids
 constexpr uint32_t kTable = 4 * kLightMax;   // hash slots per warp (load factor <= 1/4)
 constexpr size_t kLightSmem = (size_t)(kTcThreads / 32) * (kSlice + kTable) * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __restrict__ dag_off,
+__global__ void __launch_bounds__(kTcThreads, 5) tc_light_kernel(const uint64_t* __restrict__ dag_off,
                                                               const uint32_t* __restrict__ dag_col,
                                                               const uint64_t* __restrict__ in_off,
                                                               const uint32_t* __restrict__ in_col,
@@ -406,7 +466,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __
   __syncwarp();
   uint32_t phase = 0;
   uint32_t have = kInf;  // centre whose N+ is staged and hashed in this warp's slice
-  uint32_t head = 0, dc = 0, bits = 5;
+  uint32_t head = 0, dc = 0, bits = 5, lo = 0, hi = 0;
   uint64_t hits = 0;
   while (true) {
     uint32_t idx = 0;
@@ -420,7 +480,10 @@ __global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __
       uint64_t a0 = beg & ~3ull, a1 = (end + 3) & ~3ull;
       head = (uint32_t)(beg - a0);
       dc = (uint32_t)(end - beg);
-      __syncwarp();  // every lane is done with the previous slice and table
+      // every lane is done with the previous slice and table, and its reads
+      // are ordered before the bulk copy's writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
       bool ok = true;
       if (lane == 0) {
         bulk_load(buf, dag_col + a0, (uint32_t)((a1 - a0) * 4), &bar[w]);
@@ -435,27 +498,22 @@ __global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __
       const uint32_t slots = 1u << bits;
       for (uint32_t i = lane; i < slots; i += 32) table[i] = kInf;
       __syncwarp();
+      uint32_t mn = kInf, mx = 0;
       for (uint32_t k = lane; k < dc; k += 32) {
         uint32_t x = buf[head + k];
+        mn = min(mn, x);
+        mx = max(mx, x);
         uint32_t h = (x * 0x9E3779B1u) >> (32 - bits);
         while (atomicCAS(table + h, kInf, x) != kInf) h = (h + 1) & (slots - 1);
       }
+      lo = __reduce_min_sync(0xFFFFFFFFu, mn);
+      hi = __reduce_max_sync(0xFFFFFFFFu, mx);
       __syncwarp();
       have = c;
     }
-    const uint32_t* list = buf + head;
-    SmemHash set{table, (1u << bits) - 1, 32 - bits};
-    const uint32_t lo_id = list[0], hi_id = list[dc - 1];
-    const uint32_t* partners = t.kind == 0 ? list : in_col + in_off[c];
-    for (uint32_t k0 = t.lo; k0 < t.hi; k0 += 32) {
-      uint32_t k = k0 + lane;
-      bool has = k < t.hi;
-      uint32_t p = has ? partners[k] : 0;
-      uint64_t vb;
-      uint32_t len;
-      partner_list(dag_off, has, p, t.kind, dc, &vb, &len);
-      hits += warp_count_group(dag_col, vb, len, set, lo_id, hi_id);
-    }
+    SmemHash set{table, (1u << bits) - 1, 32 - bits, lo, hi};
+    const uint32_t* partners = t.kind == 0 ? dag_col + dag_off[c] : in_col + in_off[c];
+    hits += walk_partners(dag_off, dag_col, partners, t, dc, 0, 1, set);
   }
   uint64_t sum = hits;
 #pragma unroll
@@ -464,42 +522,78 @@ __global__ void __launch_bounds__(kTcThreads) tc_light_kernel(const uint64_t* __
 }
 
 constexpr uint32_t kHeavyTable = 2 * kWindow;
-constexpr size_t kHeavySmem = (size_t)(kWindow + 8 + kHeavyTable) * sizeof(uint32_t);
+constexpr uint32_t kHeavyWords = kWindow + 8 + kHeavyTable;  // 32-bit words of dynamic shared memory
+constexpr uint32_t kBitmapBits = 32 * (kHeavyWords & ~3u);   // bitmap capacity of the same memory
+constexpr size_t kHeavySmem = (size_t)kHeavyWords * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __restrict__ dag_off,
+// One CTA per task.  Bitmap mode (the n - 1 - c ranks above c fit in
+// `bitmap_bits`): N+(c) is set into a bitmap of that range, read straight
+// from the DAG, and kept while the CTA's next task has the same centre.
+// Hash mode: N+(c) is staged by TMA in windows of `window` ids, each hashed.
+__global__ void __launch_bounds__(kTcThreads, 4) tc_heavy_kernel(const uint64_t* __restrict__ dag_off,
                                                               const uint32_t* __restrict__ dag_col,
                                                               const uint64_t* __restrict__ in_off,
                                                               const uint32_t* __restrict__ in_col,
                                                               const TcTask* __restrict__ tasks, uint64_t ntasks,
-                                                              uint32_t* ctr, unsigned long long* count,
-                                                              uint32_t window, uint64_t limit_ns) {
+                                                              uint32_t n, uint32_t* ctr, unsigned long long* count,
+                                                              uint32_t window, uint32_t bitmap_bits,
+                                                              uint64_t limit_ns) {
   extern __shared__ __align__(16) uint32_t win[];
   uint32_t* table = win + kWindow + 8;
   __shared__ __align__(8) uint64_t bar;
   __shared__ bool ok_s;
-  __shared__ uint32_t idx_s;
+  __shared__ uint32_t idx_s[2], lo_s, hi_s;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t* err = ctr + 3;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t phase = 0;
+  uint32_t have = kInf;  // centre whose bitmap is in shared memory
   uint64_t hits = 0;
-  while (true) {
-    if (threadIdx.x == 0) idx_s = atomicAdd(ctr + 4, 1u);
+  // The task index alternates between two slots: a task may pass without a
+  // barrier (same centre, bitmap kept), and thread 0 must not overwrite the
+  // slot another thread has yet to read.
+  for (uint32_t it = 0;; ++it) {
+    if (threadIdx.x == 0) idx_s[it & 1] = atomicAdd(ctr + 4, 1u);
     __syncthreads();
-    const uint32_t idx = idx_s;
+    const uint32_t idx = idx_s[it & 1];
     if (idx >= ntasks) break;
     const TcTask t = tasks[idx];
     const uint32_t c = t.c;
     const uint64_t beg = dag_off[c], end = dag_off[c + 1];
     const uint32_t dc = (uint32_t)(end - beg);
     const uint32_t* partners = t.kind == 0 ? dag_col + beg : in_col + in_off[c];
+    const uint32_t above = n - 1 - c;  // N+(c) lies in the ranks (c, n)
+    if (above <= bitmap_bits) {
+      if (c != have) {
+        const uint32_t words = (above + 127) / 128 * 4;
+        __syncthreads();  // every thread is done with the previous set
+        uint4* w4 = reinterpret_cast<uint4*>(win);
+        for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < dc; k += blockDim.x) {
+          const uint32_t x = __ldg(dag_col + beg + k) - (c + 1);
+          atomicOr(win + (x >> 5), 1u << (x & 31));
+        }
+        __syncthreads();
+        have = c;
+      }
+      SmemBits set{win, c + 1, above};
+      hits += walk_partners(dag_off, dag_col, partners, t, dc, w, nw, set);
+      continue;
+    }
+    have = kInf;
     for (uint64_t wb = beg; wb < end; wb += window) {
       uint64_t we = wb + window < end ? wb + window : end;
       uint64_t a0 = wb & ~3ull, a1 = (we + 3) & ~3ull;
       uint32_t head = (uint32_t)(wb - a0), wlen = (uint32_t)(we - wb);
-      __syncthreads();  // every thread is done with the previous window and table
+      // every thread is done with the previous window, table or bitmap, and
+      // its shared-memory accesses are ordered before the bulk copy's writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
       if (threadIdx.x == 0) {
+        lo_s = kInf;
+        hi_s = 0;
         bulk_load(win, dag_col + a0, (uint32_t)((a1 - a0) * 4), &bar);
         ok_s = mbar_wait(&bar, phase, err, limit_ns);
       }
@@ -513,23 +607,23 @@ __global__ void __launch_bounds__(kTcThreads) tc_heavy_kernel(const uint64_t* __
       const uint32_t slots = 1u << bits;
       for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) table[i] = kInf;
       __syncthreads();
+      uint32_t mn = kInf, mx = 0;
       for (uint32_t k = threadIdx.x; k < wlen; k += blockDim.x) {
         uint32_t x = list[k];
+        mn = min(mn, x);
+        mx = max(mx, x);
         uint32_t h = (x * 0x9E3779B1u) >> (32 - bits);
         while (atomicCAS(table + h, kInf, x) != kInf) h = (h + 1) & (slots - 1);
       }
-      __syncthreads();
-      SmemHash set{table, slots - 1, 32 - bits};
-      const uint32_t lo_id = list[0], hi_id = list[wlen - 1];
-      for (uint32_t k0 = t.lo + w * 32; k0 < t.hi; k0 += nw * 32) {
-        uint32_t k = k0 + lane;
-        bool has = k < t.hi;
-        uint32_t p = has ? __ldg(partners + k) : 0;
-        uint64_t vb;
-        uint32_t len;
-        partner_list(dag_off, has, p, t.kind, dc, &vb, &len);
-        hits += warp_count_group(dag_col, vb, len, set, lo_id, hi_id);
+      mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+      mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+      if (lane == 0) {
+        atomicMin(&lo_s, mn);
+        atomicMax(&hi_s, mx);
       }
+      __syncthreads();
+      SmemHash set{table, slots - 1, 32 - bits, lo_s, hi_s};
+      hits += walk_partners(dag_off, dag_col, partners, t, dc, w, nw, set);
     }
   }
   uint64_t sum = hits;
@@ -556,6 +650,7 @@ byo_status ensure_tc_work(byo_graph* g) {
   if (st == BYO_OK) st = dev_alloc_t(&w->in_off, g->n + 1ull, "TC DAG in-offsets");
   if (st == BYO_OK) st = dev_alloc_t(&w->in_col, w->half_cap + 8, "TC DAG in-neighbours");
   if (st == BYO_OK) st = dev_alloc_t(&w->outdeg, g->n, "TC out-degrees");
+  if (st == BYO_OK) st = dev_alloc_t(&w->rank, g->n, "TC ranks");
   if (st == BYO_OK) st = dev_alloc_t(&w->cnt_l, g->n, "TC task counts");
   if (st == BYO_OK) st = dev_alloc_t(&w->cnt_h, g->n, "TC task counts");
   if (st == BYO_OK) st = dev_alloc_t(&w->pos_l, g->n + 1ull, "TC task offsets");
@@ -582,23 +677,24 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
   const uint32_t n = g->n;
   const uint64_t half = g->m / 2;
   VBins bins = make_vbins(g, 4, 10, kTcThreads);
+  // rank(v) = position of (degree(v), v) in ascending order
+  BYO_RETURN_IF(degree_rank(g, view, w->rank, nullptr, s));
   {
     ProfScope ps("tc_outdeg", s);
-    tc_outdeg_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->outdeg);
+    tc_outdeg_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->rank, w->outdeg, w->cnt_l);
     ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_outdeg_kernel");
   BYO_RETURN_IF(scan_u32_to_u64(w->outdeg, w->dag_off, n, nullptr, s));
   tc_set_last_kernel<<<1, 1, 0, s>>>(w->dag_off, n, half);
-  tc_indeg_kernel<<<grid_for(n, 256), 256, 0, s>>>(view, w->outdeg, w->cnt_l);
-  ::byo::note_launch(2);
-  BYO_CHECK_LAUNCH("tc_indeg_kernel");
+  ::byo::note_launch();
   BYO_RETURN_IF(scan_u32_to_u64(w->cnt_l, w->in_off, n, nullptr, s));
   tc_set_last_kernel<<<1, 1, 0, s>>>(w->in_off, n, half);
   ::byo::note_launch();
   {
     ProfScope ps("tc_fill", s);
-    tc_fill_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->dag_off, w->dag_col, w->in_off, w->in_col);
+    tc_fill_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->rank, w->dag_off, w->dag_col, w->in_off,
+                                                           w->in_col);
     ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_fill_kernel");
@@ -651,8 +747,8 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
     if (e == cudaSuccess) {
       ProfScope ps("tc_heavy", s);
       tc_heavy_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kHeavySmem, s>>>(
-          w->dag_off, w->dag_col, w->in_off, w->in_col, th, nh, w->ctr, w->count, env_cap("BYO_TC_WINDOW", kWindow),
-          limit);
+          w->dag_off, w->dag_col, w->in_off, w->in_col, th, nh, n, w->ctr, w->count, env_cap("BYO_TC_WINDOW", kWindow),
+          env_cap("BYO_TC_BITMAP_BITS", kBitmapBits), limit);
       ::byo::note_launch();
       e = cudaGetLastError();
     }

@@ -39,6 +39,12 @@ inline uint32_t vbins_grid(const VBins& b) {
 
 enum VRole { kRoleThread = 0, kRoleWarp = 1, kRoleCta = 2 };
 
+// Vertex at vorder index i; a null vorder is the identity (a graph whose ids
+// are already in degree order).
+__device__ __forceinline__ uint32_t vbins_vertex(const VBins& b, uint64_t i) {
+  return b.vorder ? __ldg(b.vorder + i) : (uint32_t)i;
+}
+
 struct VRange {
   int role;
   uint64_t begin, end, stride;  // vorder indices this block (thread / warp) walks

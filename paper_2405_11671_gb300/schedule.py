@@ -13,15 +13,16 @@ action meaning
 4      push by one CTA alone, no grid barrier between such levels
 ====== =========================================================
 
-The direction (push or pull) stays with the Beamer rule; the network chooses
-which push variant (1-4) runs on the levels the rule pushes.  Training data are
-timings the engine records itself: every training graph is traversed once per
-action with that action forced at every level, and the per-iteration device
-times (``byo_bfs_trace``) give, for each level, the time of each action on the
-same frontier (BFS frontiers do not depend on the schedule).  Samples are the
-levels the rule would push; a sample's label is the fastest push variant the
-device would allow and its weight is the time the worst one would lose,
-relative to the traversal's best total.  The network is trained by the
+The network chooses among the actions a level allows: any push variant; pull
+only where a Beamer test would pull (frontier edges > unvisited edges / alpha,
+or |F| >= n / beta), so that a misprediction never pulls a small frontier; the
+single-CTA push only for small frontiers.  Training data are timings the engine
+records itself: every training graph is traversed once per action with that
+action forced at every level, and the per-iteration device times
+(``byo_bfs_trace``) give, for each level, the time of each action on the same
+frontier (BFS frontiers do not depend on the schedule).  Every level is a
+sample; its label is the fastest allowed action and its weight the log of the
+slowest over the fastest allowed action's time.  The network is trained by the
 library's own forward/backward/Adam kernels.
 
 ``python -m paper_2405_11671_gb300.schedule train --out sched_mlp.json`` builds
@@ -67,6 +68,11 @@ def trace_features(trace, n: int, m: int) -> np.ndarray:
                      for r in trace]) if trace else np.zeros((0, NUM_FEATURES), np.float32)
 
 
+ALPHA, BETA = 15.0, 18.0  # the default Beamer constants of a schedule
+SOLO_MAX_EDGES = 16384  # the device only lets the network pick action 4 below this
+SOLO_MAX_VERTICES = 1024
+
+
 def forced_sched(byo, action: int):
     return byo.make_sched(byo.BYO_SCHED_FIXED, 16, 1024, action=action)
 
@@ -97,42 +103,31 @@ def time_actions(byo, g, sources, repeats: int = 2):
     return out
 
 
-def allowed(feats_row, t_row, mf):
-    """Per-level times with the single-CTA action masked where the device
-    would not let the network take it."""
+def allowed(t_row, stats_row, alpha: float = ALPHA, beta: float = BETA):
+    """Per-level times with the actions the device would not let the network
+    take masked: pull unless a Beamer test would pull (frontier edges >
+    unvisited edges / alpha, or |F| >= n / beta), the single-CTA push unless
+    the frontier is small.  stats_row: (|F|, frontier edges, unvisited edges, n)."""
+    nf, mf, mu, n = stats_row
     t = np.array(t_row, np.float64)
-    if mf > SOLO_MAX_EDGES:
+    if mf > SOLO_MAX_EDGES or nf > SOLO_MAX_VERTICES:
         t[4] = np.inf
+    if not (mf > mu / alpha or nf >= n / beta):
+        t[0] = np.inf
     return t
 
 
-def beamer_pushes(stats, alpha: float = 15.0, beta: float = 18.0):
-    """Per level, whether the Beamer rule (as the device applies it) pushes.
-    stats rows: (frontier, frontier_edges, unvisited_edges, n)."""
-    prev, out = 1, []
-    for nf, mf, mu, n in stats:
-        d = (0 if mf > mu / alpha else 1) if prev == 1 else (1 if nf < n / beta else 0)
-        out.append(d == 1)
-        prev = d
-    return out
-
-
 def samples_from_timings(tables):
-    """Samples = levels the Beamer rule pushes; label = fastest allowed push
-    variant; weight = log of the worst / best allowed push variant's time on
-    that level (scale-free, so the many short levels of a deep traversal count
-    as much as the few long levels of a shallow one), clipped to [0.01, 3]."""
+    """Samples = every level; label = fastest allowed action; weight = log of
+    the worst / best allowed action's time on that level (scale-free, so the
+    many short levels of a deep traversal count as much as the few long levels
+    of a shallow one), clipped to [0.01, 3]."""
     X, y, w = [], [], []
     for feats, t, mf, stats in tables:
         if len(t) == 0:
             continue
-        t = np.stack([allowed(feats[i], t[i], mf[i]) for i in range(len(t))])
-        t[:, 0] = np.inf  # pull is the rule's decision, not the network's
-        push = beamer_pushes(stats)
-        best_total = float(t[:, 1:].min(axis=1).sum()) or 1.0
+        t = np.stack([allowed(t[i], stats[i]) for i in range(len(t))])
         for i in range(len(t)):
-            if not push[i]:
-                continue
             X.append(feats[i])
             y.append(int(np.argmin(t[i])))
             fin = t[i][np.isfinite(t[i])]
@@ -146,7 +141,6 @@ def regret(t, choices) -> float:
     return float(sum(t[i, c] - t[i].min() for i, c in enumerate(choices)))
 
 
-SOLO_MAX_EDGES = 16384  # the device only lets the network pick action 4 below this
 
 
 def training_graphs(seed: int = 0xB10 + 50):

@@ -220,17 +220,53 @@ def test_pagerank_tolerance(byo, case):
     assert abs(res - wres[-1]) <= 1e-6 + 1e-3 * wres[-1]
 
 
+def test_pagerank_graph_replay_on_side_stream(byo):
+    # on a non-default stream the iterations are captured once as a CUDA graph
+    # and replayed; replays must give the same ranks, and a new iteration count
+    # or a structural change must re-capture
+    n, src, dst = graphgen.rmat_small(13, 16, 606)
+    ref = oracle.csr_build(n, src, dst)
+    g = byo.Graph(n, dev_u32(src), dev_u32(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        p1, _ = byo.byo_pagerank(g.handle, 0.85, 20)
+        p1 = p1.clone()
+        p2, _ = byo.byo_pagerank(g.handle, 0.85, 20)
+        p7, _ = byo.byo_pagerank(g.handle, 0.85, 7)
+        p7 = p7.clone()
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2)
+    for got, it in ((p1, 20), (p7, 7)):
+        want, _ = oracle.pagerank(ref, 0.85, it)
+        gotd = got.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(gotd - want) / want) <= PR_MAX_REL and np.sum(np.abs(gotd - want)) <= PR_L1
+    ins_s, ins_d = graphgen.rmat(13, 3000, 607)
+    byo.byo_insert_batch(g.handle, dev_u32(ins_s), dev_u32(ins_d))
+    dg = oracle.DynGraph(n, src, dst)
+    dg.insert(ins_s, ins_d)
+    with torch.cuda.stream(side):
+        p3, _ = byo.byo_pagerank(g.handle, 0.85, 20)
+    torch.cuda.synchronize()
+    want, _ = oracle.pagerank(dg.csr(), 0.85, 20)
+    gotd = p3.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(gotd - want) / want) <= PR_MAX_REL and np.sum(np.abs(gotd - want)) <= PR_L1
+    g.close()
+
+
 def test_triangle_count(byo, case):
     _, _, _, _, ref, g = case
     assert byo.byo_tc(g.handle) == oracle.tc(ref)
 
 
-@pytest.mark.parametrize("light_max,window", [(4, 16), (2, 4), (64, 1024)])
-def test_triangle_count_cta_path_and_windows(byo, monkeypatch, light_max, window):
-    # lower the light/heavy split and the window so that the CTA path and
-    # multi-window intersections run on small graphs
+@pytest.mark.parametrize("light_max,window,bitmap_bits", [(4, 16, 4), (2, 4, 4), (64, 1024, 4), (4, 16, 1 << 30),
+                                                          (2, 4, 3000), (64, 1024, 1 << 30)])
+def test_triangle_count_cta_path_and_windows(byo, monkeypatch, light_max, window, bitmap_bits):
+    # lower the light/heavy split, the window and the bitmap range so that the
+    # CTA path, hashed multi-window intersections and the bitmap run on small
+    # graphs (4 bits: every CTA centre hashed; 3000: both kinds)
     monkeypatch.setenv("BYO_TC_LIGHT_MAX", str(light_max))
     monkeypatch.setenv("BYO_TC_WINDOW", str(window))
+    monkeypatch.setenv("BYO_TC_BITMAP_BITS", str(bitmap_bits))
     for n, src, dst in (graphgen.rmat_small(13, 16, 44), _complete(90), graphgen.workload("tiny")):
         ref = oracle.csr_build(n, src, dst)
         g = byo.Graph(n, dev_u32(src), dev_u32(dst))
