@@ -260,10 +260,11 @@ __global__ void tc_set_last_kernel(uint64_t* dag_off, uint32_t n, uint64_t total
 
 // Work items.  Every DAG edge a->b is intersected from the side with the
 // shorter out-list: at centre a (walk N+(b), probe N+(a)) when d+(b) <= d+(a),
-// else at centre b (walk N+(a), probe N+(b)).  A task is one centre c (whose
-// N+(c) is hashed) and a chunk of at most kPartners partners: kind 0 takes
-// partners from N+(c), kind 1 from N-(c).  Tasks of centres with d+(c) <=
-// light_max go to the warp kernel, the others to the CTA kernel.
+// else at centre b (walk N+(a), probe N+(b)).  A warp task is one centre c
+// (whose N+(c) is hashed) with d+(c) <= light_max and a chunk of at most
+// kPartners partners: kind 0 takes partners from N+(c), kind 1 from N-(c).  A
+// CTA task is a whole larger centre (kind 2): its warps take groups of 32
+// partners, first from N+(c) then from N-(c), from a shared counter.
 constexpr uint32_t kPartners = 512;
 
 struct TcTask {
@@ -309,7 +310,7 @@ __global__ void tc_task_count_kernel(const uint64_t* __restrict__ dag_off, const
     uint32_t dm = (uint32_t)(in_off[c + 1] - in_off[c]);
     uint32_t t = (dp >= 2 ? chunks(dp) : 0) + (dp >= 1 ? chunks(dm) : 0);
     cnt_light[c] = dp <= light_max ? t : 0;
-    cnt_heavy[c] = dp <= light_max ? 0 : t;
+    cnt_heavy[c] = dp <= light_max ? 0 : 1;  // one task per CTA centre
   }
 }
 
@@ -319,7 +320,11 @@ __global__ void tc_task_fill_kernel(const uint64_t* __restrict__ dag_off, const 
   for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t dp = (uint32_t)(dag_off[c + 1] - dag_off[c]);
     uint32_t dm = (uint32_t)(in_off[c + 1] - in_off[c]);
-    TcTask* out = dp <= light_max ? light + pos_light[c] : heavy + pos_heavy[c];
+    if (dp > light_max) {
+      heavy[pos_heavy[c]] = TcTask{(uint32_t)c, 2u, 0u, dp};
+      continue;
+    }
+    TcTask* out = light + pos_light[c];
     if (dp >= 2)
       for (uint32_t lo = 0; lo < dp; lo += kPartners) *out++ = TcTask{(uint32_t)c, 0u, lo, min(dp, lo + kPartners)};
     if (dp >= 1)
@@ -351,23 +356,25 @@ struct SmemHash {
 struct SmemBits {
   const uint32_t* b;
   uint32_t base, nbits;
-  __device__ __forceinline__ bool contains(uint32_t x) const {
+  __device__ __forceinline__ uint32_t contains(uint32_t x) const {
     const uint32_t i = x - base;  // wraps for x < base
-    return i < nbits && ((b[i >> 5] >> (i & 31)) & 1u);
+    const uint32_t in = i < nbits;
+    const uint32_t word = b[(in ? i : 0u) >> 5];  // no branch: out-of-range ids read word 0
+    return __funnelshift_r(word, 0u, i) & in;     // the shift takes i mod 32
   }
 };
 
 // The warp walks the lists dag_col[vb .. vb+len) held by its lanes (len = 0
 // for lanes without a partner) and counts the ids the set contains.  Lists of
-// 32 ids or more are walked one at a time by the whole warp (coalesced, four
+// 32 ids or more are walked one at a time by the whole warp (coalesced, eight
 // loads in flight per lane, no bookkeeping per id); the shorter ones are
 // concatenated and walked 32 ids at a time, each lane finding the list its id
 // belongs to by a 5-step search over the lanes' prefix sums.
 template <typename Set>
-__device__ __forceinline__ uint64_t warp_count_group(const uint32_t* __restrict__ dag_col, uint64_t vb, uint32_t len,
+__device__ __forceinline__ uint32_t warp_count_group(const uint32_t* __restrict__ dag_col, uint64_t vb, uint32_t len,
                                                      const Set& set) {
   const uint32_t lane = lane_id();
-  uint64_t hits = 0;
+  uint32_t hits = 0;
   uint32_t longs = __ballot_sync(0xFFFFFFFFu, len >= 32);
   while (longs) {
     const int l = __ffs(longs) - 1;
@@ -376,12 +383,20 @@ __device__ __forceinline__ uint64_t warp_count_group(const uint32_t* __restrict_
     const uint32_t ln = __shfl_sync(0xFFFFFFFFu, len, l);
     const uint32_t* p = dag_col + b;
     uint32_t k = lane;
-    for (; k + 96 < ln; k += 128) {
-      const uint32_t w0 = __ldg(p + k), w1 = __ldg(p + k + 32), w2 = __ldg(p + k + 64), w3 = __ldg(p + k + 96);
-      hits += set.contains(w0);
-      hits += set.contains(w1);
-      hits += set.contains(w2);
-      hits += set.contains(w3);
+    for (; k + 224 < ln; k += 256) {
+      uint32_t w[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = __ldg(p + k + 32 * j);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) hits += set.contains(w[j]);
+    }
+    if (k + 96 < ln) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = __ldg(p + k + 32 * j);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) hits += set.contains(w[j]);
+      k += 128;
     }
     for (; k < ln; k += 32) hits += set.contains(__ldg(p + k));
   }
@@ -405,7 +420,7 @@ __device__ __forceinline__ uint64_t warp_count_group(const uint32_t* __restrict_
     }
     const uint32_t oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
     const uint64_t ob = __shfl_sync(0xFFFFFFFFu, vb, owner);
-    if (e < total && set.contains(__ldg(dag_col + ob + (e - oex)))) ++hits;
+    if (e < total) hits += set.contains(__ldg(dag_col + ob + (e - oex)));
   }
   return hits;
 }
@@ -426,21 +441,35 @@ __device__ __forceinline__ void partner_list(const uint64_t* __restrict__ dag_of
 }
 
 // Walks the partners [t.lo, t.hi) of a task with `warps` warps (this one is
-// warp `w`) and counts the ids of their out-lists that `set` contains.
+// warp `w`) and counts the ids of their out-lists that `set` contains.  The
+// partner ids and out-list bounds of the next two groups are loaded while the
+// current group is walked.
 template <typename Set>
 __device__ __forceinline__ uint64_t walk_partners(const uint64_t* __restrict__ dag_off,
                                                   const uint32_t* __restrict__ dag_col, const uint32_t* partners,
                                                   const TcTask& t, uint32_t dc, uint32_t w, uint32_t warps,
                                                   const Set& set) {
+  const uint32_t lane = lane_id(), step = warps * 32;
   uint64_t hits = 0;
-  for (uint32_t k0 = t.lo + w * 32; k0 < t.hi; k0 += warps * 32) {
-    const uint32_t k = k0 + lane_id();
-    const bool has = k < t.hi;
-    const uint32_t p = has ? __ldg(partners + k) : 0;
-    uint64_t vb;
-    uint32_t len;
-    partner_list(dag_off, has, p, t.kind, dc, &vb, &len);
+  uint32_t k0 = t.lo + w * 32;
+  bool has = k0 + lane < t.hi;
+  uint32_t p = has ? __ldg(partners + k0 + lane) : 0;
+  uint64_t vb;
+  uint32_t len;
+  partner_list(dag_off, has, p, t.kind, dc, &vb, &len);
+  bool has1 = k0 + step + lane < t.hi;
+  uint32_t p1 = has1 ? __ldg(partners + k0 + step + lane) : 0;
+  for (; k0 < t.hi; k0 += step) {
+    uint64_t vb1;
+    uint32_t len1;
+    partner_list(dag_off, has1, p1, t.kind, dc, &vb1, &len1);  // group k0 + step
+    const bool has2 = k0 + 2 * step + lane < t.hi;
+    const uint32_t p2 = has2 ? __ldg(partners + k0 + 2 * step + lane) : 0;
     hits += warp_count_group(dag_col, vb, len, set);
+    vb = vb1;
+    len = len1;
+    has1 = has2;
+    p1 = p2;
   }
   return hits;
 }
@@ -526,10 +555,76 @@ constexpr uint32_t kHeavyWords = kWindow + 8 + kHeavyTable;  // 32-bit words of 
 constexpr uint32_t kBitmapBits = 32 * (kHeavyWords & ~3u);   // bitmap capacity of the same memory
 constexpr size_t kHeavySmem = (size_t)kHeavyWords * sizeof(uint32_t);
 
-// One CTA per task.  Bitmap mode (the n - 1 - c ranks above c fit in
-// `bitmap_bits`): N+(c) is set into a bitmap of that range, read straight
-// from the DAG, and kept while the CTA's next task has the same centre.
-// Hash mode: N+(c) is staged by TMA in windows of `window` ids, each hashed.
+// The partners of group g of a CTA centre: groups [0, g0) hold N+(c) in 32s,
+// groups [g0, gt) hold N-(c).  Returns this lane's partner (has = false past
+// the end of the list) and its kind.
+struct CentreGroups {
+  const uint32_t* out;  // N+(c)
+  const uint32_t* in;   // N-(c)
+  uint32_t dc, dm, g0, gt;
+  __device__ __forceinline__ uint32_t partner(uint32_t g, bool* has, uint32_t* kind) const {
+    const uint32_t lane = lane_id();
+    if (g < g0) {
+      const uint32_t k = g * 32 + lane;
+      *kind = 0;
+      *has = k < dc;
+      return *has ? __ldg(out + k) : 0u;
+    }
+    const uint32_t k = (g - g0) * 32 + lane;
+    *kind = 1;
+    *has = k < dm;
+    return *has ? __ldg(in + k) : 0u;
+  }
+};
+
+__device__ __forceinline__ uint32_t grab_group(uint32_t* gctr) {
+  uint32_t g = 0;
+  if (lane_id() == 0) g = atomicAdd(gctr, 1u);
+  return __shfl_sync(0xFFFFFFFFu, g, 0);
+}
+
+// A warp's share of a CTA centre: groups taken from the CTA's counter until
+// they run out.  The partner ids of the group after next and the out-list
+// bounds of the next group are loaded while the current group is walked.
+template <typename Set>
+__device__ __forceinline__ uint32_t walk_groups(const uint64_t* __restrict__ dag_off,
+                                                const uint32_t* __restrict__ dag_col, const CentreGroups& cg,
+                                                uint32_t* gctr, const Set& set) {
+  uint32_t g = grab_group(gctr);
+  if (g >= cg.gt) return 0;
+  bool has;
+  uint32_t kind;
+  uint32_t p = cg.partner(g, &has, &kind);
+  uint64_t vb;
+  uint32_t len;
+  partner_list(dag_off, has, p, kind, cg.dc, &vb, &len);
+  uint32_t gn = grab_group(gctr);
+  bool hasn = false;
+  uint32_t kindn = 0, pn = gn < cg.gt ? cg.partner(gn, &hasn, &kindn) : 0u;
+  uint32_t hits = 0;
+  while (true) {
+    uint64_t vbn;
+    uint32_t lenn;
+    partner_list(dag_off, hasn, pn, kindn, cg.dc, &vbn, &lenn);
+    const uint32_t gnn = gn < cg.gt ? grab_group(gctr) : cg.gt;
+    bool hasnn = false;
+    uint32_t kindnn = 0, pnn = gnn < cg.gt ? cg.partner(gnn, &hasnn, &kindnn) : 0u;
+    hits += warp_count_group(dag_col, vb, len, set);
+    if (gn >= cg.gt) break;
+    vb = vbn;
+    len = lenn;
+    gn = gnn;
+    hasn = hasnn;
+    kindn = kindnn;
+    pn = pnn;
+  }
+  return hits;
+}
+
+// One CTA per centre, the largest centres (highest ranks) first.  Bitmap mode
+// (the n - 1 - c ranks above c fit in `bitmap_bits`): N+(c) is set into a
+// bitmap of that range, read straight from the DAG.  Hash mode: N+(c) is
+// staged by TMA in windows of `window` ids, each hashed.
 __global__ void __launch_bounds__(kTcThreads, 4) tc_heavy_kernel(const uint64_t* __restrict__ dag_off,
                                                               const uint32_t* __restrict__ dag_col,
                                                               const uint64_t* __restrict__ in_off,
@@ -542,47 +637,38 @@ __global__ void __launch_bounds__(kTcThreads, 4) tc_heavy_kernel(const uint64_t*
   uint32_t* table = win + kWindow + 8;
   __shared__ __align__(8) uint64_t bar;
   __shared__ bool ok_s;
-  __shared__ uint32_t idx_s[2], lo_s, hi_s;
-  const uint32_t lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ uint32_t idx_s, lo_s, hi_s, gctr;
+  const uint32_t lane = lane_id();
   uint32_t* err = ctr + 3;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t phase = 0;
-  uint32_t have = kInf;  // centre whose bitmap is in shared memory
   uint64_t hits = 0;
-  // The task index alternates between two slots: a task may pass without a
-  // barrier (same centre, bitmap kept), and thread 0 must not overwrite the
-  // slot another thread has yet to read.
-  for (uint32_t it = 0;; ++it) {
-    if (threadIdx.x == 0) idx_s[it & 1] = atomicAdd(ctr + 4, 1u);
-    __syncthreads();
-    const uint32_t idx = idx_s[it & 1];
+  while (true) {
+    if (threadIdx.x == 0) idx_s = atomicAdd(ctr + 4, 1u);
+    __syncthreads();  // also: every thread is done with the previous centre
+    const uint32_t idx = idx_s;
     if (idx >= ntasks) break;
-    const TcTask t = tasks[idx];
-    const uint32_t c = t.c;
-    const uint64_t beg = dag_off[c], end = dag_off[c + 1];
-    const uint32_t dc = (uint32_t)(end - beg);
-    const uint32_t* partners = t.kind == 0 ? dag_col + beg : in_col + in_off[c];
+    const uint32_t c = tasks[ntasks - 1 - idx].c;
+    const uint64_t beg = dag_off[c], end = dag_off[c + 1], ib = in_off[c];
+    const uint32_t dc = (uint32_t)(end - beg), dm = (uint32_t)(in_off[c + 1] - ib);
+    const uint32_t g0 = (dc + 31) / 32;
+    const CentreGroups cg{dag_col + beg, in_col + ib, dc, dm, g0, g0 + (dm + 31) / 32};
     const uint32_t above = n - 1 - c;  // N+(c) lies in the ranks (c, n)
     if (above <= bitmap_bits) {
-      if (c != have) {
-        const uint32_t words = (above + 127) / 128 * 4;
-        __syncthreads();  // every thread is done with the previous set
-        uint4* w4 = reinterpret_cast<uint4*>(win);
-        for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x) w4[i] = make_uint4(0u, 0u, 0u, 0u);
-        __syncthreads();
-        for (uint32_t k = threadIdx.x; k < dc; k += blockDim.x) {
-          const uint32_t x = __ldg(dag_col + beg + k) - (c + 1);
-          atomicOr(win + (x >> 5), 1u << (x & 31));
-        }
-        __syncthreads();
-        have = c;
+      const uint32_t words = (above + 127) / 128 * 4;
+      uint4* w4 = reinterpret_cast<uint4*>(win);
+      for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (threadIdx.x == 0) gctr = 0;
+      __syncthreads();  // idx_s is read by every thread before thread 0 rewrites it
+      for (uint32_t k = threadIdx.x; k < dc; k += blockDim.x) {
+        const uint32_t x = __ldg(dag_col + beg + k) - (c + 1);
+        atomicOr(win + (x >> 5), 1u << (x & 31));
       }
-      SmemBits set{win, c + 1, above};
-      hits += walk_partners(dag_off, dag_col, partners, t, dc, w, nw, set);
+      __syncthreads();
+      hits += walk_groups(dag_off, dag_col, cg, &gctr, SmemBits{win, c + 1, above});
       continue;
     }
-    have = kInf;
     for (uint64_t wb = beg; wb < end; wb += window) {
       uint64_t we = wb + window < end ? wb + window : end;
       uint64_t a0 = wb & ~3ull, a1 = (we + 3) & ~3ull;
@@ -594,6 +680,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) tc_heavy_kernel(const uint64_t*
       if (threadIdx.x == 0) {
         lo_s = kInf;
         hi_s = 0;
+        gctr = 0;
         bulk_load(win, dag_col + a0, (uint32_t)((a1 - a0) * 4), &bar);
         ok_s = mbar_wait(&bar, phase, err, limit_ns);
       }
@@ -622,8 +709,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) tc_heavy_kernel(const uint64_t*
         atomicMax(&hi_s, mx);
       }
       __syncthreads();
-      SmemHash set{table, slots - 1, 32 - bits, lo_s, hi_s};
-      hits += walk_partners(dag_off, dag_col, partners, t, dc, w, nw, set);
+      hits += walk_groups(dag_off, dag_col, cg, &gctr, SmemHash{table, slots - 1, 32 - bits, lo_s, hi_s});
     }
   }
   uint64_t sum = hits;
