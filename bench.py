@@ -143,16 +143,19 @@ def measured_peaks():
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if one exists for
-    this kernel and workload (profiles/traffic.json); None otherwise."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes (read + write) per launch from the committed ncu summary
+    profiles/traffic.md (a table | workload | kernel | bytes | ... |), if it has
+    a row for this kernel and workload; None otherwise."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
     try:
         with open(p) as f:
-            d = json.load(f)
-        e = d.get(workload, {}).get(kernel)
-        return None if e is None else float(e)
+            for line in f:
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) >= 3 and cells[0] == workload and cells[1] == kernel:
+                    return float(cells[2].replace(",", ""))
     except (OSError, ValueError):
         return None
+    return None
 
 
 def sched_struct(byo, name, mlp=None):
@@ -180,9 +183,9 @@ def load_mlp(byo):
 def algo_bytes(kernel: str, n: int, m: int, off: int, trace=None) -> float | None:
     """Bytes the method must move per launch of `kernel` (a model, not a counter)."""
     if kernel == "pr_iter":
-        # offsets + neighbour ids + one read of every contribution + vertex order
-        # + read/write rank + write next contribution
-        return off * (n + 1) + 4.0 * m + 4.0 * n * 5
+        # offsets of the degree-ordered copy (always 8 bytes) + neighbour ids + one
+        # read of every contribution + read/write rank + write next contribution
+        return 8.0 * (n + 1) + 4.0 * m + 16.0 * n
     if kernel == "bfs_persistent" and trace is not None:
         b = 8.0 * n + n / 8.0  # level + parent init, visited bits
         for r in trace:
@@ -552,7 +555,11 @@ def main():
     for name, (nl, ms) in ranked:
         if name == "tc_count":
             tc_work = byo.byo_tc_work(g.handle)
-            b = 4.0 * (tc_work[0] + tc_work[1])  # ids of both out-lists of every DAG edge
+            # what this intersection must read: the shorter out-list of every DAG
+            # edge (sum of min(d+u, d+v) ids), every partner's id and out-list
+            # bounds (each DAG edge is a partner once from each end: m ids,
+            # 2 x 8-byte offsets each), every centre's out-list once (m/2 ids)
+            b = 4.0 * tc_work[2] + 20.0 * m + 2.0 * m
         elif name == "bfs_persistent":
             b = statistics.mean(bfs_bytes)
         else:
@@ -566,9 +573,13 @@ def main():
                 "algorithmic_bytes_per_launch": b, "avg_launch_ms": round(avg_ms, 4),
                 "share": round(ms / tot, 4), "peak_kind": peak_kind}
         if tc_work is not None:
+            merge_b = 4.0 * (tc_work[0] + tc_work[1])
             roof["tc_ids_walked"] = tc_work[2]
-            roof["note"] = ("hash-probe intersection: issue/latency bound, far below the HBM roofline; "
-                            "bytes = both out-lists of every DAG edge")
+            roof["merge_model_bytes"] = merge_b
+            roof["merge_model_frac"] = round(merge_b / (avg_ms / 1e3) / 1e9 / peak, 4)
+            roof["note"] = ("bytes = shorter out-list of each DAG edge + partner ids and bounds + centre lists "
+                            "(the walk-shorter/probe-set method); mostly L2 hits, latency/issue bound. "
+                            "merge_model_* = both out-lists of every DAG edge (a sorted merge's reads)")
         break
     kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot, 4)}
                     for k, v in ranked}

@@ -705,7 +705,7 @@ __device__ void fast_solo(const BfsArgs<G>& a, BfsShared& S, SoloShared& Q, uint
 }
 
 template <typename G, bool kParents>
-__global__ void __launch_bounds__(kBfsThreads) bfs_kernel(BfsArgs<G> a) {
+__global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
   __shared__ BfsShared S;
   __shared__ SoloShared Q;
   __shared__ float wsm[kMlpParams];

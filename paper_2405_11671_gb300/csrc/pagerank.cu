@@ -181,7 +181,8 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
 }
 
 // Compensated sum of c[ids[k]] for k = first, first+stride, ... < len, with
-// eight independent id loads and eight independent gathers in flight per step.
+// eight independent id loads and eight independent gathers in flight per step
+// (four, two and one for the tail).
 __device__ __forceinline__ void gather_sum(Comp& acc, const uint32_t* __restrict__ ids, uint32_t first, uint32_t len,
                                            uint32_t stride, const float* __restrict__ c) {
   uint32_t k = first;
@@ -195,7 +196,25 @@ __device__ __forceinline__ void gather_sum(Comp& acc, const uint32_t* __restrict
 #pragma unroll
     for (int j = 0; j < 8; ++j) neumaier_add(acc, x[j]);
   }
-  for (; k < len; k += stride) neumaier_add(acc, __ldg(c + ld_stream(ids + k)));
+  if (k + 3 * stride < len) {  // the tail: four, two, one more
+    uint32_t u[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u[j] = ld_stream(ids + k + j * stride);
+    float x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = __ldg(c + u[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) neumaier_add(acc, x[j]);
+    k += 4 * stride;
+  }
+  if (k + stride < len) {
+    const uint32_t u0 = ld_stream(ids + k), u1 = ld_stream(ids + k + stride);
+    const float x0 = __ldg(c + u0), x1 = __ldg(c + u1);
+    neumaier_add(acc, x0);
+    neumaier_add(acc, x1);
+    k += 2 * stride;
+  }
+  if (k < len) neumaier_add(acc, __ldg(c + ld_stream(ids + k)));
 }
 
 // Low-degree vertices (degree < small_lim) are processed in id order, 32 per
@@ -227,7 +246,7 @@ __device__ __forceinline__ void pr_stream_warp(const G& g, uint32_t v0, uint32_t
   const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
   const uint32_t excl = incl - len;
   Comp acc{0.f, 0.f};
-  constexpr int kU = 4;  // chunks of 32 ids per step: kU independent gathers per lane in flight
+  constexpr int kU = 2;  // chunks of 32 ids per step: kU independent gathers per lane in flight
   for (uint32_t e00 = 0; e00 < total; e00 += 32 * kU) {
     int key[kU];
     uint32_t id[kU];
@@ -273,7 +292,7 @@ __device__ __forceinline__ void pr_stream_warp(const G& g, uint32_t v0, uint32_t
 }
 
 template <typename G>
-__global__ void __launch_bounds__(kPrThreads) pr_iter_kernel(G g, VBins bins, CtaChunks hubs, uint32_t small_lim,
+__global__ void __launch_bounds__(kPrThreads, 8) pr_iter_kernel(G g, VBins bins, CtaChunks hubs, uint32_t small_lim,
                                                              uint32_t stream_n, float damping, const float* __restrict__ c,
                                                              float* __restrict__ cn, float* ranks, float2* part,
                                                              uint32_t* hub_ticket, double* partials, double* scal,
@@ -431,7 +450,7 @@ byo_status ensure_pr_work(byo_graph* g, uint32_t blocks, uint64_t parts, uint64_
 template <typename G>
 byo_status run_pr(byo_graph* g, G view, float damping, uint32_t iters, float* ranks, double* host_residual,
                   cudaStream_t s) {
-  constexpr int kSmallBucket = 5;  // degree < 32 goes to the warp stream
+  constexpr int kSmallBucket = 8;  // degree < 256 goes to the warp stream
   const uint32_t n = g->n;
   // bins of the relabelled copy: bucket b holds the ranks [bstart[b], bstart[b+1])
   VBins bins = make_vbins(g, kSmallBucket, 10, kPrThreads);

@@ -30,7 +30,7 @@
 namespace byo {
 
 constexpr uint32_t kLightMax = 256;   // capacity of a warp's shared-memory slice (ids)
-constexpr uint32_t kWindow = 4096;    // capacity of a CTA's shared-memory window (ids)
+constexpr uint32_t kWindow = 2048;    // capacity of a CTA's shared-memory window (ids)
 constexpr int kTcThreads = 256;
 
 // The light/heavy split, the window length and the bitmap range can be
@@ -625,7 +625,7 @@ __device__ __forceinline__ uint32_t walk_groups(const uint64_t* __restrict__ dag
 // (the n - 1 - c ranks above c fit in `bitmap_bits`): N+(c) is set into a
 // bitmap of that range, read straight from the DAG.  Hash mode: N+(c) is
 // staged by TMA in windows of `window` ids, each hashed.
-__global__ void __launch_bounds__(kTcThreads, 4) tc_heavy_kernel(const uint64_t* __restrict__ dag_off,
+__global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const uint64_t* __restrict__ dag_off,
                                                               const uint32_t* __restrict__ dag_col,
                                                               const uint64_t* __restrict__ in_off,
                                                               const uint32_t* __restrict__ in_col,
