@@ -40,6 +40,7 @@ namespace byo {
 constexpr int kBfsThreads = 256;
 constexpr int kPullThreadMax = 32;  // pull: degrees above this are scanned by a whole warp
 constexpr uint32_t kChunk = 2048;   // push: edges per CTA work item in the CTA bin
+static_assert(kChunk == 1u << 11, "bucket b >= 12 splits into 2^(b - 11) CTA work items");
 constexpr uint32_t kTraceCap = 1u << 16;
 
 struct BfsCtl {
@@ -268,35 +269,47 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, uint32_t L, int nx
   const uint32_t* fb = a.fb + (size_t)(L & 1) * a.nw;
   uint32_t* fbn = a.fb + (size_t)((L + 1) & 1) * a.nw;
   const uint32_t n = a.g.num_vertices();
+  // the visited bits of a warp's next word are loaded while it works on the current one
+  uint32_t vw_next = gwarp < a.nw ? ld_cg(a.vis + gwarp) : ~0u;
   for (uint32_t w = gwarp; w < a.nw; w += nwarps) {
-    uint32_t vw = ld_cg(a.vis + w);
+    const uint32_t vw = vw_next;
     uint32_t v = w * 32 + lane;
     bool todo = v < n && !((vw >> lane) & 1u);
+    Seg s{nullptr, 0};
+    if (todo) s = a.g.seg(v);
+    vw_next = w + nwarps < a.nw ? ld_cg(a.vis + w + nwarps) : ~0u;
     if (__ballot_sync(0xFFFFFFFFu, todo) == 0) {
       if (lane == 0) fbn[w] = 0;
       continue;
     }
-    Seg s{nullptr, 0};
-    if (todo) s = a.g.seg(v);
     bool found = false;
     uint32_t par = kInf;
     if (todo && s.len <= (uint32_t)kPullThreadMax && s.len > 0) {
+      // eight ids (two 16-byte loads) and their eight frontier words in flight
+      // per step; the scan stops at the first frontier neighbour
       const uint32_t* al = align16_down(s.p);
       uint32_t head = (uint32_t)(s.p - al);
       uint32_t end = head + s.len;
-      for (uint32_t i = 0; i < end && !found; i += 4) {
-        uint4 q = ld_nc_v4(al + i);
-        uint32_t x[4] = {q.x, q.y, q.z, q.w};
+      for (uint32_t i = 0; i < end && !found; i += 8) {
+        const uint4 q0 = ld_nc_v4(al + i);
+        const uint4 q1 = i + 4 < end ? ld_nc_v4(al + i + 4) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t x[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        uint32_t hit = kInf, hf = 8;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint32_t idx = i + c;
-          if (!found && idx >= head && idx < end) {
-            ++acc_scan;
-            if (in_frontier(fb, x[c])) {
-              found = true;
-              par = x[c];
-            }
+        for (int c = 7; c >= 0; --c) {  // the lowest hit wins
+          const uint32_t idx = i + c;
+          if (idx >= head && idx < end && in_frontier(fb, x[c])) {
+            hit = x[c];
+            hf = (uint32_t)c;
           }
+        }
+        const uint32_t lo = head > i ? head : i;
+        if (hf < 8) {
+          found = true;
+          par = hit;
+          acc_scan += i + hf + 1 - lo;  // ids up to and including the hit
+        } else {
+          acc_scan += (end < i + 8 ? end : i + 8) - lo;
         }
       }
     }

@@ -37,7 +37,6 @@ void dyn_free(DynStore* d) {
 
 namespace {
 
-constexpr int kDynThreads = 256;
 
 __host__ __device__ inline uint32_t run_class(uint32_t deg) {
   // smallest c with (2^c blocks * 32 ids) >= deg

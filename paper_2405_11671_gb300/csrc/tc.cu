@@ -287,7 +287,7 @@ __global__ void tc_work_kernel(const uint64_t* __restrict__ dag_off, const uint6
     for (uint64_t i = b; i < e; ++i) {  // in-neighbour a of c: edge a->c
       const uint32_t a = in_col[i];
       const unsigned long long da = dag_off[a + 1] - dag_off[a];
-      mn += da < dp ? da : dp;
+      mn += da < dp ? (da >= 2 ? da : 0) : dp;  // a kind-1 out-list of length 1 is not walked
     }
   }
 #pragma unroll
@@ -308,7 +308,8 @@ __global__ void tc_task_count_kernel(const uint64_t* __restrict__ dag_off, const
   for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t dp = (uint32_t)(dag_off[c + 1] - dag_off[c]);
     uint32_t dm = (uint32_t)(in_off[c + 1] - in_off[c]);
-    uint32_t t = (dp >= 2 ? chunks(dp) : 0) + (dp >= 1 ? chunks(dm) : 0);
+    // kind 0 needs two out-neighbours; kind 1 a partner with 2 <= d+(p) < d+(c)
+    uint32_t t = (dp >= 2 ? chunks(dp) : 0) + (dp >= 3 ? chunks(dm) : 0);
     cnt_light[c] = dp <= light_max ? t : 0;
     cnt_heavy[c] = dp <= light_max ? 0 : 1;  // one task per CTA centre
   }
@@ -327,7 +328,7 @@ __global__ void tc_task_fill_kernel(const uint64_t* __restrict__ dag_off, const 
     TcTask* out = light + pos_light[c];
     if (dp >= 2)
       for (uint32_t lo = 0; lo < dp; lo += kPartners) *out++ = TcTask{(uint32_t)c, 0u, lo, min(dp, lo + kPartners)};
-    if (dp >= 1)
+    if (dp >= 3)
       for (uint32_t lo = 0; lo < dm; lo += kPartners) *out++ = TcTask{(uint32_t)c, 1u, lo, min(dm, lo + kPartners)};
   }
 }
@@ -426,7 +427,9 @@ __device__ __forceinline__ uint32_t warp_count_group(const uint32_t* __restrict_
 }
 
 // A lane's partner p: its out-list, kept only on the side that walks the
-// shorter list (kind 0: d+(p) <= d+(c); kind 1: d+(p) < d+(c)).
+// shorter list (kind 0: d+(p) <= d+(c); kind 1: d+(p) < d+(c)).  A kind-1
+// partner's out-list holds c itself, which N+(c) does not, so one of length 1
+// cannot meet N+(c) and is skipped.
 __device__ __forceinline__ void partner_list(const uint64_t* __restrict__ dag_off, bool has, uint32_t p, uint32_t kind,
                                              uint32_t dc, uint64_t* vb, uint32_t* len) {
   *vb = 0;
@@ -434,7 +437,7 @@ __device__ __forceinline__ void partner_list(const uint64_t* __restrict__ dag_of
   if (!has) return;
   uint64_t b = dag_off[p];
   uint32_t d = (uint32_t)(dag_off[p + 1] - b);
-  if (kind == 0 ? d <= dc : d < dc) {
+  if (kind == 0 ? d <= dc : (d < dc && d >= 2)) {
     *vb = b;
     *len = d;
   }
