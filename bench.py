@@ -196,8 +196,10 @@ def algo_bytes(kernel: str, n: int, m: int, off: int, trace=None) -> float | Non
         nxt = [r.frontier for r in trace[1:]] + [0]
         b += 12.0 * sum(nxt)
         return b
-    if kernel == "cc_hook":
-        return off * (n + 1) + 4.0 * n + 4.0 * (m / 2 + n) + 8.0 * (m / 2)
+    if kernel == "cc_sample":
+        # identity labels, two sampling rounds (offsets, one neighbour id and the
+        # two endpoints' labels each), one flattening pass (read + write)
+        return 4.0 * n + 2 * (off * (n + 1) + 4.0 * n + 8.0 * n) + 8.0 * n
     if kernel == "tc_outdeg" or kernel == "tc_fill":
         return off * (n + 1) + 4.0 * n + 4.0 * m + 2 * off * m + (4.0 * m / 2 if kernel == "tc_fill" else 4.0 * n)
     return None
