@@ -390,7 +390,18 @@ __global__ void __launch_bounds__(kPrThreads) pr_relabel_kernel(G g, VBins bins,
     const uint32_t v = vbins_vertex(bins, i);
     const Seg sg = g.seg(v);
     uint32_t* out = rcol + roff[__ldg(rank + v)];
-    for (uint32_t k = first; k < sg.len; k += step) out[k] = __ldg(rank + ld_stream(sg.p + k));
+    // eight ids, then their eight ranks, in flight before the stores
+    for (uint32_t k = first; k < sg.len; k += 8 * step) {
+      uint32_t u[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) u[j] = k + j * step < sg.len ? ld_stream(sg.p + k + j * step) : 0u;
+      uint32_t ru[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ru[j] = k + j * step < sg.len ? __ldg(rank + u[j]) : 0u;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (k + j * step < sg.len) out[k + j * step] = ru[j];
+    }
   }
 }
 

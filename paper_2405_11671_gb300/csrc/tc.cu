@@ -141,7 +141,13 @@ __global__ void __launch_bounds__(kTcThreads) tc_outdeg_kernel(G g, VBins bins, 
       Seg s = g.seg(v);
       const uint32_t rv = __ldg(rank + v);
       uint32_t c = 0;
-      for (uint32_t k = 0; k < s.len; ++k) c += __ldg(rank + __ldg(s.p + k)) > rv;
+      for (uint32_t k = 0; k < s.len; k += 8) {  // eight ids and their ranks in flight
+        uint32_t u[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) u[j] = k + j < s.len ? __ldg(s.p + k + j) : 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c += k + j < s.len && __ldg(rank + u[j]) > rv;
+      }
       outdeg[rv] = c;
       indeg[rv] = s.len - c;
     }
@@ -151,7 +157,13 @@ __global__ void __launch_bounds__(kTcThreads) tc_outdeg_kernel(G g, VBins bins, 
       Seg s = g.seg(v);
       const uint32_t rv = __ldg(rank + v);
       uint32_t c = 0;
-      for (uint32_t k = lane; k < s.len; k += 32) c += __ldg(rank + __ldg(s.p + k)) > rv;
+      for (uint32_t k = lane; k < s.len; k += 128) {  // four chunks in flight
+        uint32_t u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = k + 32 * j < s.len ? __ldg(s.p + k + 32 * j) : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c += k + 32 * j < s.len && __ldg(rank + u[j]) > rv;
+      }
       c = __reduce_add_sync(0xFFFFFFFFu, c);
       if (lane == 0) {
         outdeg[rv] = c;
@@ -197,10 +209,18 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
       Seg s = g.seg(v);
       const uint32_t rv = __ldg(rank + v);
       uint64_t o = dag_off[rv], q = in_off[rv];
-      for (uint32_t k = 0; k < s.len; ++k) {
-        uint32_t ru = __ldg(rank + __ldg(s.p + k));
-        if (ru > rv) dag_col[o++] = ru;
-        else in_col[q++] = ru;
+      for (uint32_t k = 0; k < s.len; k += 8) {  // eight ids and their ranks in flight before the stores
+        uint32_t u[8], ru[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) u[j] = k + j < s.len ? __ldg(s.p + k + j) : 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ru[j] = k + j < s.len ? __ldg(rank + u[j]) : 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (k + j >= s.len) break;
+          if (ru[j] > rv) dag_col[o++] = ru[j];
+          else in_col[q++] = ru[j];
+        }
       }
     }
   } else if (r.role == kRoleWarp) {
@@ -209,16 +229,26 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
       Seg s = g.seg(v);
       const uint32_t rv = __ldg(rank + v);
       uint64_t o = dag_off[rv], q = in_off[rv];
-      for (uint32_t base = 0; base < s.len; base += 32) {
-        uint32_t k = base + lane;
-        uint32_t ru = k < s.len ? __ldg(rank + __ldg(s.p + k)) : 0;
-        bool keep = k < s.len && ru > rv;
-        bool back = k < s.len && !keep;
-        uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep), bbk = __ballot_sync(0xFFFFFFFFu, back);
-        if (keep) dag_col[o + __popc(bal & lanemask_lt())] = ru;
-        if (back) in_col[q + __popc(bbk & lanemask_lt())] = ru;
-        o += __popc(bal);
-        q += __popc(bbk);
+      for (uint32_t base = 0; base < s.len; base += 128) {  // four chunks' ranks in flight before the stores
+        uint32_t ru[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t k = base + 32 * j + lane;
+          ru[j] = k < s.len ? __ldg(s.p + k) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ru[j] = base + 32 * j + lane < s.len ? __ldg(rank + ru[j]) : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t k = base + 32 * j + lane;
+          bool keep = k < s.len && ru[j] > rv;
+          bool back = k < s.len && !keep;
+          uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep), bbk = __ballot_sync(0xFFFFFFFFu, back);
+          if (keep) dag_col[o + __popc(bal & lanemask_lt())] = ru[j];
+          if (back) in_col[q + __popc(bbk & lanemask_lt())] = ru[j];
+          o += __popc(bal);
+          q += __popc(bbk);
+        }
       }
     }
   } else {
