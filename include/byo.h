@@ -211,10 +211,12 @@ byo_status byo_bfs_trace(const byo_graph* g, byo_bfs_iter* host_records, uint32_
 
 /*
  * Connected components (the paper's connectivity algorithm, Section 6.2):
- * labels[v] = the minimum vertex id of v's component.  Concurrent union-find
- * over every edge, hooking the larger root under the smaller, then full path
+ * labels[v] = the minimum vertex id of v's component.  Concurrent union-find,
+ * hooking the larger root under the smaller, with the edges taken in Afforest
+ * order (each vertex's first two neighbours, then every neighbour of the
+ * vertices outside the largest sampled component), then full path
  * compression.  labels is caller-owned device memory of n entries and doubles
- * as the union-find parent array.  Errors: INVALID_ARG, CUDA.
+ * as the union-find parent array.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA.
  */
 byo_status byo_cc(const byo_graph* g, uint32_t* labels, void* stream);
 
@@ -223,9 +225,12 @@ byo_status byo_cc(const byo_graph* g, uint32_t* labels, void* stream);
  *   p_0 = 1/n,  p_{t+1}(v) = (1-d)/n + d*( sum_{u in N(v)} p_t(u)/deg(u) + D_t/n ),
  * D_t = sum of p_t over degree-0 vertices.  Contributions p/deg are FP32 and
  * summed per vertex with compensated (Neumaier) FP32 arithmetic; the dangling
- * mass D_t and the L1 residual are reduced in FP64.  host_residual (nullable)
- * receives sum_v |p_iters(v) - p_{iters-1}(v)|; if non-NULL the call
- * synchronises.  Errors: INVALID_ARG (d outside [0,1], NULL ranks), CUDA.
+ * mass D_t and the L1 residual are reduced in FP64.  The iterations run on a
+ * copy of the graph relabelled by degree order that the call builds (library
+ * scratch of 4m + 16n bytes, kept with the graph); each vertex's sum keeps its
+ * neighbour order.  host_residual (nullable) receives
+ * sum_v |p_iters(v) - p_{iters-1}(v)|; if non-NULL the call synchronises.
+ * Errors: INVALID_ARG (d outside [0,1], NULL ranks), OUT_OF_MEMORY, CUDA.
  */
 byo_status byo_pagerank(const byo_graph* g, float damping, uint32_t iters, float* ranks, double* host_residual,
                         void* stream);
@@ -233,9 +238,12 @@ byo_status byo_pagerank(const byo_graph* g, float damping, uint32_t iters, float
 /*
  * Triangle count (Section 4.4: filter to a DAG, then intersect).  Each edge is
  * kept in the direction of increasing (degree, id); the count is the sum over
- * DAG edges u->v of |N+(u) intersect N+(v)|, with N+(u) staged in shared
- * memory by TMA bulk copies.  *host_count receives the number of triangles;
- * synchronises.  Errors: INVALID_ARG, OUT_OF_MEMORY, TIMEOUT, CUDA.
+ * DAG edges u->v of |N+(u) intersect N+(v)|.  The DAG is stored with vertices
+ * relabelled by that order; each DAG edge is intersected from the side with
+ * the shorter out-list, the other side's N+ held in shared memory (staged by
+ * TMA bulk copies and hashed, or a bitmap of the ranks above a high-degree
+ * vertex).  *host_count receives the number of triangles; synchronises.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, TIMEOUT, CUDA.
  */
 byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
 
