@@ -8,10 +8,16 @@
 // IPDPS 2018), which the paper's comparison with other frameworks credits with
 // examining far fewer than all m edges: every vertex is first linked to a
 // sample of its neighbours (its first two list entries); the root most of an
-// even sample of vertices share is then taken as the large component; a final
-// pass links every neighbour of the vertices outside that component only.  An edge whose two
-// ends are both in the large component needs no link, and an edge with one end
-// outside is linked from that end, so every edge is covered.
+// even sample of vertices share is then taken as the large component, and the
+// vertices in it at that moment are marked in a bit array.  A final pass
+// visits only the unmarked vertices: each links its smaller neighbours, and
+// its larger neighbours that are marked.  So an edge between two marked
+// vertices needs no link (same component), an edge with one marked end is
+// linked from the other end, and an edge between two unmarked vertices is
+// linked from its larger end: every edge is covered.  When no component holds
+// half of the sample (a batch of many similar graphs) nothing is marked and
+// the final pass links every edge from its larger end alone, reading only
+// each list's ascending prefix of smaller neighbours.
 #include "byo_internal.cuh"
 #include "prof.cuh"
 #include "container.cuh"
@@ -102,45 +108,88 @@ __global__ void __launch_bounds__(kGiantSample) cc_giant_kernel(const uint32_t* 
     atomicMax(&best, ((unsigned long long)(t - lo + 1) << 32) | r[t]);
   }
   __syncthreads();
-  if (t == 0) *giant = (uint32_t)(best & 0xFFFFFFFFull);
+  if (t == 0) {
+    giant[0] = (uint32_t)(best & 0xFFFFFFFFull);
+    giant[1] = (uint32_t)(best >> 32) * 2 >= kGiantSample;  // a component of at least half the sample
+  }
 }
 
-// Final pass: the vertices outside the large component link every neighbour
-// (the first two again as well; repeated links are no-ops).  Threads, warps or CTA chunks by degree, as in the other kernels.
+// The vertices whose root is the large component's, one bit each (a snapshot
+// taken between the sampling and the final pass).  No vertex is marked when
+// no component holds half of the sample (many similar components, as in a
+// batch of graphs): the final pass then takes every edge from its larger end.
+__global__ void cc_mark_kernel(const uint32_t* p, uint32_t n, const uint32_t* giant_p, uint32_t* marked) {
+  const uint32_t giant = __ldg(giant_p), any = __ldg(giant_p + 1);
+  const uint32_t nw = (n + 31) / 32;
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+       w += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    uint32_t x = (uint32_t)w * 32 + lane_id();
+    bool in = false;
+    if (x < n) {
+      uint32_t px = ld_cg(p + x);
+      while (px != x) {
+        x = px;
+        px = ld_cg(p + x);
+      }
+      in = any && x == giant;
+    }
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, in);
+    if (lane_id() == 0) marked[w] = b;
+  }
+}
+
+__device__ __forceinline__ bool cc_marked(const uint32_t* marked, uint32_t u) {
+  return (__ldg(marked + (u >> 5)) >> (u & 31)) & 1u;
+}
+
+// Final pass over the unmarked vertices: each links its smaller neighbours and
+// its marked larger ones.  Threads, warps or CTA chunks by degree, as in the
+// other kernels.
+// With nothing marked only the ascending prefix of smaller neighbours is
+// read (early exit at the first larger one).
 template <typename G>
 __global__ void __launch_bounds__(kCcThreads) cc_final_kernel(G g, VBins bins, CtaChunks hubs, uint32_t* p,
-                                                              const uint32_t* giant_p) {
+                                                              const uint32_t* __restrict__ marked,
+                                                              const uint32_t* __restrict__ giant_p) {
   VRange r = vbins_range(bins);
   const uint32_t lane = lane_id();
-  const uint32_t giant = __ldg(giant_p);
+  const bool any = __ldg(giant_p + 1) != 0;
   if (r.role == kRoleThread) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
-      if (cc_find(p, v) == giant) continue;
+      if (cc_marked(marked, v)) continue;
       Seg s = g.seg(v);
-      for (uint32_t k = 0; k < s.len; ++k) cc_union(p, __ldg(s.p + k), v);
+      for (uint32_t k = 0; k < s.len; ++k) {
+        const uint32_t u = __ldg(s.p + k);
+        if (u < v) cc_union(p, u, v);
+        else if (!any) break;
+        else if (cc_marked(marked, u)) cc_union(p, u, v);
+      }
     }
   } else if (r.role == kRoleWarp) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
-      if (__shfl_sync(0xFFFFFFFFu, lane == 0 ? cc_find(p, v) : 0u, 0) == giant) continue;
+      if (cc_marked(marked, v)) continue;
       Seg s = g.seg(v);
-      for (uint32_t k = lane; k < s.len; k += 32) cc_union(p, __ldg(s.p + k), v);
+      for (uint32_t base = 0; base < s.len; base += 32) {
+        const uint32_t k = base + lane;
+        const uint32_t u = k < s.len ? __ldg(s.p + k) : kInf;
+        if (u < v || (any && k < s.len && cc_marked(marked, u))) cc_union(p, u, v);
+        if (!any && __ballot_sync(0xFFFFFFFFu, u >= v) != 0) break;
+      }
     }
   } else {
-    __shared__ uint32_t root_s;
     for (uint64_t j = blockIdx.x - bins.nbT - bins.nbW; j < hubs.items; j += bins.nbC) {
       ChunkItem it = chunk_item(hubs, j);
       uint32_t v = __ldg(bins.vorder + it.vidx);
-      if (threadIdx.x == 0) root_s = cc_find(p, v);
-      __syncthreads();
-      const bool skip = root_s == giant;
-      __syncthreads();
-      if (skip) continue;
+      if (cc_marked(marked, v)) continue;  // uniform over the block
       Seg s = g.seg(v);
       uint32_t lo, hi;
       chunk_range(s.len, it.chunk, it.K, &lo, &hi);
-      for (uint32_t k = lo + threadIdx.x; k < hi; k += blockDim.x) cc_union(p, __ldg(s.p + k), v);
+      for (uint32_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const uint32_t u = __ldg(s.p + k);
+        if (u < v || (any && cc_marked(marked, u))) cc_union(p, u, v);
+      }
     }
   }
 }
@@ -173,8 +222,12 @@ __global__ void cc_compress_kernel(uint32_t* p, uint32_t n) {
 template <typename G>
 byo_status run_cc(const byo_graph* g, G view, uint32_t* labels, cudaStream_t s) {
   unsigned grid = (unsigned)((uint64_t)sm_count() * 8);
-  uint32_t* giant = nullptr;
-  BYO_RETURN_IF(tmp_alloc_t(&giant, 1, s, "CC large-component root"));
+  uint32_t *giant = nullptr, *marked = nullptr;
+  BYO_RETURN_IF(tmp_alloc_t(&giant, 2, s, "CC large-component root"));
+  if (tmp_alloc_t(&marked, (g->n + 31) / 32, s, "CC large-component marks") != BYO_OK) {
+    tmp_free(giant, s);
+    return BYO_ERR_OUT_OF_MEMORY;
+  }
   VBins bins = make_vbins(g, 5, 11, kCcThreads);
   CtaChunks hubs = make_cta_chunks(g, 12, 12);  // degrees >= 2048, chunks of <= 4096 ids
   {
@@ -189,19 +242,21 @@ byo_status run_cc(const byo_graph* g, G view, uint32_t* labels, cudaStream_t s) 
     cc_sample_kernel<<<grid, kCcThreads, 0, s>>>(view, labels, 1u);
     cc_flatten_kernel<<<grid, kCcThreads, 0, s>>>(labels, g->n);
     cc_giant_kernel<<<1, kGiantSample, 0, s>>>(labels, g->n, giant);
-    ::byo::note_launch(5);
+    cc_mark_kernel<<<grid, kCcThreads, 0, s>>>(labels, g->n, giant, marked);
+    ::byo::note_launch(6);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_status(e, "cc sampling");
   }
   if (st == BYO_OK) {
     ProfScope ps("cc_final", s);
-    cc_final_kernel<<<vbins_grid(bins), kCcThreads, 0, s>>>(view, bins, hubs, labels, giant);
+    cc_final_kernel<<<vbins_grid(bins), kCcThreads, 0, s>>>(view, bins, hubs, labels, marked, giant);
     cc_compress_kernel<<<grid, kCcThreads, 0, s>>>(labels, g->n);
     ::byo::note_launch(2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_status(e, "cc final pass");
   }
   tmp_free(giant, s);
+  tmp_free(marked, s);
   return st;
 }
 
