@@ -305,19 +305,23 @@ __device__ __forceinline__ uint32_t chunks(uint32_t len) { return (len + kPartne
 
 // Intersection work of the DAG: the out-list lengths every method must read
 // (sum over edges a->b of d+(a) + d+(b) = sum_c d+(c)^2 + d-(c) d+(c)) and the
-// ids this implementation walks (sum over edges of min(d+(a), d+(b))).
+// ids this implementation walks: per edge a->b the shorter out-list, d+(b) at
+// centre a when d+(b) <= d+(a), else d+(a) at centre b, nothing when the
+// walked side is the single-entry list of a (see the task rules).  One thread
+// per vertex over its out-list (out-lists are short in this order).
 __global__ void tc_work_kernel(const uint64_t* __restrict__ dag_off, const uint64_t* __restrict__ in_off,
-                               const uint32_t* __restrict__ in_col, uint32_t n, unsigned long long* work) {
+                               const uint32_t* __restrict__ dag_col, uint32_t n, unsigned long long* work) {
   unsigned long long sq = 0, io = 0, mn = 0;
-  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
-    const unsigned long long dp = dag_off[c + 1] - dag_off[c];
-    const uint64_t b = in_off[c], e = in_off[c + 1];
-    sq += dp * dp;
-    io += (e - b) * dp;
-    for (uint64_t i = b; i < e; ++i) {  // in-neighbour a of c: edge a->c
-      const uint32_t a = in_col[i];
-      const unsigned long long da = dag_off[a + 1] - dag_off[a];
-      mn += da < dp ? (da >= 2 ? da : 0) : dp;  // a kind-1 out-list of length 1 is not walked
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b0 = dag_off[a], b1 = dag_off[a + 1];
+    const unsigned long long da = b1 - b0;
+    sq += da * da;
+    io += (in_off[a + 1] - in_off[a]) * da;
+    if (da < 2) continue;
+    for (uint64_t i = b0; i < b1; ++i) {
+      const uint32_t b = dag_col[i];
+      const unsigned long long db = dag_off[b + 1] - dag_off[b];
+      mn += db <= da ? db : da;
     }
   }
 #pragma unroll
@@ -819,7 +823,7 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
   BYO_CHECK_LAUNCH("tc_fill_kernel");
   if (want_work) {
     cudaMemsetAsync(w->work, 0, 4 * sizeof(unsigned long long), s);
-    tc_work_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, w->in_col, n, w->work);
+    tc_work_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, w->dag_col, n, w->work);
     ::byo::note_launch();
     BYO_CUDA(cudaMemcpyAsync(w->host_work, w->work, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   }
