@@ -129,7 +129,7 @@ byo_status scan_impl(const In* in, uint64_t* out, uint64_t n, uint64_t* host_tot
 // ---------------------------------------------------------------- radix sort
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 16;  // keys per lane
+constexpr int kSortRounds = 8;  // keys per lane
 constexpr int kWarpKeys = 32 * kSortRounds;
 constexpr uint64_t kSortTile = (uint64_t)kSortWarps * kWarpKeys;
 constexpr int kRadix = 256;
@@ -149,17 +149,28 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(uint64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint64_t* __restrict__ keys,
+// One tile of kSortTile keys per CTA.  Each key's rank among the tile's keys
+// of its digit comes from warp matches and per-warp digit counters; the tile
+// is then reordered by digit in shared memory (stable: warps, then rounds,
+// then lanes in order) and written out run by run, so that consecutive
+// threads store consecutive addresses of a digit's output range.
+constexpr size_t kScatterSmem = (size_t)kSortTile * sizeof(uint64_t);
+
+__global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(const uint64_t* __restrict__ keys,
                                                                      uint64_t* __restrict__ out, uint64_t n,
                                                                      int shift, uint32_t mask,
                                                                      const uint64_t* __restrict__ offs,
                                                                      uint64_t ntiles) {
+  extern __shared__ __align__(16) uint64_t sk[];  // the tile, reordered by digit
   __shared__ uint32_t cnt[kSortWarps][kRadix];
+  __shared__ uint32_t start[kRadix];              // tile-local start of each digit
+  __shared__ uint64_t gbase[kRadix];              // global start of each digit's run of this tile
   const int w = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
   for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  const uint64_t base = (uint64_t)blockIdx.x * kSortTile + (uint64_t)w * kWarpKeys;
+  const uint64_t tile0 = (uint64_t)blockIdx.x * kSortTile;
+  const uint64_t base = tile0 + (uint64_t)w * kWarpKeys;
   uint64_t k[kSortRounds];
   uint32_t rank[kSortRounds];
 #pragma unroll
@@ -177,6 +188,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint6
     __syncwarp();
   }
   __syncthreads();
+  // per digit: exclusive offsets over the warps, and the digit's tile total
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
     uint32_t run = 0;
 #pragma unroll
@@ -185,6 +197,29 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint6
       cnt[ww][d] = run;
       run += t;
     }
+    start[d] = run;  // total for now
+    gbase[d] = offs[(uint64_t)d * ntiles + blockIdx.x];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the digit totals (256 = 8 per lane)
+    uint32_t v[kRadix / 32], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kRadix / 32; ++j) {
+      v[j] = start[lane * (kRadix / 32) + j];
+      sum += v[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int j = 0; j < kRadix / 32; ++j) {
+      start[lane * (kRadix / 32) + j] = run;
+      run += v[j];
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -192,9 +227,15 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint6
     uint64_t idx = base + (uint64_t)r * 32 + lane;
     if (idx < n) {
       uint32_t d = (uint32_t)(k[r] >> shift) & mask;
-      uint64_t pos = offs[(uint64_t)d * ntiles + blockIdx.x] + cnt[w][d] + rank[r];
-      out[pos] = k[r];
+      sk[start[d] + cnt[w][d] + rank[r]] = k[r];
     }
+  }
+  __syncthreads();
+  const uint32_t count = (uint32_t)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
+  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const uint64_t key = sk[i];
+    const uint32_t d = (uint32_t)(key >> shift) & mask;
+    out[gbase[d] + (i - start[d])] = key;
   }
 }
 
@@ -220,9 +261,14 @@ byo_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint64_t n, int bits, u
     tmp_free(hist, s);
     return st;
   }
+  {
+    cudaError_t e = cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kScatterSmem);
+    if (e != cudaSuccess) st = cuda_status(e, "radix_scatter_kernel shared memory");
+  }
   uint64_t* a = keys;
   uint64_t* b = tmp;
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = 0; shift < bits && st == BYO_OK; shift += 8) {
     int w = bits - shift < 8 ? bits - shift : 8;
     uint32_t mask = (1u << w) - 1u;
     radix_hist_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(a, n, shift, mask, hist, ntiles); ::byo::note_launch();
@@ -233,7 +279,8 @@ byo_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint64_t n, int bits, u
     }
     st = scan_u32_to_u64(hist, offs, (uint64_t)kRadix * ntiles, nullptr, s);
     if (st != BYO_OK) break;
-    radix_scatter_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(a, b, n, shift, mask, offs, ntiles); ::byo::note_launch();
+    radix_scatter_kernel<<<(unsigned)ntiles, kSortThreads, kScatterSmem, s>>>(a, b, n, shift, mask, offs, ntiles);
+    ::byo::note_launch();
     le = cudaGetLastError();
     if (le != cudaSuccess) {
       st = cuda_status(le, "radix_scatter_kernel");

@@ -274,6 +274,28 @@ def test_triangle_count_cta_path_and_windows(byo, monkeypatch, light_max, window
         g.close()
 
 
+def test_triangle_work_statistics(byo):
+    # the byte model of the benchmark's roofline rests on these three sums;
+    # recompute them from the oracle's CSR with the (degree, id) orientation
+    n, src, dst = graphgen.rmat_small(12, 16, 46)
+    ref = oracle.csr_build(n, src, dst)
+    off = np.asarray(ref.off, dtype=np.int64)
+    col = np.asarray(ref.col, dtype=np.int64)
+    deg = np.diff(off)
+    row = np.repeat(np.arange(n), deg)
+    up = (deg[col] > deg[row]) | ((deg[col] == deg[row]) & (col > row))  # row -> col in the DAG
+    a, b = row[up], col[up]
+    dp = np.bincount(a, minlength=n)
+    dm = np.bincount(b, minlength=n)
+    da, db = dp[a], dp[b]
+    walked = np.where(da < 2, 0, np.minimum(da, db))
+    g = byo.Graph(n, dev_u32(src), dev_u32(dst))
+    try:
+        assert byo.byo_tc_work(g.handle) == (int((dp * dp).sum()), int((dm * dp).sum()), int(walked.sum()))
+    finally:
+        g.close()
+
+
 # ----------------------------------------------------------------------------- schedule network
 
 def _mlp_batch(B=333, seed=0):
