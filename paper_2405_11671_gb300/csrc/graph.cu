@@ -8,6 +8,8 @@
 
 #include <mutex>
 
+#include <atomic>
+
 #include "byo_internal.cuh"
 #include "prof.cuh"
 #include "container.cuh"
@@ -46,8 +48,32 @@ void dev_free(void* p) {
   if (p) cudaFree(p);
 }
 
+// Scratch comes from the device's stream-ordered memory pool.  The pool keeps
+// up to a quarter of the device memory mapped between calls (the default
+// releases everything at each synchronisation), so that the multi-GB scratch
+// of a large graph is not mapped again by every call.  Set once per device;
+// it lasts as long as the process.
+static void keep_pool_warm() {
+  static std::atomic<uint64_t> done_mask{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  if (done_mask.load() & (1ull << dev)) return;
+  done_mask.fetch_or(1ull << dev);
+  cudaMemPool_t pool;
+  size_t free_b = 0, total_b = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+    uint64_t keep = (uint64_t)total_b / 4;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+}
+
 byo_status tmp_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
   *p = nullptr;
+  keep_pool_warm();
   cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
