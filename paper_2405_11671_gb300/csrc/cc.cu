@@ -15,7 +15,7 @@
 // vertices needs no link (same component), an edge with one marked end is
 // linked from the other end, and an edge between two unmarked vertices is
 // linked from its larger end: every edge is covered.  When no component holds
-// half of the sample (a batch of many similar graphs) nothing is marked and
+// an eighth of the sample (a batch of many similar graphs) nothing is marked and
 // the final pass links every edge from its larger end alone, reading only
 // each list's ascending prefix of smaller neighbours.
 #include "byo_internal.cuh"
@@ -110,14 +110,14 @@ __global__ void __launch_bounds__(kGiantSample) cc_giant_kernel(const uint32_t* 
   __syncthreads();
   if (t == 0) {
     giant[0] = (uint32_t)(best & 0xFFFFFFFFull);
-    giant[1] = (uint32_t)(best >> 32) * 2 >= kGiantSample;  // a component of at least half the sample
+    giant[1] = (uint32_t)(best >> 32) * 8 >= kGiantSample;  // a component of at least 1/8 of the sample
   }
 }
 
 // The vertices whose root is the large component's, one bit each (a snapshot
 // taken between the sampling and the final pass).  No vertex is marked when
-// no component holds half of the sample (many similar components, as in a
-// batch of graphs): the final pass then takes every edge from its larger end.
+// no component holds an eighth of the sample (many similar components, as in
+// a batch of graphs): the final pass then takes every edge from its larger end.
 __global__ void cc_mark_kernel(const uint32_t* p, uint32_t n, const uint32_t* giant_p, uint32_t* marked) {
   const uint32_t giant = __ldg(giant_p), any = __ldg(giant_p + 1);
   const uint32_t nw = (n + 31) / 32;
