@@ -121,14 +121,17 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
   const float* b2 = W2 + kHidden * kHidden;
   const float* W3 = b2 + kHidden;
   const float* b3 = W3 + kActions * kHidden;
-  float h1 = b1[lane];
+  // four independent partial sums per layer keep the FMA chains short (this
+  // runs on the critical path of every BFS level)
+  float a1[4] = {b1[lane], 0.0f, 0.0f, 0.0f};
 #pragma unroll
-  for (int i = 0; i < kFeatures; ++i) h1 = fmaf(W1[i * kHidden + lane], x[i], h1);  // staged transposed
-  h1 = fmaxf(h1, 0.0f);
-  float h2 = b2[lane];
+  for (int i = 0; i < kFeatures; ++i) a1[i & 3] = fmaf(W1[i * kHidden + lane], x[i], a1[i & 3]);  // staged transposed
+  const float h1 = fmaxf((a1[0] + a1[1]) + (a1[2] + a1[3]), 0.0f);
+  float a2[4] = {b2[lane], 0.0f, 0.0f, 0.0f};
 #pragma unroll
-  for (int k = 0; k < kHidden; ++k) h2 = fmaf(W2[k * kHidden + lane], __shfl_sync(0xFFFFFFFFu, h1, k), h2);
-  h2 = fmaxf(h2, 0.0f);
+  for (int k = 0; k < kHidden; ++k)
+    a2[k & 3] = fmaf(W2[k * kHidden + lane], __shfl_sync(0xFFFFFFFFu, h1, k), a2[k & 3]);
+  const float h2 = fmaxf((a2[0] + a2[1]) + (a2[2] + a2[3]), 0.0f);
   const bool solo_ok = f.mf <= kSoloMaxEdges && f.nf <= kSoloMaxVertices;
   const bool pull_ok = sched_pull_allowed(sp, f);
   int best = -1;  // action 1 is always allowed
