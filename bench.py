@@ -201,8 +201,10 @@ def algo_bytes(kernel: str, n: int, m: int, off: int, trace=None) -> float | Non
         # identity labels, two sampling rounds (offsets, one neighbour id and the
         # two endpoints' labels each), one flattening pass (read + write)
         return 4.0 * n + 2 * (off * (n + 1) + 4.0 * n + 8.0 * n) + 8.0 * n
-    if kernel == "tc_outdeg" or kernel == "tc_fill":
-        return off * (n + 1) + 4.0 * n + 4.0 * m + 2 * off * m + (4.0 * m / 2 if kernel == "tc_fill" else 4.0 * n)
+    if kernel == "tc_fill":
+        # offsets and ids of the graph, the rank of every vertex and of every
+        # neighbour, the DAG rows written (4 B per entry), row starts and records
+        return off * (n + 1) + 4.0 * n + 4.0 * m + 4.0 * m + 4.0 * m + 8.0 * (n + 1) + 16.0 * n
     return None
 
 

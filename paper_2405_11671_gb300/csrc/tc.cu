@@ -45,16 +45,22 @@ static uint32_t env_cap(const char* name, uint32_t cap) {
   return v < (long long)cap ? (uint32_t)v : cap;
 }
 
+// A DAG row in rank space: N+(r) = dag[off, off + dplus), N-(r) = dag[off +
+// dplus, off + len); one 16-byte load gives a partner's walked list.
+struct __align__(16) RowInfo {
+  uint64_t off;
+  uint32_t dplus, len;
+};
+
 struct TcWork {
   uint32_t n = 0;
-  uint64_t half_cap = 0;        // capacity of dag_col / in_col (undirected edges)
-  uint64_t* dag_off = nullptr;  // n + 1: N+ offsets
-  uint32_t* dag_col = nullptr;  // half_cap + 8
-  uint64_t* in_off = nullptr;   // n + 1: N- offsets
-  uint32_t* in_col = nullptr;   // half_cap + 8
-  uint32_t* outdeg = nullptr;   // n (rank-indexed)
+  uint64_t cap = 0;             // capacity of dag (stored entries)
+  RowInfo* row = nullptr;       // n + 1, rank-indexed: where each DAG row starts, |N+|, |row|
+  uint64_t* roff = nullptr;     // n + 1: row starts (scan of the degrees in rank order)
+  uint32_t* dag = nullptr;      // cap + 8: row r = N+(r) then N-(r), rank ids
+  uint32_t* rdeg = nullptr;     // n: degree of rank r
   uint32_t* rank = nullptr;     // n: vertex id -> position in (degree, id) order
-  uint32_t* cnt_l = nullptr;    // n: in-degrees, then light task counts
+  uint32_t* cnt_l = nullptr;    // n: light task counts
   uint32_t* cnt_h = nullptr;    // n: heavy task counts
   uint64_t* pos_l = nullptr;    // n + 1
   uint64_t* pos_h = nullptr;    // n + 1
@@ -66,11 +72,10 @@ struct TcWork {
 
 void tc_free(TcWork* w) {
   if (!w) return;
-  dev_free(w->dag_off);
-  dev_free(w->dag_col);
-  dev_free(w->in_off);
-  dev_free(w->in_col);
-  dev_free(w->outdeg);
+  dev_free(w->row);
+  dev_free(w->roff);
+  dev_free(w->dag);
+  dev_free(w->rdeg);
   dev_free(w->rank);
   dev_free(w->cnt_l);
   dev_free(w->cnt_h);
@@ -128,79 +133,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_
 }
 
 // ---------------------------------------------------------------- filter
-// Out-degree d+(v) = |{u in N(v): rank(u) > rank(v)}| and in-degree d-(v) =
-// deg(v) - d+(v), both stored at rank(v).
-template <typename G>
-__global__ void __launch_bounds__(kTcThreads) tc_outdeg_kernel(G g, VBins bins, const uint32_t* __restrict__ rank,
-                                                               uint32_t* outdeg, uint32_t* indeg) {
-  VRange r = vbins_range(bins);
-  const uint32_t lane = lane_id();
-  if (r.role == kRoleThread) {
-    for (uint64_t i = r.begin; i < r.end; i += r.stride) {
-      uint32_t v = __ldg(bins.vorder + i);
-      Seg s = g.seg(v);
-      const uint32_t rv = __ldg(rank + v);
-      uint32_t c = 0;
-      for (uint32_t k = 0; k < s.len; k += 8) {  // eight ids and their ranks in flight
-        uint32_t u[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) u[j] = k + j < s.len ? __ldg(s.p + k + j) : 0u;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) c += k + j < s.len && __ldg(rank + u[j]) > rv;
-      }
-      outdeg[rv] = c;
-      indeg[rv] = s.len - c;
-    }
-  } else if (r.role == kRoleWarp) {
-    for (uint64_t i = r.begin; i < r.end; i += r.stride) {
-      uint32_t v = __ldg(bins.vorder + i);
-      Seg s = g.seg(v);
-      const uint32_t rv = __ldg(rank + v);
-      uint32_t c = 0;
-      for (uint32_t k = lane; k < s.len; k += 128) {  // four chunks in flight
-        uint32_t u[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) u[j] = k + 32 * j < s.len ? __ldg(s.p + k + 32 * j) : 0u;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) c += k + 32 * j < s.len && __ldg(rank + u[j]) > rv;
-      }
-      c = __reduce_add_sync(0xFFFFFFFFu, c);
-      if (lane == 0) {
-        outdeg[rv] = c;
-        indeg[rv] = s.len - c;
-      }
-    }
-  } else {
-    __shared__ uint32_t part[kTcThreads / 32];
-    for (uint64_t i = r.begin; i < r.end; i += r.stride) {
-      uint32_t v = __ldg(bins.vorder + i);
-      Seg s = g.seg(v);
-      const uint32_t rv = __ldg(rank + v);
-      uint32_t c = 0;
-      for (uint32_t k = threadIdx.x; k < s.len; k += blockDim.x) c += __ldg(rank + __ldg(s.p + k)) > rv;
-      c = __reduce_add_sync(0xFFFFFFFFu, c);
-      if (lane == 0) part[threadIdx.x >> 5] = c;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) t += part[w];
-        outdeg[rv] = t;
-        indeg[rv] = s.len - t;
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// N+(rank v) (ranks of the higher-rank neighbours) into dag_col and N-(rank v)
-// (ranks of the lower-rank ones) into in_col, both in v's stored neighbour
-// order: one pass over the list.
+// One pass over every neighbour list: the ranks of v's higher-rank neighbours
+// (N+) go to the front of row rank(v) of the DAG, those of the lower-rank ones
+// (N-) to its back, both in v's stored neighbour order; the row's RowInfo
+// records |N+|.  Rows are laid out in rank order (row starts = a scan of the
+// degrees in rank order), so no counting pass is needed.
 template <typename G>
 __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, const uint32_t* __restrict__ rank,
-                                                             const uint64_t* __restrict__ dag_off,
-                                                             uint32_t* __restrict__ dag_col,
-                                                             const uint64_t* __restrict__ in_off,
-                                                             uint32_t* __restrict__ in_col) {
+                                                             const uint64_t* __restrict__ roff,
+                                                             uint32_t* __restrict__ dag, RowInfo* __restrict__ row) {
   VRange r = vbins_range(bins);
   const uint32_t lane = lane_id();
   if (r.role == kRoleThread) {
@@ -208,7 +149,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
       const uint32_t rv = __ldg(rank + v);
-      uint64_t o = dag_off[rv], q = in_off[rv];
+      const uint64_t b = roff[rv];
+      uint64_t o = b, q = b + s.len;
       for (uint32_t k = 0; k < s.len; k += 8) {  // eight ids and their ranks in flight before the stores
         uint32_t u[8], ru[8];
 #pragma unroll
@@ -218,17 +160,19 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           if (k + j >= s.len) break;
-          if (ru[j] > rv) dag_col[o++] = ru[j];
-          else in_col[q++] = ru[j];
+          if (ru[j] > rv) dag[o++] = ru[j];
+          else dag[--q] = ru[j];
         }
       }
+      row[rv] = RowInfo{b, (uint32_t)(o - b), s.len};
     }
   } else if (r.role == kRoleWarp) {
     for (uint64_t i = r.begin; i < r.end; i += r.stride) {
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
       const uint32_t rv = __ldg(rank + v);
-      uint64_t o = dag_off[rv], q = in_off[rv];
+      const uint64_t b = roff[rv];
+      uint64_t o = b, q = b + s.len;
       for (uint32_t base = 0; base < s.len; base += 128) {  // four chunks' ranks in flight before the stores
         uint32_t ru[4];
 #pragma unroll
@@ -244,12 +188,13 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
           bool keep = k < s.len && ru[j] > rv;
           bool back = k < s.len && !keep;
           uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep), bbk = __ballot_sync(0xFFFFFFFFu, back);
-          if (keep) dag_col[o + __popc(bal & lanemask_lt())] = ru[j];
-          if (back) in_col[q + __popc(bbk & lanemask_lt())] = ru[j];
+          if (keep) dag[o + __popc(bal & lanemask_lt())] = ru[j];
+          if (back) dag[q - 1 - __popc(bbk & lanemask_lt())] = ru[j];
           o += __popc(bal);
-          q += __popc(bbk);
+          q -= __popc(bbk);
         }
       }
+      if (lane == 0) row[rv] = RowInfo{b, (uint32_t)(o - b), s.len};
     }
   } else {
     __shared__ uint32_t wcnt[2][kTcThreads / 32];
@@ -259,7 +204,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
       uint32_t v = __ldg(bins.vorder + i);
       Seg s = g.seg(v);
       const uint32_t rv = __ldg(rank + v);
-      uint64_t o = dag_off[rv], q = in_off[rv];
+      const uint64_t b = roff[rv];
+      uint64_t o = b, q = b + s.len;
       for (uint32_t base = 0; base < s.len; base += blockDim.x) {
         uint32_t k = base + threadIdx.x;
         uint32_t ru = k < s.len ? __ldg(rank + __ldg(s.p + k)) : 0;
@@ -276,17 +222,24 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
           for (uint32_t j = 0; j < nw; ++j) wpre[threadIdx.x][j + 1] = wpre[threadIdx.x][j] + wcnt[threadIdx.x][j];
         }
         __syncthreads();
-        if (keep) dag_col[o + wpre[0][w] + __popc(bal & lanemask_lt())] = ru;
-        if (back) in_col[q + wpre[1][w] + __popc(bbk & lanemask_lt())] = ru;
+        if (keep) dag[o + wpre[0][w] + __popc(bal & lanemask_lt())] = ru;
+        if (back) dag[q - 1 - wpre[1][w] - __popc(bbk & lanemask_lt())] = ru;
         o += wpre[0][nw];
-        q += wpre[1][nw];
+        q -= wpre[1][nw];
         __syncthreads();
       }
+      if (threadIdx.x == 0) row[rv] = RowInfo{b, (uint32_t)(o - b), s.len};
     }
   }
 }
 
-__global__ void tc_set_last_kernel(uint64_t* dag_off, uint32_t n, uint64_t total) { dag_off[n] = total; }
+// degree of rank r, from the sorted (degree << lbn | v) keys
+__global__ void tc_rdeg_kernel(const uint64_t* __restrict__ sorted, uint32_t n, int lbn, uint32_t* __restrict__ rdeg) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x)
+    rdeg[r] = (uint32_t)(sorted[r] >> lbn);
+}
+
+__global__ void tc_set_last_kernel(uint64_t* off, uint32_t n, uint64_t total) { off[n] = total; }
 
 // Work items.  Every DAG edge a->b is intersected from the side with the
 // shorter out-list: at centre a (walk N+(b), probe N+(a)) when d+(b) <= d+(a),
@@ -309,18 +262,17 @@ __device__ __forceinline__ uint32_t chunks(uint32_t len) { return (len + kPartne
 // centre a when d+(b) <= d+(a), else d+(a) at centre b, nothing when the
 // walked side is the single-entry list of a (see the task rules).  One thread
 // per vertex over its out-list (out-lists are short in this order).
-__global__ void tc_work_kernel(const uint64_t* __restrict__ dag_off, const uint64_t* __restrict__ in_off,
-                               const uint32_t* __restrict__ dag_col, uint32_t n, unsigned long long* work) {
+__global__ void tc_work_kernel(const RowInfo* __restrict__ row, const uint32_t* __restrict__ dag, uint32_t n,
+                               unsigned long long* work) {
   unsigned long long sq = 0, io = 0, mn = 0;
   for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t b0 = dag_off[a], b1 = dag_off[a + 1];
-    const unsigned long long da = b1 - b0;
+    const RowInfo ra = row[a];
+    const unsigned long long da = ra.dplus;
     sq += da * da;
-    io += (in_off[a + 1] - in_off[a]) * da;
+    io += (unsigned long long)(ra.len - ra.dplus) * da;
     if (da < 2) continue;
-    for (uint64_t i = b0; i < b1; ++i) {
-      const uint32_t b = dag_col[i];
-      const unsigned long long db = dag_off[b + 1] - dag_off[b];
+    for (uint64_t i = ra.off; i < ra.off + da; ++i) {
+      const unsigned long long db = row[dag[i]].dplus;
       mn += db <= da ? db : da;
     }
   }
@@ -337,11 +289,11 @@ __global__ void tc_work_kernel(const uint64_t* __restrict__ dag_off, const uint6
   }
 }
 
-__global__ void tc_task_count_kernel(const uint64_t* __restrict__ dag_off, const uint64_t* __restrict__ in_off,
-                                     uint32_t n, uint32_t light_max, uint32_t* cnt_light, uint32_t* cnt_heavy) {
+__global__ void tc_task_count_kernel(const RowInfo* __restrict__ row, uint32_t n, uint32_t light_max,
+                                     uint32_t* cnt_light, uint32_t* cnt_heavy) {
   for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t dp = (uint32_t)(dag_off[c + 1] - dag_off[c]);
-    uint32_t dm = (uint32_t)(in_off[c + 1] - in_off[c]);
+    const RowInfo rc = row[c];
+    const uint32_t dp = rc.dplus, dm = rc.len - rc.dplus;
     // kind 0 needs two out-neighbours; kind 1 a partner with 2 <= d+(p) < d+(c)
     uint32_t t = (dp >= 2 ? chunks(dp) : 0) + (dp >= 3 ? chunks(dm) : 0);
     cnt_light[c] = dp <= light_max ? t : 0;
@@ -349,12 +301,12 @@ __global__ void tc_task_count_kernel(const uint64_t* __restrict__ dag_off, const
   }
 }
 
-__global__ void tc_task_fill_kernel(const uint64_t* __restrict__ dag_off, const uint64_t* __restrict__ in_off,
-                                    uint32_t n, uint32_t light_max, const uint64_t* __restrict__ pos_light,
-                                    const uint64_t* __restrict__ pos_heavy, TcTask* light, TcTask* heavy) {
+__global__ void tc_task_fill_kernel(const RowInfo* __restrict__ row, uint32_t n, uint32_t light_max,
+                                    const uint64_t* __restrict__ pos_light, const uint64_t* __restrict__ pos_heavy,
+                                    TcTask* light, TcTask* heavy) {
   for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t dp = (uint32_t)(dag_off[c + 1] - dag_off[c]);
-    uint32_t dm = (uint32_t)(in_off[c + 1] - in_off[c]);
+    const RowInfo rc = row[c];
+    const uint32_t dp = rc.dplus, dm = rc.len - rc.dplus;
     if (dp > light_max) {
       heavy[pos_heavy[c]] = TcTask{(uint32_t)c, 2u, 0u, dp};
       continue;
@@ -464,15 +416,15 @@ __device__ __forceinline__ uint32_t warp_count_group(const uint32_t* __restrict_
 // shorter list (kind 0: d+(p) <= d+(c); kind 1: d+(p) < d+(c)).  A kind-1
 // partner's out-list holds c itself, which N+(c) does not, so one of length 1
 // cannot meet N+(c) and is skipped.
-__device__ __forceinline__ void partner_list(const uint64_t* __restrict__ dag_off, bool has, uint32_t p, uint32_t kind,
+__device__ __forceinline__ void partner_list(const RowInfo* __restrict__ row, bool has, uint32_t p, uint32_t kind,
                                              uint32_t dc, uint64_t* vb, uint32_t* len) {
   *vb = 0;
   *len = 0;
   if (!has) return;
-  uint64_t b = dag_off[p];
-  uint32_t d = (uint32_t)(dag_off[p + 1] - b);
+  const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + p));  // off (2 words), dplus, len
+  const uint32_t d = q.z;
   if (kind == 0 ? d <= dc : (d < dc && d >= 2)) {
-    *vb = b;
+    *vb = ((uint64_t)q.y << 32) | q.x;
     *len = d;
   }
 }
@@ -482,7 +434,7 @@ __device__ __forceinline__ void partner_list(const uint64_t* __restrict__ dag_of
 // partner ids and out-list bounds of the next two groups are loaded while the
 // current group is walked.
 template <typename Set>
-__device__ __forceinline__ uint64_t walk_partners(const uint64_t* __restrict__ dag_off,
+__device__ __forceinline__ uint64_t walk_partners(const RowInfo* __restrict__ row,
                                                   const uint32_t* __restrict__ dag_col, const uint32_t* partners,
                                                   const TcTask& t, uint32_t dc, uint32_t w, uint32_t warps,
                                                   const Set& set) {
@@ -493,13 +445,13 @@ __device__ __forceinline__ uint64_t walk_partners(const uint64_t* __restrict__ d
   uint32_t p = has ? __ldg(partners + k0 + lane) : 0;
   uint64_t vb;
   uint32_t len;
-  partner_list(dag_off, has, p, t.kind, dc, &vb, &len);
+  partner_list(row, has, p, t.kind, dc, &vb, &len);
   bool has1 = k0 + step + lane < t.hi;
   uint32_t p1 = has1 ? __ldg(partners + k0 + step + lane) : 0;
   for (; k0 < t.hi; k0 += step) {
     uint64_t vb1;
     uint32_t len1;
-    partner_list(dag_off, has1, p1, t.kind, dc, &vb1, &len1);  // group k0 + step
+    partner_list(row, has1, p1, t.kind, dc, &vb1, &len1);  // group k0 + step
     const bool has2 = k0 + 2 * step + lane < t.hi;
     const uint32_t p2 = has2 ? __ldg(partners + k0 + 2 * step + lane) : 0;
     hits += warp_count_group(dag_col, vb, len, set);
@@ -515,10 +467,8 @@ constexpr uint32_t kSlice = kLightMax + 8;  // staged N+(u) (+ alignment slack),
 constexpr uint32_t kTable = 4 * kLightMax;   // hash slots per warp (load factor <= 1/4)
 constexpr size_t kLightSmem = (size_t)(kTcThreads / 32) * (kSlice + kTable) * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(kTcThreads, 5) tc_light_kernel(const uint64_t* __restrict__ dag_off,
+__global__ void __launch_bounds__(kTcThreads, 5) tc_light_kernel(const RowInfo* __restrict__ row,
                                                               const uint32_t* __restrict__ dag_col,
-                                                              const uint64_t* __restrict__ in_off,
-                                                              const uint32_t* __restrict__ in_col,
                                                               const TcTask* __restrict__ tasks, uint64_t ntasks,
                                                               uint32_t* ctr, unsigned long long* count,
                                                               uint64_t limit_ns) {
@@ -542,7 +492,8 @@ __global__ void __launch_bounds__(kTcThreads, 5) tc_light_kernel(const uint64_t*
     const TcTask t = tasks[idx];
     const uint32_t c = t.c;
     if (c != have) {
-      uint64_t beg = dag_off[c], end = dag_off[c + 1];
+      const RowInfo rc = row[c];
+      uint64_t beg = rc.off, end = rc.off + rc.dplus;
       uint64_t a0 = beg & ~3ull, a1 = (end + 3) & ~3ull;
       head = (uint32_t)(beg - a0);
       dc = (uint32_t)(end - beg);
@@ -578,8 +529,9 @@ __global__ void __launch_bounds__(kTcThreads, 5) tc_light_kernel(const uint64_t*
       have = c;
     }
     SmemHash set{table, (1u << bits) - 1, 32 - bits, lo, hi};
-    const uint32_t* partners = t.kind == 0 ? dag_col + dag_off[c] : in_col + in_off[c];
-    hits += walk_partners(dag_off, dag_col, partners, t, dc, 0, 1, set);
+    const RowInfo rc = row[c];
+    const uint32_t* partners = dag_col + rc.off + (t.kind == 0 ? 0u : rc.dplus);
+    hits += walk_partners(row, dag_col, partners, t, dc, 0, 1, set);
   }
   uint64_t sum = hits;
 #pragma unroll
@@ -624,7 +576,7 @@ __device__ __forceinline__ uint32_t grab_group(uint32_t* gctr) {
 // they run out.  The partner ids of the group after next and the out-list
 // bounds of the next group are loaded while the current group is walked.
 template <typename Set>
-__device__ __forceinline__ uint32_t walk_groups(const uint64_t* __restrict__ dag_off,
+__device__ __forceinline__ uint32_t walk_groups(const RowInfo* __restrict__ row,
                                                 const uint32_t* __restrict__ dag_col, const CentreGroups& cg,
                                                 uint32_t* gctr, const Set& set) {
   uint32_t g = grab_group(gctr);
@@ -634,7 +586,7 @@ __device__ __forceinline__ uint32_t walk_groups(const uint64_t* __restrict__ dag
   uint32_t p = cg.partner(g, &has, &kind);
   uint64_t vb;
   uint32_t len;
-  partner_list(dag_off, has, p, kind, cg.dc, &vb, &len);
+  partner_list(row, has, p, kind, cg.dc, &vb, &len);
   uint32_t gn = grab_group(gctr);
   bool hasn = false;
   uint32_t kindn = 0, pn = gn < cg.gt ? cg.partner(gn, &hasn, &kindn) : 0u;
@@ -642,7 +594,7 @@ __device__ __forceinline__ uint32_t walk_groups(const uint64_t* __restrict__ dag
   while (true) {
     uint64_t vbn;
     uint32_t lenn;
-    partner_list(dag_off, hasn, pn, kindn, cg.dc, &vbn, &lenn);
+    partner_list(row, hasn, pn, kindn, cg.dc, &vbn, &lenn);
     const uint32_t gnn = gn < cg.gt ? grab_group(gctr) : cg.gt;
     bool hasnn = false;
     uint32_t kindnn = 0, pnn = gnn < cg.gt ? cg.partner(gnn, &hasnn, &kindnn) : 0u;
@@ -662,10 +614,8 @@ __device__ __forceinline__ uint32_t walk_groups(const uint64_t* __restrict__ dag
 // (the n - 1 - c ranks above c fit in `bitmap_bits`): N+(c) is set into a
 // bitmap of that range, read straight from the DAG.  Hash mode: N+(c) is
 // staged by TMA in windows of `window` ids, each hashed.
-__global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const uint64_t* __restrict__ dag_off,
+__global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const RowInfo* __restrict__ row,
                                                               const uint32_t* __restrict__ dag_col,
-                                                              const uint64_t* __restrict__ in_off,
-                                                              const uint32_t* __restrict__ in_col,
                                                               const TcTask* __restrict__ tasks, uint64_t ntasks,
                                                               uint32_t n, uint32_t* ctr, unsigned long long* count,
                                                               uint32_t window, uint32_t bitmap_bits,
@@ -687,10 +637,11 @@ __global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const uint64_t*
     const uint32_t idx = idx_s;
     if (idx >= ntasks) break;
     const uint32_t c = tasks[ntasks - 1 - idx].c;
-    const uint64_t beg = dag_off[c], end = dag_off[c + 1], ib = in_off[c];
-    const uint32_t dc = (uint32_t)(end - beg), dm = (uint32_t)(in_off[c + 1] - ib);
+    const RowInfo rc = row[c];
+    const uint64_t beg = rc.off, end = rc.off + rc.dplus, ib = end;
+    const uint32_t dc = rc.dplus, dm = rc.len - rc.dplus;
     const uint32_t g0 = (dc + 31) / 32;
-    const CentreGroups cg{dag_col + beg, in_col + ib, dc, dm, g0, g0 + (dm + 31) / 32};
+    const CentreGroups cg{dag_col + beg, dag_col + ib, dc, dm, g0, g0 + (dm + 31) / 32};
     const uint32_t above = n - 1 - c;  // N+(c) lies in the ranks (c, n)
     if (above <= bitmap_bits) {
       const uint32_t words = (above + 127) / 128 * 4;
@@ -703,7 +654,7 @@ __global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const uint64_t*
         atomicOr(win + (x >> 5), 1u << (x & 31));
       }
       __syncthreads();
-      hits += walk_groups(dag_off, dag_col, cg, &gctr, SmemBits{win, c + 1, above});
+      hits += walk_groups(row, dag_col, cg, &gctr, SmemBits{win, c + 1, above});
       continue;
     }
     for (uint64_t wb = beg; wb < end; wb += window) {
@@ -746,7 +697,7 @@ __global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const uint64_t*
         atomicMax(&hi_s, mx);
       }
       __syncthreads();
-      hits += walk_groups(dag_off, dag_col, cg, &gctr, SmemHash{table, slots - 1, 32 - bits, lo_s, hi_s});
+      hits += walk_groups(row, dag_col, cg, &gctr, SmemHash{table, slots - 1, 32 - bits, lo_s, hi_s});
     }
   }
   uint64_t sum = hits;
@@ -756,7 +707,7 @@ __global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const uint64_t*
 }
 
 byo_status ensure_tc_work(byo_graph* g) {
-  if (g->tc && g->tc->half_cap >= g->m / 2) return BYO_OK;
+  if (g->tc && g->tc->cap >= g->m) return BYO_OK;
   if (g->tc) {  // the dynamic container grew
     tc_free(g->tc);
     g->tc = nullptr;
@@ -767,12 +718,11 @@ byo_status ensure_tc_work(byo_graph* g) {
     return BYO_ERR_OUT_OF_MEMORY;
   }
   w->n = g->n;
-  w->half_cap = g->m / 2 + (g->dyn ? g->m / 8 : 0);  // headroom for later inserts
-  byo_status st = dev_alloc_t(&w->dag_off, g->n + 1ull, "TC DAG offsets");
-  if (st == BYO_OK) st = dev_alloc_t(&w->dag_col, w->half_cap + 8, "TC DAG neighbours");
-  if (st == BYO_OK) st = dev_alloc_t(&w->in_off, g->n + 1ull, "TC DAG in-offsets");
-  if (st == BYO_OK) st = dev_alloc_t(&w->in_col, w->half_cap + 8, "TC DAG in-neighbours");
-  if (st == BYO_OK) st = dev_alloc_t(&w->outdeg, g->n, "TC out-degrees");
+  w->cap = g->m + (g->dyn ? g->m / 4 : 0);  // headroom for later inserts
+  byo_status st = dev_alloc_t(&w->row, g->n + 1ull, "TC DAG rows");
+  if (st == BYO_OK) st = dev_alloc_t(&w->roff, g->n + 1ull, "TC DAG row starts");
+  if (st == BYO_OK) st = dev_alloc_t(&w->dag, w->cap + 8, "TC DAG");
+  if (st == BYO_OK) st = dev_alloc_t(&w->rdeg, g->n, "TC degrees by rank");
   if (st == BYO_OK) st = dev_alloc_t(&w->rank, g->n, "TC ranks");
   if (st == BYO_OK) st = dev_alloc_t(&w->cnt_l, g->n, "TC task counts");
   if (st == BYO_OK) st = dev_alloc_t(&w->cnt_h, g->n, "TC task counts");
@@ -782,7 +732,7 @@ byo_status ensure_tc_work(byo_graph* g) {
   if (st == BYO_OK) st = dev_alloc_t(&w->count, 1, "TC count");
   if (st == BYO_OK) st = dev_alloc_t(&w->work, 4, "TC work counters");
   if (st == BYO_OK) {
-    cudaError_t e = cudaMemset(w->dag_col, 0, sizeof(uint32_t) * (w->half_cap + 8));
+    cudaError_t e = cudaMemset(w->dag, 0, sizeof(uint32_t) * (w->cap + 8));
     if (e != cudaSuccess) st = cuda_status(e, "cudaMemset");
   }
   if (st != BYO_OK) {
@@ -798,38 +748,35 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
   BYO_RETURN_IF(ensure_tc_work(g));
   TcWork* w = g->tc;
   const uint32_t n = g->n;
-  const uint64_t half = g->m / 2;
   VBins bins = make_vbins(g, 4, 10, kTcThreads);
-  // rank(v) = position of (degree(v), v) in ascending order
-  BYO_RETURN_IF(degree_rank(g, view, w->rank, nullptr, s));
+  // rank(v) = position of (degree(v), v) in ascending order; the DAG rows are
+  // laid out in rank order, row r holding deg(r) entries
   {
-    ProfScope ps("tc_outdeg", s);
-    tc_outdeg_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->rank, w->outdeg, w->cnt_l);
+    uint64_t* sorted = nullptr;
+    BYO_RETURN_IF(degree_rank(g, view, w->rank, &sorted, s));
+    tc_rdeg_kernel<<<grid_for(n, 256), 256, 0, s>>>(sorted, n, id_bits(n), w->rdeg);
+    ::byo::note_launch();
+    tmp_free(sorted, s);
+    BYO_CHECK_LAUNCH("tc_rdeg_kernel");
+    BYO_RETURN_IF(scan_u32_to_u64(w->rdeg, w->roff, n, nullptr, s));
+    tc_set_last_kernel<<<1, 1, 0, s>>>(w->roff, n, g->m);
     ::byo::note_launch();
   }
-  BYO_CHECK_LAUNCH("tc_outdeg_kernel");
-  BYO_RETURN_IF(scan_u32_to_u64(w->outdeg, w->dag_off, n, nullptr, s));
-  tc_set_last_kernel<<<1, 1, 0, s>>>(w->dag_off, n, half);
-  ::byo::note_launch();
-  BYO_RETURN_IF(scan_u32_to_u64(w->cnt_l, w->in_off, n, nullptr, s));
-  tc_set_last_kernel<<<1, 1, 0, s>>>(w->in_off, n, half);
-  ::byo::note_launch();
   {
     ProfScope ps("tc_fill", s);
-    tc_fill_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->rank, w->dag_off, w->dag_col, w->in_off,
-                                                           w->in_col);
+    tc_fill_kernel<<<vbins_grid(bins), kTcThreads, 0, s>>>(view, bins, w->rank, w->roff, w->dag, w->row);
     ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_fill_kernel");
   if (want_work) {
     cudaMemsetAsync(w->work, 0, 4 * sizeof(unsigned long long), s);
-    tc_work_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, w->dag_col, n, w->work);
+    tc_work_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->row, w->dag, n, w->work);
     ::byo::note_launch();
     BYO_CUDA(cudaMemcpyAsync(w->host_work, w->work, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   }
   // tasks
   const uint32_t light_max = env_cap("BYO_TC_LIGHT_MAX", kLightMax);
-  tc_task_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, n, light_max, w->cnt_l, w->cnt_h);
+  tc_task_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->row, n, light_max, w->cnt_l, w->cnt_h);
   ::byo::note_launch();
   BYO_CHECK_LAUNCH("tc_task_count_kernel");
   uint64_t nl = 0, nh = 0;
@@ -839,7 +786,7 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
   byo_status st = tmp_alloc_t(&tl, nl + 1, s, "TC light tasks");
   if (st == BYO_OK) st = tmp_alloc_t(&th, nh + 1, s, "TC heavy tasks");
   if (st == BYO_OK) {
-    tc_task_fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->dag_off, w->in_off, n, light_max, w->pos_l, w->pos_h, tl,
+    tc_task_fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->row, n, light_max, w->pos_l, w->pos_h, tl,
                                                          th);
     ::byo::note_launch();
     cudaMemsetAsync(w->ctr, 0, 8 * sizeof(uint32_t), s);
@@ -856,7 +803,7 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
     if (e == cudaSuccess) {
       ProfScope ps("tc_light", s);
       tc_light_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kLightSmem, s>>>(
-          w->dag_off, w->dag_col, w->in_off, w->in_col, tl, nl, w->ctr, w->count, limit);
+          w->row, w->dag, tl, nl, w->ctr, w->count, limit);
       ::byo::note_launch();
       e = cudaGetLastError();
     }
@@ -870,7 +817,7 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
     if (e == cudaSuccess) {
       ProfScope ps("tc_heavy", s);
       tc_heavy_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kHeavySmem, s>>>(
-          w->dag_off, w->dag_col, w->in_off, w->in_col, th, nh, n, w->ctr, w->count, env_cap("BYO_TC_WINDOW", kWindow),
+          w->row, w->dag, th, nh, n, w->ctr, w->count, env_cap("BYO_TC_WINDOW", kWindow),
           env_cap("BYO_TC_BITMAP_BITS", kBitmapBits), limit);
       ::byo::note_launch();
       e = cudaGetLastError();
