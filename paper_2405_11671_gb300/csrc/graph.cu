@@ -136,37 +136,119 @@ __global__ void make_keys_kernel(const uint32_t* __restrict__ src, const uint32_
   }
 }
 
-// flag[i] = 1 iff keys[i] is the first copy of a valid key.
-__global__ void unique_flags_kernel(const uint64_t* __restrict__ keys, uint64_t cnt, int lb, uint32_t* flags) {
-  const uint64_t sentinel = (lb == 32) ? ~0ull : ((1ull << (2 * lb)) - 1);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t x = keys[i];
-    flags[i] = (x != sentinel && (i == 0 || keys[i - 1] != x)) ? 1u : 0u;
+// Unique pairs of the sorted keys, in tiles of kUniqTile keys striped over
+// the CTA (key tile0 + r * kUniqThreads + t is thread t's key of round r).
+// Key i is kept iff it is valid (not the sentinel of a dropped self loop) and
+// differs from key i - 1: the first copy of each pair.
+constexpr int kUniqThreads = 512;
+constexpr int kUniqRounds = 8;
+constexpr int kUniqWarps = kUniqThreads / 32;
+constexpr uint64_t kUniqTile = (uint64_t)kUniqThreads * kUniqRounds;
+
+struct UniqKey {
+  uint64_t x;     // the key (the sentinel past the end)
+  uint64_t prev;  // key i - 1 (meaningless for i = 0)
+  bool keep;      // first copy of a valid key
+};
+
+__device__ __forceinline__ UniqKey uniq_key(const uint64_t* __restrict__ keys, uint64_t i, uint64_t cnt,
+                                            uint64_t sentinel) {
+  UniqKey u;
+  u.x = i < cnt ? __ldg(keys + i) : sentinel;
+  u.prev = __shfl_up_sync(0xFFFFFFFFu, u.x, 1);
+  if (lane_id() == 0) u.prev = (i > 0 && i < cnt) ? __ldg(keys + i - 1) : ~u.x;
+  u.keep = u.x != sentinel && (i == 0 || u.prev != u.x);
+  return u;
+}
+
+__global__ void __launch_bounds__(kUniqThreads) unique_count_kernel(const uint64_t* __restrict__ keys, uint64_t cnt,
+                                                                     uint64_t sentinel,
+                                                                     uint32_t* __restrict__ tile_counts) {
+  __shared__ uint32_t wsum[kUniqWarps];
+  const uint64_t tile0 = (uint64_t)blockIdx.x * kUniqTile;
+  uint32_t c = 0;
+#pragma unroll
+  for (int r = 0; r < kUniqRounds; ++r)
+    c += __popc(__ballot_sync(0xFFFFFFFFu, uniq_key(keys, tile0 + (uint64_t)r * kUniqThreads + threadIdx.x, cnt,
+                                                    sentinel).keep));
+  if (lane_id() == 0) wsum[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t t = threadIdx.x < kUniqWarps ? wsum[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, o);
+    if (threadIdx.x == 0) tile_counts[blockIdx.x] = t;
   }
 }
 
-__global__ void compact_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ pos,
-                               const uint32_t* __restrict__ flags, uint64_t cnt, int lb, uint32_t* __restrict__ col,
-                               uint32_t* __restrict__ rows) {
+// Writes the kept keys of each tile from position tile_offs[tile] on, in key
+// order: col[p] = destination, rows[p] = source (if rows is not null), and,
+// if off is not null, the CSR offsets: off[s] = p for every row s in
+// (source of key i - 1, source of key i] when kept key i starts a row, and
+// off[s] = m for every s after the source of the last valid key.  Consecutive
+// lanes write consecutive positions.
+template <typename OffT>
+__global__ void __launch_bounds__(kUniqThreads) unique_write_kernel(const uint64_t* __restrict__ keys, uint64_t cnt,
+                                                                     uint64_t sentinel, int lb,
+                                                                     const uint64_t* __restrict__ tile_offs,
+                                                                     uint64_t m, uint32_t n,
+                                                                     uint32_t* __restrict__ col,
+                                                                     uint32_t* __restrict__ rows,
+                                                                     OffT* __restrict__ off) {
+  __shared__ uint32_t wsum[kUniqRounds * kUniqWarps];  // kept keys per (round, warp), then their exclusive scan
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  const uint64_t tile0 = (uint64_t)blockIdx.x * kUniqTile;
   const uint64_t lowmask = (lb == 32) ? 0xFFFFFFFFull : ((1ull << lb) - 1);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
-    if (flags[i]) {
-      uint64_t p = pos[i];
-      col[p] = (uint32_t)(keys[i] & lowmask);
-      rows[p] = (uint32_t)(keys[i] >> lb);
+  UniqKey u[kUniqRounds];
+  uint32_t ball[kUniqRounds];
+#pragma unroll
+  for (int r = 0; r < kUniqRounds; ++r) {
+    u[r] = uniq_key(keys, tile0 + (uint64_t)r * kUniqThreads + threadIdx.x, cnt, sentinel);
+    ball[r] = __ballot_sync(0xFFFFFFFFu, u[r].keep);
+    if (lane == 0) wsum[r * kUniqWarps + w] = __popc(ball[r]);
+  }
+  __syncthreads();
+  if (w == 0) {  // exclusive scan of the kUniqRounds * kUniqWarps counts, in key order
+    constexpr int kPer = kUniqRounds * kUniqWarps / 32;
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      v[j] = wsum[lane * kPer + j];
+      sum += v[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      wsum[lane * kPer + j] = run;
+      run += v[j];
     }
   }
-}
-
-// off[s] for every s from the sorted row ids: the first entry of row s.
-template <typename OffT>
-__global__ void offsets_kernel(const uint32_t* __restrict__ rows, uint64_t m, uint32_t n, OffT* __restrict__ off) {
-  uint64_t total = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= m; p += total) {
-    uint32_t hi = p < m ? rows[p] : n;  // rows [prev+1, hi] start at p
-    uint32_t lo = p == 0 ? 0 : rows[p - 1] + 1;
-    if (p == 0) lo = 0;
-    for (uint64_t s = lo; s <= hi && s <= n; ++s) off[s] = (OffT)p;
+  __syncthreads();
+  const uint64_t base = tile_offs[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < kUniqRounds; ++r) {
+    const uint64_t i = tile0 + (uint64_t)r * kUniqThreads + threadIdx.x;
+    const uint64_t x = u[r].x;
+    if (u[r].keep) {
+      const uint64_t p = base + wsum[r * kUniqWarps + w] + __popc(ball[r] & lanemask_lt());
+      const uint32_t src = (uint32_t)(x >> lb);
+      col[p] = (uint32_t)(x & lowmask);
+      if (rows) rows[p] = src;
+      if (off) {
+        // key i - 1 is valid (keys are sorted and the sentinel is the largest)
+        const uint64_t lo = i == 0 ? 0 : ((u[r].prev >> lb) + 1);
+        for (uint64_t s = lo; s <= src; ++s) off[s] = (OffT)p;
+      }
+    }
+    if (off && x != sentinel && (i + 1 >= cnt || __ldg(keys + i + 1) == sentinel)) {
+      for (uint64_t s = (x >> lb) + 1; s <= n; ++s) off[s] = (OffT)m;
+    }
   }
 }
 
@@ -263,11 +345,72 @@ int bits_for(uint32_t n) {
   return lb;
 }
 
+// The sorted keys (source << lb | destination) of the k pairs, and of their
+// reverses if sym; self loops become the sentinel, which sorts last.  *keys
+// and *tmp are the two key buffers (cnt entries each, released by the
+// caller); *sorted is the one holding the result.
+byo_status sorted_pair_keys(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t k, bool sym, int lb,
+                            cudaStream_t s, uint64_t** keys, uint64_t** tmp, uint64_t** sorted) {
+  const uint64_t cnt = sym ? 2 * k : k;
+  *keys = *tmp = *sorted = nullptr;
+  uint32_t* bad = nullptr;
+  byo_status st = tmp_alloc_t(&bad, 4, s, "flag");
+  if (st == BYO_OK) st = tmp_alloc_t(keys, cnt, s, "edge keys");
+  if (st == BYO_OK) st = tmp_alloc_t(tmp, cnt, s, "edge keys tmp");
+  if (st == BYO_OK) {
+    cudaMemsetAsync(bad, 0, 16, s);
+    if (k) {
+      make_keys_kernel<<<grid_for(k, 256), 256, 0, s>>>(src, dst, k, n, lb, sym, *keys, bad);
+      ::byo::note_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    uint32_t hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "make_keys_kernel");
+    else if (hbad) {
+      set_error("a vertex id is >= n (%u)", n);
+      st = BYO_ERR_INVALID_ARG;
+    }
+  }
+  if (st == BYO_OK) st = radix_sort_u64(*keys, *tmp, cnt, 2 * lb, sorted, s);
+  tmp_free(bad, s);
+  return st;
+}
+
+uint64_t pair_sentinel(int lb) { return (lb == 32) ? ~0ull : ((1ull << (2 * lb)) - 1); }
+
+// First output position of each tile's kept keys (*tile_offs, released by the
+// caller) and the number of kept keys *m (read back to the host).
+byo_status unique_positions(const uint64_t* sorted, uint64_t cnt, int lb, cudaStream_t s, uint64_t** tile_offs,
+                            uint64_t* m) {
+  *tile_offs = nullptr;
+  *m = 0;
+  const uint64_t ntiles = (cnt + kUniqTile - 1) / kUniqTile;
+  if (ntiles == 0) return BYO_OK;
+  uint32_t* counts = nullptr;
+  BYO_RETURN_IF(tmp_alloc_t(&counts, ntiles, s, "unique counts"));
+  byo_status st = tmp_alloc_t(tile_offs, ntiles, s, "unique positions");
+  if (st == BYO_OK) {
+    unique_count_kernel<<<(unsigned)ntiles, kUniqThreads, 0, s>>>(sorted, cnt, pair_sentinel(lb), counts);
+    ::byo::note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_status(e, "unique_count_kernel");
+  }
+  if (st == BYO_OK) st = scan_u32_to_u64(counts, *tile_offs, ntiles, m, s);
+  tmp_free(counts, s);
+  return st;
+}
+
 template <typename OffT>
-byo_status finish_csr(byo_graph* g, const uint32_t* rows, cudaStream_t s) {
-  OffT* off = static_cast<OffT*>(g->off);
-  offsets_kernel<OffT><<<grid_for(g->m + 1, 256), 256, 0, s>>>(rows, g->m, g->n, off); ::byo::note_launch();
-  BYO_CHECK_LAUNCH("offsets_kernel");
+byo_status unique_write(const uint64_t* sorted, uint64_t cnt, int lb, const uint64_t* tile_offs, uint64_t m,
+                        uint32_t n, uint32_t* col, uint32_t* rows, OffT* off, cudaStream_t s) {
+  const uint64_t ntiles = (cnt + kUniqTile - 1) / kUniqTile;
+  if (ntiles == 0 || m == 0) return BYO_OK;
+  unique_write_kernel<OffT><<<(unsigned)ntiles, kUniqThreads, 0, s>>>(sorted, cnt, pair_sentinel(lb), lb, tile_offs,
+                                                                       m, n, col, rows, off);
+  ::byo::note_launch();
+  BYO_CHECK_LAUNCH("unique_write_kernel");
   return BYO_OK;
 }
 
@@ -330,18 +473,31 @@ void graph_free(byo_graph* g) {
 
 byo_status build_csr(byo_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t k, bool sym, cudaStream_t s) {
   const uint32_t n = g->n;
-  uint32_t *rows = nullptr, *cols = nullptr, *bad = nullptr;
+  const int lb = bits_for(n > 1 ? n : 2);
+  const uint64_t cnt = sym ? 2 * k : k;
+  uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr, *tile_offs = nullptr;
+  uint32_t *rows = nullptr, *bad = nullptr;
   uint64_t m = 0;
-  BYO_RETURN_IF(sort_unique_pairs(n, src, dst, k, sym, s, &rows, &cols, &m));
-  g->m = m;
-  g->off64 = (g->flags & BYO_OFFSETS64) || m >= (1ull << 32);
-  byo_status st = dev_alloc(&g->off, (size_t)(n + 1) * (g->off64 ? 8 : 4) + 16, "CSR offsets");
+  byo_status st = sorted_pair_keys(n, src, dst, k, sym, lb, s, &keys, &tmp, &sorted);
+  if (st == BYO_OK) st = unique_positions(sorted, cnt, lb, s, &tile_offs, &m);
+  if (st == BYO_OK) {
+    g->m = m;
+    g->off64 = (g->flags & BYO_OFFSETS64) || m >= (1ull << 32);
+    st = dev_alloc(&g->off, (size_t)(n + 1) * (g->off64 ? 8 : 4) + 16, "CSR offsets");
+  }
   if (st == BYO_OK) st = dev_alloc_t(&g->col, m + 4, "CSR neighbours");
+  if (st == BYO_OK && !sym && m) st = tmp_alloc_t(&rows, m, s, "sorted rows");
   if (st == BYO_OK) {
     cudaMemsetAsync(g->col + m, 0, 16, s);
-    if (m) cudaMemcpyAsync(g->col, cols, sizeof(uint32_t) * m, cudaMemcpyDeviceToDevice, s);
-    st = g->off64 ? finish_csr<uint64_t>(g, rows, s) : finish_csr<uint32_t>(g, rows, s);
+    if (m == 0) cudaMemsetAsync(g->off, 0, (size_t)(n + 1) * (g->off64 ? 8 : 4), s);
+    st = g->off64 ? unique_write<uint64_t>(sorted, cnt, lb, tile_offs, m, n, g->col, rows,
+                                           static_cast<uint64_t*>(g->off), s)
+                  : unique_write<uint32_t>(sorted, cnt, lb, tile_offs, m, n, g->col, rows,
+                                           static_cast<uint32_t*>(g->off), s);
   }
+  tmp_free(keys, s);
+  tmp_free(tmp, s);
+  tmp_free(tile_offs, s);
   if (st == BYO_OK && !sym && m) st = tmp_alloc_t(&bad, 1, s, "flag");
   if (st == BYO_OK && !sym && m) {
     cudaMemsetAsync(bad, 0, 4, s);
@@ -361,7 +517,6 @@ byo_status build_csr(byo_graph* g, const uint32_t* src, const uint32_t* dst, uin
     }
   }
   tmp_free(rows, s);
-  tmp_free(cols, s);
   tmp_free(bad, s);
   if (st == BYO_OK) st = rebuild_buckets(g, s);
   if (st == BYO_OK) {
@@ -379,56 +534,17 @@ byo_status sort_unique_pairs(uint32_t n, const uint32_t* src, const uint32_t* ds
   *count = 0;
   const int lb = bits_for(n > 1 ? n : 2);
   const uint64_t cnt = sym ? 2 * k : k;
-  uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr, *pos = nullptr;
-  uint32_t *flags = nullptr, *rows = nullptr, *cols = nullptr, *bad = nullptr;
-  byo_status st = tmp_alloc_t(&bad, 4, s, "flag");
-  if (st == BYO_OK) st = tmp_alloc_t(&keys, cnt, s, "edge keys");
-  if (st == BYO_OK) st = tmp_alloc_t(&tmp, cnt, s, "edge keys tmp");
-  if (st == BYO_OK) {
-    cudaMemsetAsync(bad, 0, 16, s);
-    if (k) {
-      make_keys_kernel<<<grid_for(k, 256), 256, 0, s>>>(src, dst, k, n, lb, sym, keys, bad);
-      ::byo::note_launch();
-    }
-    cudaError_t e = cudaGetLastError();
-    uint32_t hbad = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = cuda_status(e, "make_keys_kernel");
-    else if (hbad) {
-      set_error("a vertex id is >= n (%u)", n);
-      st = BYO_ERR_INVALID_ARG;
-    }
-  }
-  if (st == BYO_OK) st = radix_sort_u64(keys, tmp, cnt, 2 * lb, &sorted, s);
-  if (st == BYO_OK) {
-    pos = sorted == keys ? tmp : keys;  // the other key buffer holds the positions
-    st = tmp_alloc_t(&flags, cnt, s, "unique flags");
-  }
+  uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr, *tile_offs = nullptr;
+  uint32_t *rows = nullptr, *cols = nullptr;
   uint64_t m = 0;
-  if (st == BYO_OK) {
-    if (cnt) {
-      unique_flags_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(sorted, cnt, lb, flags);
-      ::byo::note_launch();
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) st = cuda_status(e, "unique_flags_kernel");
-  }
-  if (st == BYO_OK) st = scan_u32_to_u64(flags, pos, cnt, &m, s);
+  byo_status st = sorted_pair_keys(n, src, dst, k, sym, lb, s, &keys, &tmp, &sorted);
+  if (st == BYO_OK) st = unique_positions(sorted, cnt, lb, s, &tile_offs, &m);
   if (st == BYO_OK) st = tmp_alloc_t(&rows, m + 4, s, "sorted rows");
   if (st == BYO_OK) st = tmp_alloc_t(&cols, m + 4, s, "sorted cols");
-  if (st == BYO_OK) {
-    if (cnt) {
-      compact_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(sorted, pos, flags, cnt, lb, cols, rows);
-      ::byo::note_launch();
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) st = cuda_status(e, "compact_kernel");
-  }
+  if (st == BYO_OK) st = unique_write<uint32_t>(sorted, cnt, lb, tile_offs, m, n, cols, rows, nullptr, s);
   tmp_free(keys, s);
   tmp_free(tmp, s);
-  tmp_free(flags, s);
-  tmp_free(bad, s);
+  tmp_free(tile_offs, s);
   if (st != BYO_OK) {
     tmp_free(rows, s);
     tmp_free(cols, s);

@@ -140,11 +140,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
   __shared__ uint32_t h[kRadix];
   for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
   __syncthreads();
-  uint64_t base = (uint64_t)blockIdx.x * kSortTile;
-  for (uint64_t i = threadIdx.x; i < kSortTile; i += blockDim.x) {
-    uint64_t idx = base + i;
-    if (idx < n) atomicAdd(&h[(uint32_t)(keys[idx] >> shift) & mask], 1u);
+  const uint64_t base = (uint64_t)blockIdx.x * kSortTile + threadIdx.x;
+  uint64_t k[kSortRounds];
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {  // all loads in flight before the first count
+    const uint64_t idx = base + (uint64_t)r * kSortThreads;
+    k[r] = idx < n ? __ldg(keys + idx) : 0;
   }
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r)
+    if (base + (uint64_t)r * kSortThreads < n) atomicAdd(&h[(uint32_t)(k[r] >> shift) & mask], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(uint64_t)d * ntiles + blockIdx.x] = h[d];
 }
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(const ui
   extern __shared__ __align__(16) uint64_t sk[];  // the tile, reordered by digit
   __shared__ uint32_t cnt[kSortWarps][kRadix];
   __shared__ uint32_t start[kRadix];              // tile-local start of each digit
-  __shared__ uint64_t gbase[kRadix];              // global start of each digit's run of this tile
+  __shared__ uint64_t gbase[kRadix];              // output index of the digit's tile-local position 0
   const int w = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
   for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&cnt[0][0])[i] = 0;
@@ -218,6 +223,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(const ui
 #pragma unroll
     for (int j = 0; j < kRadix / 32; ++j) {
       start[lane * (kRadix / 32) + j] = run;
+      gbase[lane * (kRadix / 32) + j] -= run;  // now the output index of tile-local position 0 of the digit
       run += v[j];
     }
   }
@@ -234,8 +240,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(const ui
   const uint32_t count = (uint32_t)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
   for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
     const uint64_t key = sk[i];
-    const uint32_t d = (uint32_t)(key >> shift) & mask;
-    out[gbase[d] + (i - start[d])] = key;
+    out[gbase[(uint32_t)(key >> shift) & mask] + i] = key;
   }
 }
 
