@@ -242,7 +242,9 @@ byo_status byo_pagerank(const byo_graph* g, float damping, uint32_t iters, float
  * relabelled by that order; each DAG edge is intersected from the side with
  * the shorter out-list, the other side's N+ held in shared memory (staged by
  * TMA bulk copies and hashed, or a bitmap of the ranks above a high-degree
- * vertex).  *host_count receives the number of triangles; synchronises.
+ * vertex); out-lists of 32..16384 ids are sorted by rank first, so that a
+ * walked out-list of a lower-ranked endpoint starts after the other endpoint.
+ * *host_count receives the number of triangles; synchronises.
  * Errors: INVALID_ARG, OUT_OF_MEMORY, TIMEOUT, CUDA.
  */
 byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
@@ -250,7 +252,8 @@ byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
 /* Runs byo_tc and reports its intersection work (host_work3, host array of 3):
  * [0] sum_c d+(c)^2 and [1] sum_c d-(c) d+(c) -- together the out-list ids a
  * merge of both lists of every DAG edge reads -- and [2] the ids this library
- * walks (sum over DAG edges of the shorter out-list).  Synchronises. */
+ * walks (sum over DAG edges of the shorter out-list, only its ids ranked above
+ * the other endpoint when that list is sorted).  Synchronises. */
 byo_status byo_tc_work(const byo_graph* g, uint64_t* host_work3, void* stream);
 
 /* ------------------------------------------------------------------------ */

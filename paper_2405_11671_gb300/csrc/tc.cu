@@ -19,6 +19,11 @@
 // rank range above c fits the CTA's shared memory, N+(c) becomes a bitmap of
 // that range (one probe per id, no collisions), otherwise it is staged in
 // windows of kWindow ids, each hashed into the CTA's shared memory.
+// Out-lists of kSortedMin..kSortedMax ids are sorted by rank after the filter
+// (bitonic networks: one warp per list up to kWarpSortMax ids, in registers,
+// one CTA per longer list, in shared memory), so that the walk of an
+// in-neighbour p's out-list for a centre c skips the ids at or below c, which
+// N+(c) cannot hold: the lane holding p finds where they end by binary search.
 #include <stdlib.h>
 
 #include "byo_internal.cuh"
@@ -32,11 +37,15 @@ namespace byo {
 constexpr uint32_t kLightMax = 256;   // capacity of a warp's shared-memory slice (ids)
 constexpr uint32_t kWindow = 2048;    // capacity of a CTA's shared-memory window (ids)
 constexpr int kTcThreads = 256;
+constexpr uint32_t kSortedMin = 32;       // shorter out-lists are walked in concatenation, never trimmed
+constexpr uint32_t kWarpSortMax = 1024;   // longest out-list sorted by one warp
+constexpr uint32_t kSortedMax = 16384;    // longest out-list sorted at all (by one CTA)
 
-// The light/heavy split, the window length and the bitmap range can be
-// lowered (never raised) with BYO_TC_LIGHT_MAX / BYO_TC_WINDOW /
-// BYO_TC_BITMAP_BITS, so that small test graphs exercise the CTA path, the
-// hashed windows and multi-window intersections.
+// The light/heavy split, the window length, the bitmap range and the sorted
+// out-list lengths can be lowered (never raised) with BYO_TC_LIGHT_MAX /
+// BYO_TC_WINDOW / BYO_TC_BITMAP_BITS / BYO_TC_WARP_SORT_MAX / BYO_TC_SORT_MAX,
+// so that small test graphs exercise the CTA path, the hashed windows,
+// multi-window intersections, both sorts and unsorted long out-lists.
 static uint32_t env_cap(const char* name, uint32_t cap) {
   const char* e = getenv(name);
   if (!e || !*e) return cap;
@@ -233,6 +242,108 @@ __global__ void __launch_bounds__(kTcThreads) tc_fill_kernel(G g, VBins bins, co
   }
 }
 
+// ---------------------------------------------------------------- sorted out-lists
+// Ascending bitonic sorting network over buf[0, S) (S a power of two) by
+// `lanes` threads, this one numbered t; the stages are ordered by a warp
+// (kCta = false) or CTA barrier.
+template <bool kCta>
+__device__ __forceinline__ void bitonic_sort(uint32_t* buf, uint32_t S, uint32_t t, uint32_t lanes) {
+  for (uint32_t k = 2; k <= S; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t q = t; q < S / 2; q += lanes) {  // pair q: (i, i + j), i = q with a zero inserted at bit j
+        const uint32_t i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+        const uint32_t l = i | j;
+        const uint32_t a = buf[i], b = buf[l];
+        if ((a > b) == ((i & k) == 0)) {
+          buf[i] = b;
+          buf[l] = a;
+        }
+      }
+      if (kCta) __syncthreads();
+      else __syncwarp();
+    }
+}
+
+__host__ __device__ __forceinline__ uint32_t pow2_at_least(uint32_t d) {
+  uint32_t s = 1;
+  while (s < d) s <<= 1;
+  return s;
+}
+
+// One warp sorts an out-list of d <= 32 R ids held in registers: element
+// e = 32 r + lane is v[r] of that lane, padded with kInf.  Stages that pair
+// elements less than 32 apart exchange them between lanes, the others between
+// a lane's registers.
+template <int R>
+__device__ __forceinline__ void warp_sort_list(uint32_t* p, uint32_t d) {
+  const uint32_t lane = lane_id();
+  uint32_t v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = r * 32 + lane < d ? p[r * 32 + lane] : kInf;
+#pragma unroll
+  for (uint32_t k = 2; k <= 32u * R; k <<= 1) {
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int r2 = r | (int)(j / 32);
+          if (r2 != r) {
+            const bool asc = ((uint32_t)(r * 32) & k) == 0;  // k >= 64: the lane bits do not matter
+            const uint32_t a = v[r], b = v[r2];
+            v[r] = asc ? min(a, b) : max(a, b);
+            v[r2] = asc ? max(a, b) : min(a, b);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, v[r], j);
+          const bool asc = ((r * 32 + lane) & k) == 0, lower = (lane & j) == 0;
+          v[r] = asc == lower ? min(v[r], o) : max(v[r], o);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r * 32 + lane < d) p[r * 32 + lane] = v[r];
+}
+
+// Out-lists of kSortedMin..wmax ids, one warp each: the warp reads the row
+// records of 32 rows at a time and sorts the ones in range in registers.
+__global__ void __launch_bounds__(kTcThreads) tc_sort_warp_kernel(const RowInfo* __restrict__ row,
+                                                                 uint32_t* __restrict__ dag, uint32_t n,
+                                                                 uint32_t wmax) {
+  const uint32_t lane = lane_id();
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r0 = gw * 32; r0 < n; r0 += nw * 32) {
+    uint64_t off = 0;
+    uint32_t d = 0;
+    if (r0 + lane < n) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + r0 + lane));
+      off = ((uint64_t)q.y << 32) | q.x;
+      d = q.z;
+    }
+    uint32_t todo = __ballot_sync(0xFFFFFFFFu, d >= kSortedMin && d <= wmax);
+    while (todo) {
+      const int l = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t dl = __shfl_sync(0xFFFFFFFFu, d, l);
+      uint32_t* p = dag + __shfl_sync(0xFFFFFFFFu, off, l);
+      switch (pow2_at_least(dl)) {
+        case 32: warp_sort_list<1>(p, dl); break;
+        case 64: warp_sort_list<2>(p, dl); break;
+        case 128: warp_sort_list<4>(p, dl); break;
+        case 256: warp_sort_list<8>(p, dl); break;
+        case 512: warp_sort_list<16>(p, dl); break;
+        default: warp_sort_list<32>(p, dl); break;  // 1024 = kWarpSortMax
+      }
+    }
+  }
+}
+
 // degree of rank r, from the sorted (degree << lbn | v) keys
 __global__ void tc_rdeg_kernel(const uint64_t* __restrict__ sorted, uint32_t n, int lbn, uint32_t* __restrict__ rdeg) {
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x)
@@ -259,11 +370,13 @@ __device__ __forceinline__ uint32_t chunks(uint32_t len) { return (len + kPartne
 // Intersection work of the DAG: the out-list lengths every method must read
 // (sum over edges a->b of d+(a) + d+(b) = sum_c d+(c)^2 + d-(c) d+(c)) and the
 // ids this implementation walks: per edge a->b the shorter out-list, d+(b) at
-// centre a when d+(b) <= d+(a), else d+(a) at centre b, nothing when the
-// walked side is the single-entry list of a (see the task rules).  One thread
-// per vertex over its out-list (out-lists are short in this order).
+// centre a when d+(b) <= d+(a), else N+(a) at centre b (only its ids above b
+// when N+(a) is sorted: kSortedMin <= d+(a) <= smax), nothing when the walked
+// side is the single-entry list of a (see the task rules).  One thread per
+// vertex over its out-list (out-lists are short in this order); runs after
+// the sorts.
 __global__ void tc_work_kernel(const RowInfo* __restrict__ row, const uint32_t* __restrict__ dag, uint32_t n,
-                               unsigned long long* work) {
+                               uint32_t smax, unsigned long long* work) {
   unsigned long long sq = 0, io = 0, mn = 0;
   for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (uint64_t)gridDim.x * blockDim.x) {
     const RowInfo ra = row[a];
@@ -271,9 +384,10 @@ __global__ void tc_work_kernel(const RowInfo* __restrict__ row, const uint32_t* 
     sq += da * da;
     io += (unsigned long long)(ra.len - ra.dplus) * da;
     if (da < 2) continue;
+    const bool sorted = da >= kSortedMin && da <= smax;
     for (uint64_t i = ra.off; i < ra.off + da; ++i) {
       const unsigned long long db = row[dag[i]].dplus;
-      mn += db <= da ? db : da;
+      mn += db <= da ? db : (sorted ? da - 1 - (i - ra.off) : da);
     }
   }
 #pragma unroll
@@ -316,6 +430,32 @@ __global__ void tc_task_fill_kernel(const RowInfo* __restrict__ row, uint32_t n,
       for (uint32_t lo = 0; lo < dp; lo += kPartners) *out++ = TcTask{(uint32_t)c, 0u, lo, min(dp, lo + kPartners)};
     if (dp >= 3)
       for (uint32_t lo = 0; lo < dm; lo += kPartners) *out++ = TcTask{(uint32_t)c, 1u, lo, min(dm, lo + kPartners)};
+  }
+}
+
+// Out-lists of more than lo and at most hi ids, one CTA each, in dynamic
+// shared memory of pow2_at_least(hi) words.  Every out-list longer than wmax
+// is a CTA centre (wmax is at least the light/heavy split), so the CTA tasks
+// list them.  Two launches: up to kSortMidMax ids with many small CTAs, the
+// longer lists with room for kSortedMax ids.
+constexpr uint32_t kSortMidMax = 4096;
+
+__global__ void __launch_bounds__(kTcThreads) tc_sort_cta_kernel(const RowInfo* __restrict__ row,
+                                                                uint32_t* __restrict__ dag,
+                                                                const TcTask* __restrict__ tasks, uint64_t ntasks,
+                                                                uint32_t lo, uint32_t hi) {
+  extern __shared__ __align__(16) uint32_t cbuf[];
+  for (uint64_t t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const RowInfo ri = row[tasks[t].c];
+    const uint32_t d = ri.dplus;
+    if (d <= lo || d > hi) continue;
+    uint32_t* p = dag + ri.off;
+    const uint32_t S = pow2_at_least(d);
+    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) cbuf[i] = i < d ? p[i] : kInf;
+    __syncthreads();
+    bitonic_sort<true>(cbuf, S, threadIdx.x, blockDim.x);
+    for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) p[i] = cbuf[i];
+    __syncthreads();
   }
 }
 
@@ -415,17 +555,29 @@ __device__ __forceinline__ uint32_t warp_count_group(const uint32_t* __restrict_
 // A lane's partner p: its out-list, kept only on the side that walks the
 // shorter list (kind 0: d+(p) <= d+(c); kind 1: d+(p) < d+(c)).  A kind-1
 // partner's out-list holds c itself, which N+(c) does not, so one of length 1
-// cannot meet N+(c) and is skipped.
-__device__ __forceinline__ void partner_list(const RowInfo* __restrict__ row, bool has, uint32_t p, uint32_t kind,
-                                             uint32_t dc, uint64_t* vb, uint32_t* len) {
+// cannot meet N+(c) and is skipped; a sorted one (kSortedMin..smax ids) keeps
+// only its ids above c (a binary search by the lane).
+__device__ __forceinline__ void partner_list(const RowInfo* __restrict__ row, const uint32_t* __restrict__ dag_col,
+                                             bool has, uint32_t p, uint32_t kind, uint32_t c, uint32_t dc,
+                                             uint32_t smax, uint64_t* vb, uint32_t* len) {
   *vb = 0;
   *len = 0;
   if (!has) return;
   const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + p));  // off (2 words), dplus, len
   const uint32_t d = q.z;
   if (kind == 0 ? d <= dc : (d < dc && d >= 2)) {
-    *vb = ((uint64_t)q.y << 32) | q.x;
-    *len = d;
+    uint64_t b = ((uint64_t)q.y << 32) | q.x;
+    uint32_t lo = 0;
+    if (kind == 1 && d >= kSortedMin && d <= smax) {
+      uint32_t hi = d;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(dag_col + b + mid) > c) hi = mid;
+        else lo = mid + 1;
+      }
+    }
+    *vb = b + lo;
+    *len = d - lo;
   }
 }
 
@@ -436,8 +588,8 @@ __device__ __forceinline__ void partner_list(const RowInfo* __restrict__ row, bo
 template <typename Set>
 __device__ __forceinline__ uint64_t walk_partners(const RowInfo* __restrict__ row,
                                                   const uint32_t* __restrict__ dag_col, const uint32_t* partners,
-                                                  const TcTask& t, uint32_t dc, uint32_t w, uint32_t warps,
-                                                  const Set& set) {
+                                                  const TcTask& t, uint32_t dc, uint32_t smax, uint32_t w,
+                                                  uint32_t warps, const Set& set) {
   const uint32_t lane = lane_id(), step = warps * 32;
   uint64_t hits = 0;
   uint32_t k0 = t.lo + w * 32;
@@ -445,13 +597,13 @@ __device__ __forceinline__ uint64_t walk_partners(const RowInfo* __restrict__ ro
   uint32_t p = has ? __ldg(partners + k0 + lane) : 0;
   uint64_t vb;
   uint32_t len;
-  partner_list(row, has, p, t.kind, dc, &vb, &len);
+  partner_list(row, dag_col, has, p, t.kind, t.c, dc, smax, &vb, &len);
   bool has1 = k0 + step + lane < t.hi;
   uint32_t p1 = has1 ? __ldg(partners + k0 + step + lane) : 0;
   for (; k0 < t.hi; k0 += step) {
     uint64_t vb1;
     uint32_t len1;
-    partner_list(row, has1, p1, t.kind, dc, &vb1, &len1);  // group k0 + step
+    partner_list(row, dag_col, has1, p1, t.kind, t.c, dc, smax, &vb1, &len1);  // group k0 + step
     const bool has2 = k0 + 2 * step + lane < t.hi;
     const uint32_t p2 = has2 ? __ldg(partners + k0 + 2 * step + lane) : 0;
     hits += warp_count_group(dag_col, vb, len, set);
@@ -471,7 +623,7 @@ __global__ void __launch_bounds__(kTcThreads, 5) tc_light_kernel(const RowInfo* 
                                                               const uint32_t* __restrict__ dag_col,
                                                               const TcTask* __restrict__ tasks, uint64_t ntasks,
                                                               uint32_t* ctr, unsigned long long* count,
-                                                              uint64_t limit_ns) {
+                                                              uint32_t smax, uint64_t limit_ns) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ __align__(8) uint64_t bar[kTcThreads / 32];
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
@@ -531,7 +683,7 @@ __global__ void __launch_bounds__(kTcThreads, 5) tc_light_kernel(const RowInfo* 
     SmemHash set{table, (1u << bits) - 1, 32 - bits, lo, hi};
     const RowInfo rc = row[c];
     const uint32_t* partners = dag_col + rc.off + (t.kind == 0 ? 0u : rc.dplus);
-    hits += walk_partners(row, dag_col, partners, t, dc, 0, 1, set);
+    hits += walk_partners(row, dag_col, partners, t, dc, smax, 0, 1, set);
   }
   uint64_t sum = hits;
 #pragma unroll
@@ -550,7 +702,7 @@ constexpr size_t kHeavySmem = (size_t)kHeavyWords * sizeof(uint32_t);
 struct CentreGroups {
   const uint32_t* out;  // N+(c)
   const uint32_t* in;   // N-(c)
-  uint32_t dc, dm, g0, gt;
+  uint32_t c, dc, dm, g0, gt, smax;
   __device__ __forceinline__ uint32_t partner(uint32_t g, bool* has, uint32_t* kind) const {
     const uint32_t lane = lane_id();
     if (g < g0) {
@@ -586,7 +738,7 @@ __device__ __forceinline__ uint32_t walk_groups(const RowInfo* __restrict__ row,
   uint32_t p = cg.partner(g, &has, &kind);
   uint64_t vb;
   uint32_t len;
-  partner_list(row, has, p, kind, cg.dc, &vb, &len);
+  partner_list(row, dag_col, has, p, kind, cg.c, cg.dc, cg.smax, &vb, &len);
   uint32_t gn = grab_group(gctr);
   bool hasn = false;
   uint32_t kindn = 0, pn = gn < cg.gt ? cg.partner(gn, &hasn, &kindn) : 0u;
@@ -594,7 +746,7 @@ __device__ __forceinline__ uint32_t walk_groups(const RowInfo* __restrict__ row,
   while (true) {
     uint64_t vbn;
     uint32_t lenn;
-    partner_list(row, hasn, pn, kindn, cg.dc, &vbn, &lenn);
+    partner_list(row, dag_col, hasn, pn, kindn, cg.c, cg.dc, cg.smax, &vbn, &lenn);
     const uint32_t gnn = gn < cg.gt ? grab_group(gctr) : cg.gt;
     bool hasnn = false;
     uint32_t kindnn = 0, pnn = gnn < cg.gt ? cg.partner(gnn, &hasnn, &kindnn) : 0u;
@@ -619,7 +771,7 @@ __global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const RowInfo* 
                                                               const TcTask* __restrict__ tasks, uint64_t ntasks,
                                                               uint32_t n, uint32_t* ctr, unsigned long long* count,
                                                               uint32_t window, uint32_t bitmap_bits,
-                                                              uint64_t limit_ns) {
+                                                              uint32_t smax, uint64_t limit_ns) {
   extern __shared__ __align__(16) uint32_t win[];
   uint32_t* table = win + kWindow + 8;
   __shared__ __align__(8) uint64_t bar;
@@ -641,7 +793,7 @@ __global__ void __launch_bounds__(kTcThreads, 6) tc_heavy_kernel(const RowInfo* 
     const uint64_t beg = rc.off, end = rc.off + rc.dplus, ib = end;
     const uint32_t dc = rc.dplus, dm = rc.len - rc.dplus;
     const uint32_t g0 = (dc + 31) / 32;
-    const CentreGroups cg{dag_col + beg, dag_col + ib, dc, dm, g0, g0 + (dm + 31) / 32};
+    const CentreGroups cg{dag_col + beg, dag_col + ib, c, dc, dm, g0, g0 + (dm + 31) / 32, smax};
     const uint32_t above = n - 1 - c;  // N+(c) lies in the ranks (c, n)
     if (above <= bitmap_bits) {
       const uint32_t words = (above + 127) / 128 * 4;
@@ -768,14 +920,11 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
     ::byo::note_launch();
   }
   BYO_CHECK_LAUNCH("tc_fill_kernel");
-  if (want_work) {
-    cudaMemsetAsync(w->work, 0, 4 * sizeof(unsigned long long), s);
-    tc_work_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->row, w->dag, n, w->work);
-    ::byo::note_launch();
-    BYO_CUDA(cudaMemcpyAsync(w->host_work, w->work, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  }
   // tasks
   const uint32_t light_max = env_cap("BYO_TC_LIGHT_MAX", kLightMax);
+  uint32_t wmax = env_cap("BYO_TC_WARP_SORT_MAX", kWarpSortMax);
+  if (wmax < light_max) wmax = light_max;  // longer out-lists are CTA centres, listed by the CTA tasks
+  const uint32_t smax = env_cap("BYO_TC_SORT_MAX", kSortedMax);
   tc_task_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->row, n, light_max, w->cnt_l, w->cnt_h);
   ::byo::note_launch();
   BYO_CHECK_LAUNCH("tc_task_count_kernel");
@@ -794,6 +943,39 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_status(e, "tc_task_fill_kernel");
   }
+  if (st == BYO_OK) {  // sort the out-lists the walks may trim
+    cudaError_t e;
+    {
+      ProfScope ps("tc_sort", s);
+      tc_sort_warp_kernel<<<sm_count() * 4, kTcThreads, 0, s>>>(w->row, w->dag, n, wmax < smax ? wmax : smax);
+      ::byo::note_launch();
+      e = cudaGetLastError();
+    }
+    const uint32_t mid = smax < kSortMidMax ? smax : kSortMidMax;
+    const uint32_t tiers[2][3] = {{wmax, mid, 8}, {mid, smax, 2}};  // lo, hi, CTAs per SM
+    for (const auto& tier : tiers) {
+      if (e != cudaSuccess || !nh || tier[1] <= tier[0]) continue;
+      const size_t smem = (size_t)pow2_at_least(tier[1]) * sizeof(uint32_t);
+      e = cudaFuncSetAttribute(tc_sort_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) break;
+      ProfScope ps("tc_sort_cta", s);
+      const uint64_t cap = (uint64_t)sm_count() * tier[2];
+      tc_sort_cta_kernel<<<(unsigned)(nh < cap ? nh : cap), kTcThreads, smem, s>>>(w->row, w->dag, th, nh, tier[0],
+                                                                                    tier[1]);
+      ::byo::note_launch();
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = cuda_status(e, "tc_sort");
+  }
+  if (st == BYO_OK && want_work) {
+    cudaMemsetAsync(w->work, 0, 4 * sizeof(unsigned long long), s);
+    tc_work_kernel<<<grid_for(n, 256), 256, 0, s>>>(w->row, w->dag, n, smax, w->work);
+    ::byo::note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(w->host_work, w->work, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_status(e, "tc_work_kernel");
+  }
   const uint64_t limit = timeout_ns();
   if (st == BYO_OK && nl) {
     int per_sm = 0;
@@ -803,7 +985,7 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
     if (e == cudaSuccess) {
       ProfScope ps("tc_light", s);
       tc_light_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kLightSmem, s>>>(
-          w->row, w->dag, tl, nl, w->ctr, w->count, limit);
+          w->row, w->dag, tl, nl, w->ctr, w->count, smax, limit);
       ::byo::note_launch();
       e = cudaGetLastError();
     }
@@ -818,7 +1000,7 @@ byo_status run_tc(byo_graph* g, G view, uint64_t* host_count, bool want_work, cu
       ProfScope ps("tc_heavy", s);
       tc_heavy_kernel<<<(unsigned)(sm_count() * (per_sm > 0 ? per_sm : 1)), kTcThreads, kHeavySmem, s>>>(
           w->row, w->dag, th, nh, n, w->ctr, w->count, env_cap("BYO_TC_WINDOW", kWindow),
-          env_cap("BYO_TC_BITMAP_BITS", kBitmapBits), limit);
+          env_cap("BYO_TC_BITMAP_BITS", kBitmapBits), smax, limit);
       ::byo::note_launch();
       e = cudaGetLastError();
     }

@@ -274,6 +274,24 @@ def test_triangle_count_cta_path_and_windows(byo, monkeypatch, light_max, window
         g.close()
 
 
+@pytest.mark.parametrize("light_max,warp_sort_max,sort_max", [(256, 1024, 16384), (4, 32, 16384), (4, 32, 48),
+                                                              (64, 64, 40), (4, 4, 4)])
+def test_triangle_count_sorted_out_lists(byo, monkeypatch, light_max, warp_sort_max, sort_max):
+    # out-lists of 32..sort_max ids are sorted by rank, by one warp up to
+    # max(warp_sort_max, light_max) ids and by one CTA above, and the walk of
+    # an in-neighbour's sorted out-list starts after the centre; longer lists
+    # are walked whole.  K_1100 has out-lists of up to 1,099 ids (the CTA sort
+    # at the default limits) and C(1100, 3) triangles.
+    monkeypatch.setenv("BYO_TC_LIGHT_MAX", str(light_max))
+    monkeypatch.setenv("BYO_TC_WARP_SORT_MAX", str(warp_sort_max))
+    monkeypatch.setenv("BYO_TC_SORT_MAX", str(sort_max))
+    for n, src, dst in (graphgen.rmat_small(13, 16, 44), _complete(90), _complete(1100)):
+        want = n * (n - 1) * (n - 2) // 6 if len(src) == n * (n - 1) // 2 else oracle.tc(oracle.csr_build(n, src, dst))
+        g = byo.Graph(n, dev_u32(src), dev_u32(dst))
+        assert byo.byo_tc(g.handle) == want
+        g.close()
+
+
 def test_triangle_work_statistics(byo):
     # the byte model of the benchmark's roofline rests on these three sums;
     # recompute them from the oracle's CSR with the (degree, id) orientation
@@ -288,7 +306,16 @@ def test_triangle_work_statistics(byo):
     dp = np.bincount(a, minlength=n)
     dm = np.bincount(b, minlength=n)
     da, db = dp[a], dp[b]
-    walked = np.where(da < 2, 0, np.minimum(da, db))
+    # at centre b (d+(a) < d+(b)) a sorted out-list of a (32..16384 ids) is
+    # walked from the first id above b: the ids of N+(a) ranked above b
+    rank = np.empty(n, np.int64)
+    rank[np.lexsort((np.arange(n), deg))] = np.arange(n)
+    o = np.lexsort((rank[b], a))
+    pos = np.empty(len(a), np.int64)
+    pos[o] = np.arange(len(a)) - np.searchsorted(a[o], a[o], "left")
+    trimmed = np.where((da >= 32) & (da <= 16384), da - 1 - pos, da)
+    walked = np.where(da < 2, 0, np.where(db <= da, db, trimmed))
+    assert (trimmed < da).any()  # the graph has sorted out-lists that are trimmed
     g = byo.Graph(n, dev_u32(src), dev_u32(dst))
     try:
         assert byo.byo_tc_work(g.handle) == (int((dp * dp).sum()), int((dm * dp).sum()), int(walked.sum()))
