@@ -561,10 +561,11 @@ def main():
     for name, (nl, ms) in ranked:
         if name == "tc_count":
             tc_work = byo.byo_tc_work(g.handle)
-            # what this intersection must read: the shorter out-list of every DAG
-            # edge (sum of min(d+u, d+v) ids), every partner's id and out-list
-            # bounds (each DAG edge is a partner once from each end: m ids,
-            # 2 x 8-byte offsets each), every centre's out-list once (m/2 ids)
+            # what this intersection must read: the ids it walks (per DAG edge
+            # the shorter out-list, an in-neighbour's sorted list only above the
+            # centre: byo_tc_work[2]), every partner's id and out-list bounds
+            # (each DAG edge is a partner once from each end: m ids, 2 x 8-byte
+            # offsets each), every centre's out-list once (m/2 ids)
             b = 4.0 * tc_work[2] + 20.0 * m + 2.0 * m
         elif name == "bfs_persistent":
             b = statistics.mean(bfs_bytes)
@@ -584,8 +585,9 @@ def main():
             entry["merge_model_bytes"] = merge_b
             entry["merge_model_frac"] = round(merge_b / (avg_ms / 1e3) / 1e9 / peak, 4)
             entry["note"] = ("bytes = shorter out-list of each DAG edge + partner ids and bounds + centre lists "
-                             "(the walk-shorter/probe-set method; latency/issue bound at RMAT-22 where L2 serves "
-                             "most walks, near DRAM-bound at RMAT-25). merge_model_* = both out-lists of every "
+                             "(the walk-shorter/probe-set method, in-neighbour walks trimmed to the ids above the "
+                             "centre; issue bound at RMAT-22 where L2 serves most walks, walks from DRAM at RMAT-25). "
+                             "merge_model_* = both out-lists of every "
                              "DAG edge (a sorted merge's reads)")
         if roof is None:
             roof = entry
