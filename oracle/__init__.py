@@ -2,7 +2,8 @@
 
 Python handle on ``byo_oracle.c``: a plain, serial CPU restatement of the BYO
 paper's definitions (CSR build, BFS, connected components, PageRank, triangle
-counting, batch updates of the edge set) plus the FP64 schedule network.  Only
+counting, single-source betweenness, batch updates of the edge set) plus the
+FP64 schedule network.  Only
 ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it; the CUDA library never does, and this module imports
 nothing from it.
@@ -60,6 +61,8 @@ def _load():
         lib.ora_pagerank.restype = None
         lib.ora_pagerank.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_double, ctypes.c_uint32,
                                      _f64p, _f64p]
+        lib.ora_bc.restype = None
+        lib.ora_bc.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_uint32, _u32p, _f64p, _f64p]
         lib.ora_tc.restype = ctypes.c_uint64
         lib.ora_tc.argtypes = [ctypes.c_uint32, _u64p, _u32p]
         lib.ora_dyn_create.restype = ctypes.c_void_p
@@ -143,6 +146,17 @@ def pagerank(g: CSR, damping: float = 0.85, iters: int = 20):
     col = g.col if len(g.col) else np.zeros(1, np.uint32)
     _load().ora_pagerank(g.n, _p(g.off), _p(col), damping, iters, _p(p), _p(r))
     return p[:g.n], r[:iters]
+
+
+def bc(g: CSR, s: int):
+    """Single-source betweenness from ``s``: (level, sigma = shortest-path
+    counts, delta = dependency of s on each vertex), Brandes' accumulation."""
+    level = np.empty(max(g.n, 1), np.uint32)
+    sigma = np.empty(max(g.n, 1), np.float64)
+    delta = np.empty(max(g.n, 1), np.float64)
+    col = g.col if len(g.col) else np.zeros(1, np.uint32)
+    _load().ora_bc(g.n, _p(g.off), _p(col), s, _p(level), _p(sigma), _p(delta))
+    return level[:g.n], sigma[:g.n], delta[:g.n]
 
 
 def tc(g: CSR) -> int:

@@ -194,6 +194,51 @@ void ora_pagerank(uint32_t n, const uint64_t* off, const uint32_t* col, double d
 }
 
 /*
+ * Single-source betweenness centrality from s (BC in the paper's table of
+ * algorithms, Section 6.2): delta[v] = sum over targets t != s, v of
+ * sigma_st(v) / sigma_st, where sigma_st counts the shortest s-t paths and
+ * sigma_st(v) those through v.  Computed by Brandes' accumulation (U. Brandes,
+ * "A faster algorithm for betweenness centrality", J. Math. Sociology 25(2),
+ * 2001): a FIFO BFS from s gives level[] and the path counts sigma[v] (sigma[s]
+ * = 1; every edge u-v with level[v] = level[u] + 1 adds sigma[u] to sigma[v]);
+ * then, over the vertices in reverse BFS order, every w adds
+ * sigma[v] / sigma[w] * (1 + delta[w]) to delta[v] for each neighbour v one
+ * level closer to s.  Reading: delta[s] = 0 (the source is not between any
+ * pair it ends); unreached vertices get level INF, sigma 0, delta 0.  FP64.
+ */
+void ora_bc(uint32_t n, const uint64_t* off, const uint32_t* col, uint32_t s, uint32_t* level, double* sigma,
+            double* delta) {
+  for (uint32_t v = 0; v < n; ++v) { level[v] = ORA_INF; sigma[v] = 0.0; delta[v] = 0.0; }
+  if (s >= n) return;
+  uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+  if (!order) return;
+  uint64_t head = 0, tail = 0;
+  order[tail++] = s;
+  level[s] = 0;
+  sigma[s] = 1.0;
+  while (head < tail) {
+    uint32_t u = order[head++];
+    for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = col[e];
+      if (level[v] == ORA_INF) {
+        level[v] = level[u] + 1;
+        order[tail++] = v;
+      }
+      if (level[v] == level[u] + 1) sigma[v] += sigma[u];
+    }
+  }
+  for (uint64_t i = tail; i-- > 0;) {
+    uint32_t w = order[i];
+    for (uint64_t e = off[w]; e < off[w + 1]; ++e) {
+      uint32_t v = col[e];
+      if (level[w] > 0 && level[v] == level[w] - 1) delta[v] += sigma[v] / sigma[w] * (1.0 + delta[w]);
+    }
+  }
+  delta[s] = 0.0;
+  free(order);
+}
+
+/*
  * Triangle count (Section 4.4: intersections of neighbour sets after a filter).
  * Plain definition: each triangle {u<v<w} is counted once, as the number of
  * w in N(u) and N(v) with w > v, over the pairs u<v that are edges; the lists

@@ -3,8 +3,10 @@
 The oracle is trusted only after it agrees with something other than itself:
 hand-derived fixtures (``tests/golden/``), closed forms (Manhattan distances on a
 grid, C(n,3) triangles in K_n, PageRank 1/n on regular graphs, the wheel and
-complete-bipartite counts), brute force on tiny inputs (Floyd-Warshall,
-transitive closure, the O(n^3) triangle loop, trace(A^3)/6), independent library
+complete-bipartite counts, binomial path counts and cycle/path/star
+dependencies for betweenness), brute force on tiny inputs (Floyd-Warshall,
+transitive closure, the O(n^3) triangle loop, trace(A^3)/6, betweenness from
+all-pairs path counts), independent library
 routines (scipy.sparse CSR construction, csgraph shortest paths and components,
 the Google-matrix power and eigenvector in numpy), invariants (sum of PageRank,
 relabelling, disjoint unions, insert-then-delete) and central finite
@@ -302,6 +304,104 @@ def test_tc_trace_a3():
     g = oracle.csr_build(n, src, dst)
     A = _dense(g)
     assert oracle.tc(g) * 6 == int(np.trace(A @ A @ A))
+
+
+# ----------------------------------------------------------------------------- betweenness
+
+def test_bc_path_star_complete():
+    # path from an end: one shortest path to each vertex, v lies on the paths to
+    # the n-1-v vertices beyond it
+    n = 9
+    level, sigma, delta = oracle.bc(oracle.csr_build(n, *_path(n)), 0)
+    assert list(level) == list(range(n)) and (sigma == 1).all()
+    assert list(delta) == [0] + [n - 1 - v for v in range(1, n)]
+    # from the middle of the path: each side on its own
+    level, sigma, delta = oracle.bc(oracle.csr_build(n, *_path(n)), 4)
+    assert list(delta) == [0, 1, 2, 3, 0, 3, 2, 1, 0]
+    # star, source a leaf: the centre is between the source and the n-2 other leaves
+    n = 12
+    g = oracle.csr_build(n, np.zeros(n - 1, np.uint32), np.arange(1, n, dtype=np.uint32))
+    level, sigma, delta = oracle.bc(g, 5)
+    assert (sigma[level != INF] == 1).all() and delta[0] == n - 2 and (np.delete(delta, 0) == 0).all()
+    # complete graph: every target is a neighbour of the source
+    level, sigma, delta = oracle.bc(oracle.csr_build(10, *_complete(10)), 3)
+    assert (delta == 0).all() and (sigma == 1).all()
+
+
+@pytest.mark.parametrize("k", [3, 5, 8])
+def test_bc_even_cycle_closed_form(k):
+    # cycle of 2k from 0: the antipode k has two shortest paths; the vertex at
+    # distance d < k on either side carries the k-1-d vertices beyond it and half
+    # of the antipode
+    n = 2 * k
+    src = np.arange(n, dtype=np.uint32)
+    level, sigma, delta = oracle.bc(oracle.csr_build(n, src, (src + 1) % n), 0)
+    assert sigma[k] == 2 and (np.delete(sigma, k) == 1).all()
+    for v in range(1, n):
+        d = min(v, n - v)
+        assert delta[v] == (0.0 if d == k else (k - 1 - d) + 0.5)
+
+
+@pytest.mark.parametrize("r,c", [(4, 6), (7, 5)])
+def test_bc_grid_path_counts_are_binomial(r, c):
+    # full grid from a corner: the shortest paths to (i, j) are the monotone
+    # lattice paths, C(i+j, i) of them
+    level, sigma, delta = oracle.bc(oracle.csr_build(r * c, *_grid_full(r, c)), 0)
+    for i in range(r):
+        for j in range(c):
+            assert level[i * c + j] == i + j and sigma[i * c + j] == math.comb(i + j, i)
+
+
+def _bfs_counts(A, s):
+    """Distances and shortest-path counts from s on a dense adjacency matrix."""
+    n = len(A)
+    dist = [-1] * n
+    cnt = [0] * n
+    dist[s], cnt[s] = 0, 1
+    frontier = [s]
+    while frontier:
+        nxt = []
+        for u in frontier:
+            for v in np.nonzero(A[u])[0]:
+                if dist[v] == -1:
+                    dist[v] = dist[u] + 1
+                    nxt.append(v)
+                if dist[v] == dist[u] + 1:
+                    cnt[v] += cnt[u]
+        frontier = nxt
+    return dist, cnt
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bc_brute_force_definition(seed):
+    # delta(v) = sum over t of sigma_st(v) / sigma_st with sigma_st(v) =
+    # sigma_sv * sigma_vt when v is on a shortest s-t path, from all-pairs
+    # path counts (exact rationals)
+    n = 40
+    g = oracle.csr_build(n, *_random_graph(n, 0.08, 300 + seed))
+    A = _dense(g)
+    s = seed % n
+    D, C = zip(*[_bfs_counts(A, v) for v in range(n)])
+    level, sigma, delta = oracle.bc(g, s)
+    for v in range(n):
+        want = Fraction(0)
+        if v != s and D[s][v] >= 0:
+            for t in range(n):
+                if t in (s, v) or D[s][t] < 0:
+                    continue
+                if D[s][v] + D[v][t] == D[s][t]:
+                    want += Fraction(C[s][v] * C[v][t], C[s][t])
+        assert sigma[v] == C[s][v]
+        assert abs(delta[v] - float(want)) <= 1e-12 * max(1.0, float(want))
+
+
+def test_bc_unreached_and_source():
+    # two components: the other one is unreached (level INF, sigma 0, delta 0)
+    src = np.array([0, 1, 3], np.uint32)
+    dst = np.array([1, 2, 4], np.uint32)
+    level, sigma, delta = oracle.bc(oracle.csr_build(5, src, dst), 0)
+    assert list(level[:3]) == [0, 1, 2] and level[3] == INF and level[4] == INF
+    assert list(sigma) == [1, 1, 1, 0, 0] and list(delta) == [0, 1, 0, 0, 0]
 
 
 # ----------------------------------------------------------------------------- PageRank
