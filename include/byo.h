@@ -244,7 +244,10 @@ byo_status byo_pagerank(const byo_graph* g, float damping, uint32_t iters, float
  * TMA bulk copies and hashed, or a bitmap of the ranks above a high-degree
  * vertex); out-lists of 32..16384 ids are sorted by rank first, so that a
  * walked out-list of a lower-ranked endpoint starts after the other endpoint.
- * *host_count receives the number of triangles; synchronises.
+ * *host_count receives the number of triangles; synchronises.  The
+ * environment variables BYO_TC_LIGHT_MAX, BYO_TC_WINDOW, BYO_TC_BITMAP_BITS,
+ * BYO_TC_WARP_SORT_MAX and BYO_TC_SORT_MAX can only lower internal limits (so
+ * that tests reach every code path on small graphs); the count is the same.
  * Errors: INVALID_ARG, OUT_OF_MEMORY, TIMEOUT, CUDA.
  */
 byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
