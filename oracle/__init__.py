@@ -2,8 +2,8 @@
 
 Python handle on ``byo_oracle.c``: a plain, serial CPU restatement of the BYO
 paper's definitions (CSR build, BFS, connected components, PageRank, triangle
-counting, single-source betweenness, batch updates of the edge set) plus the
-FP64 schedule network.  Only
+counting, single-source betweenness, byte-coded neighbour lists, batch updates
+of the edge set) plus the FP64 schedule network.  Only
 ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it; the CUDA library never does, and this module imports
 nothing from it.
@@ -43,6 +43,7 @@ _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _f64p = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def _load():
@@ -63,6 +64,10 @@ def _load():
                                      _f64p, _f64p]
         lib.ora_bc.restype = None
         lib.ora_bc.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_uint32, _u32p, _f64p, _f64p]
+        lib.ora_bytecode_encode.restype = ctypes.c_uint64
+        lib.ora_bytecode_encode.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u64p, _u8p, ctypes.c_uint64]
+        lib.ora_bytecode_decode.restype = None
+        lib.ora_bytecode_decode.argtypes = [ctypes.c_uint32, _u64p, _u64p, _u8p, _u32p]
         lib.ora_tc.restype = ctypes.c_uint64
         lib.ora_tc.argtypes = [ctypes.c_uint32, _u64p, _u32p]
         lib.ora_dyn_create.restype = ctypes.c_void_p
@@ -88,7 +93,8 @@ def _c(a, dtype):
 
 def _p(a):
     return a.ctypes.data_as({np.dtype(np.uint32): _u32p, np.dtype(np.uint64): _u64p,
-                             np.dtype(np.float64): _f64p, np.dtype(np.int32): _i32p}[a.dtype])
+                             np.dtype(np.float64): _f64p, np.dtype(np.int32): _i32p,
+                             np.dtype(np.uint8): _u8p}[a.dtype])
 
 
 class CSR:
@@ -157,6 +163,29 @@ def bc(g: CSR, s: int):
     col = g.col if len(g.col) else np.zeros(1, np.uint32)
     _load().ora_bc(g.n, _p(g.off), _p(col), s, _p(level), _p(sigma), _p(delta))
     return level[:g.n], sigma[:g.n], delta[:g.n]
+
+
+def bytecode_encode(g: CSR):
+    """Byte-coded neighbour lists: (boff uint64[n+1], bytes uint8[boff[n]])."""
+    boff = np.zeros(g.n + 1, np.uint64)
+    col = g.col if len(g.col) else np.zeros(1, np.uint32)
+    lib = _load()
+    size = int(lib.ora_bytecode_encode(g.n, _p(g.off), _p(col), _p(boff), None, 0))
+    if size == 2**64 - 1:  # sizing pass: no buffer
+        size = int(boff[g.n])
+    out = np.zeros(max(size, 1), np.uint8)
+    got = int(lib.ora_bytecode_encode(g.n, _p(g.off), _p(col), _p(boff), _p(out), len(out)))
+    assert got == size
+    return boff, out[:size]
+
+
+def bytecode_decode(n: int, off: np.ndarray, boff: np.ndarray, data: np.ndarray) -> CSR:
+    """Inverse of :func:`bytecode_encode`, given the CSR offsets (degrees)."""
+    off, boff = _c(off, np.uint64), _c(boff, np.uint64)
+    data = _c(data, np.uint8) if len(data) else np.zeros(1, np.uint8)
+    col = np.zeros(max(int(off[-1]), 1), np.uint32)
+    _load().ora_bytecode_decode(n, _p(off), _p(boff), _p(data), _p(col))
+    return CSR(n, off, col[:int(off[-1])].copy())
 
 
 def tc(g: CSR) -> int:

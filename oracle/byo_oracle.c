@@ -239,6 +239,70 @@ void ora_bc(uint32_t n, const uint64_t* off, const uint32_t* col, uint32_t s, ui
 }
 
 /*
+ * Compressed neighbour lists (the paper's compressed graphs, Section 2:
+ * difference encoding of each sorted list, the first entry relative to the
+ * source vertex, every difference stored as a byte code).  Reading of the
+ * layout, which the paper leaves to the cited byte-code work: a value is
+ * written in 7-bit groups, least significant first, every byte but the last
+ * of a value with the 0x80 bit set; the first difference u0 - v is signed and
+ * stored as 2|u0 - v| + (u0 < v); the later ones, u_i - u_(i-1) >= 1, as they
+ * are.  Degrees stay in the CSR offsets.  ora_bytecode_encode writes the start
+ * of every vertex's bytes to boff[0..n] and the bytes to out (capacity cap)
+ * and returns the total, or UINT64_MAX if cap is too small;
+ * ora_bytecode_decode writes the neighbour ids back into col (m entries, laid
+ * out by off).
+ */
+static uint64_t ora_put_code(uint64_t w, uint8_t* out, uint64_t at, uint64_t cap) {
+  do {
+    uint8_t b = (uint8_t)(w & 127u);
+    w >>= 7;
+    if (w) b |= 128u;
+    if (out && at < cap) out[at] = b;
+    ++at;
+  } while (w);
+  return at;
+}
+
+uint64_t ora_bytecode_encode(uint32_t n, const uint64_t* off, const uint32_t* col, uint64_t* boff, uint8_t* out,
+                             uint64_t cap) {
+  uint64_t at = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    boff[v] = at;
+    for (uint64_t e = off[v]; e < off[v + 1]; ++e) {
+      uint64_t w;
+      if (e == off[v]) {
+        w = col[e] >= v ? 2ull * (col[e] - v) : 2ull * (v - col[e]) + 1;
+      } else {
+        w = (uint64_t)col[e] - col[e - 1];
+      }
+      at = ora_put_code(w, out, at, cap);
+    }
+  }
+  boff[n] = at;
+  return at <= cap ? at : UINT64_MAX;
+}
+
+void ora_bytecode_decode(uint32_t n, const uint64_t* off, const uint64_t* boff, const uint8_t* in, uint32_t* col) {
+  for (uint32_t v = 0; v < n; ++v) {
+    uint64_t at = boff[v];
+    uint64_t prev = 0;
+    for (uint64_t e = off[v]; e < off[v + 1]; ++e) {
+      uint64_t w = 0;
+      int shift = 0;
+      uint8_t b;
+      do {
+        b = in[at++];
+        w |= (uint64_t)(b & 127u) << shift;
+        shift += 7;
+      } while (b & 128u);
+      if (e == off[v]) prev = (w & 1) ? (uint64_t)v - (w >> 1) : (uint64_t)v + (w >> 1);
+      else prev += w;
+      col[e] = (uint32_t)prev;
+    }
+  }
+}
+
+/*
  * Triangle count (Section 4.4: intersections of neighbour sets after a filter).
  * Plain definition: each triangle {u<v<w} is counted once, as the number of
  * w in N(u) and N(v) with w > v, over the pairs u<v that are edges; the lists
