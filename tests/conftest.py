@@ -15,7 +15,8 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests are skipped (not failed) when no GPU is visible, so that a plain
-    # `pytest` here runs the CPU suite; `-m gpu` on a GPU machine runs them.
+    # `pytest` on a machine without one runs the CPU suite; `-m gpu` on a
+    # machine with a GB300 runs them.
     try:
         import torch
         has_gpu = torch.cuda.is_available()
