@@ -16,7 +16,14 @@ pair arrays, CSR build, the four algorithms, device -> host copy of levels,
 labels and ranks -- as a streaming pipeline in which step i+1's input copy
 overlaps step i and step i's output copy overlaps its triangle count.
 
+After the timed region the line also carries the BFS schedules side by side
+(learned, heuristic, push, pull; median of repeated 8-source runs) on this
+graph and on the high-diameter grid, and the bandwidth of the largest push and
+pull levels.  Byte counts are the method's (what the algorithm must move, from
+its outputs), never a kernel's own counters.
+
   python bench.py [--gpus N --steps K --warmup W --workload rmat25 --sources 8]
+  python bench.py --workload batched | dynamic
   python bench.py --impl reference ...   # the serial CPU oracle, bounded sample
 
 N > 1 (torchrun, one rank per GPU) runs independent replicas: the path does not
@@ -39,6 +46,8 @@ sys.path.insert(0, ROOT)
 METRIC = "GTEPS & % HBM roofline (BFS/PR/CC/TC, RMAT-25); learned vs heuristic schedule"
 PR_ITERS = 20
 DAMPING = 0.85
+INF = 0xFFFFFFFF
+SCHEDULES = ("learned", "heuristic", "push", "pull")
 
 
 def parse():
@@ -53,7 +62,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--schedules", action="store_true", help="also time BFS under every schedule")
+    ap.add_argument("--no-schedules", action="store_true", help="skip the schedule comparison")
+    ap.add_argument("--sched-reps", type=int, default=5, help="timed repetitions per schedule")
     ap.add_argument("--sample-scale", type=int, default=18, help="RMAT scale of the oracle's bounded sample")
     return ap.parse_args()
 
@@ -134,6 +144,11 @@ def dev_u32(torch, a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
 
 
+def pinned_u32(torch, a):
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).pin_memory()
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -141,22 +156,6 @@ def measured_peaks():
             d = json.load(f)
         return float(d.get("hbm_gbs", 6800.0)), "measured"
     return 6800.0, "fallback"
-
-
-def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes (read + write) per launch from the committed ncu summary
-    profiles/traffic.md (a table | workload | kernel | bytes | ... |), if it has
-    a row for this kernel and workload; None otherwise."""
-    p = os.path.join(ROOT, "profiles", "traffic.md")
-    try:
-        with open(p) as f:
-            for line in f:
-                cells = [c.strip() for c in line.strip().strip("|").split("|")]
-                if len(cells) >= 3 and cells[0] == workload and cells[1] == kernel:
-                    return float(cells[2].replace(",", ""))
-    except (OSError, ValueError):
-        return None
-    return None
 
 
 def sched_struct(byo, name, mlp=None):
@@ -179,24 +178,24 @@ def load_mlp(byo):
     return m
 
 
+def roof_entry(name, bytes_, avg_ms, peak, peak_kind, share=None):
+    achieved = bytes_ / (avg_ms / 1e3) / 1e9
+    e = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+         "frac": round(achieved / peak, 4), "traffic": None, "algorithmic_bytes_per_launch": bytes_,
+         "avg_launch_ms": round(avg_ms, 4), "peak_kind": peak_kind}
+    if share is not None:
+        e["share"] = round(share, 4)
+    return e
+
+
 # ----------------------------------------------------------------------------- algorithmic bytes
 
-def algo_bytes(kernel: str, n: int, m: int, off: int, trace=None) -> float | None:
+def algo_bytes(kernel: str, n: int, m: int, off: int) -> float | None:
     """Bytes the method must move per launch of `kernel` (a model, not a counter)."""
     if kernel == "pr_iter":
         # offsets of the degree-ordered copy (always 8 bytes) + neighbour ids + one
         # read of every contribution + read/write rank + write next contribution
         return 8.0 * (n + 1) + 4.0 * m + 16.0 * n
-    if kernel == "bfs_persistent" and trace is not None:
-        b = 8.0 * n + n / 8.0  # level + parent init, visited bits
-        for r in trace:
-            if r.direction == 1:   # push: offsets and ids of F, queue in/out, level/parent/bits of F'
-                b += 2 * off * r.frontier + 4.0 * r.edges_examined + 4.0 * r.frontier
-            else:                  # pull: offsets of the unvisited, ids scanned, 3 bit arrays
-                b += 2 * off * r.unvisited + 4.0 * r.edges_examined + 3 * n / 8.0
-        nxt = [r.frontier for r in trace[1:]] + [0]
-        b += 12.0 * sum(nxt)
-        return b
     if kernel == "cc_sample":
         # identity labels, two sampling rounds (offsets, one neighbour id and the
         # two endpoints' labels each), one flattening pass (read + write)
@@ -208,7 +207,163 @@ def algo_bytes(kernel: str, n: int, m: int, off: int, trace=None) -> float | Non
     return None
 
 
-# ----------------------------------------------------------------------------- oracle sample
+def _vertex_chunks(torch, off, chunk_edges):
+    """Vertex ranges [v0, v1) holding about chunk_edges neighbour entries each."""
+    n = off.numel() - 1
+    v0 = 0
+    while v0 < n:
+        target = torch.tensor([int(off[v0]) + chunk_edges], dtype=off.dtype, device=off.device)
+        v1 = int(torch.searchsorted(off, target, right=True)[0]) - 1
+        v1 = min(n, max(v1, v0 + 1))
+        yield v0, v1
+        v0 = v1
+
+
+def first_hit_positions(torch, off, col, want_level, lvl, chunk_edges=1 << 26):
+    """fp[v] = index, within N(v) in stored (ascending) order, of the first
+    neighbour u with lvl[u] == want_level[v]; -1 where there is none or
+    want_level[v] is negative.  lvl and want_level are int64."""
+    n = off.numel() - 1
+    fp = torch.full((n,), -1, dtype=torch.long, device=lvl.device)
+    deg = off[1:] - off[:-1]
+    for v0, v1 in _vertex_chunks(torch, off, chunk_edges):
+        e0, e1 = int(off[v0]), int(off[v1])
+        if e1 == e0:
+            continue
+        rows = torch.repeat_interleave(torch.arange(v0, v1, device=lvl.device), deg[v0:v1])
+        nb = col[e0:e1].long() & INF
+        w = want_level[rows]
+        hit = (w >= 0) & (lvl[nb] == w)
+        pos = torch.arange(e0, e1, device=lvl.device) - off[rows]
+        fp.scatter_reduce_(0, rows[hit], pos[hit], reduce="amin", include_self=False)
+    return fp
+
+
+def bfs_method_bytes(torch, off, col, lv, trace, off_bytes: int):
+    """Bytes one BFS traversal must move, level by level, by the method's
+    definition (from its output levels, not from kernel counters):
+      push level: sum over u in F of (offset + 4 deg u) + 4|F| (queue) + 12|F'|
+                  (queue, level, parent of the next frontier) + n/8 (visited bits)
+      pull level: sum over unvisited v of (offset + 4 scanned(v)) + 3n/8 (frontier,
+                  visited and next bit arrays) + 8|F'|, where scanned(v) counts
+                  v's neighbours in ascending order up to and including the first
+                  one in the frontier (all of them when none is)
+      plus 8n + n/8 to initialise levels, parents and visited bits.
+    The direction of each level is the one the traversal took (trace).
+    Returns (total bytes, [(level, direction, bytes, t_ns), ...])."""
+    n = lv.numel()
+    m = int(off[-1])
+    L = lv.long() & INF
+    reached = L != INF
+    deg = (off[1:] - off[:-1]).long()
+    # the first neighbour one level closer, for every reached vertex but the source
+    want = torch.where(reached & (L > 0), L - 1, torch.full_like(L, -1))
+    fp = first_hit_positions(torch, off, col, want, L)
+    Lr = L[reached]
+    top = int(Lr.max()) if Lr.numel() else 0
+    cnt = torch.bincount(Lr, minlength=top + 2).double()
+    degL = torch.bincount(Lr, weights=deg[reached].double(), minlength=top + 2)
+    sel = reached & (L > 0)
+    fpL = torch.bincount(L[sel], weights=(fp[sel] + 1).double(), minlength=top + 2)
+    cum_cnt = torch.cumsum(cnt, 0)
+    cum_deg = torch.cumsum(degL, 0)
+    cnt, degL, fpL, cum_cnt, cum_deg = (x.cpu().tolist() for x in (cnt, degL, fpL, cum_cnt, cum_deg))
+    out = []
+    total = 8.0 * n + n / 8.0
+    for r in trace:
+        lvl_ = int(r.level)
+        F = cnt[lvl_] if lvl_ < len(cnt) else 0.0
+        Fn = cnt[lvl_ + 1] if lvl_ + 1 < len(cnt) else 0.0
+        if r.direction == 1:
+            b = off_bytes * F + 4.0 * degL[lvl_] + 4.0 * F + 12.0 * Fn + n / 8.0
+        else:
+            unvis = n - cum_cnt[lvl_]
+            deg_beyond = m - (cum_deg[lvl_ + 1] if lvl_ + 1 < len(cum_deg) else cum_deg[-1])
+            scanned = (fpL[lvl_ + 1] if lvl_ + 1 < len(fpL) else 0.0) + deg_beyond
+            b = off_bytes * unvis + 4.0 * scanned + 3.0 * n / 8.0 + 8.0 * Fn
+        total += b
+        out.append((lvl_, int(r.direction), b, int(r.t_ns)))
+    return total, out
+
+
+def level_bandwidth(levels, peak):
+    """Bandwidth of the push and pull levels: the largest level of each
+    direction (by bytes) and each direction's total bytes over total time."""
+    res = {}
+    for d, name in ((1, "push"), (0, "pull")):
+        lv = [x for x in levels if x[1] == d and x[3] > 0]
+        if not lv:
+            continue
+        big = max(lv, key=lambda x: x[2])
+        tb, tt = sum(x[2] for x in lv), sum(x[3] for x in lv)
+        res[name] = {"largest_level": big[0], "largest_bytes": big[2], "largest_us": round(big[3] / 1e3, 2),
+                     "largest_gbs": round(big[2] / big[3], 1), "largest_frac": round(big[2] / big[3] / peak, 4),
+                     "levels": len(lv), "total_bytes": tb, "total_us": round(tt / 1e3, 1),
+                     "total_gbs": round(tb / tt, 1), "total_frac": round(tb / tt / peak, 4)}
+    return res
+
+
+def msbfs_method_bytes(torch, off, col, lv, alpha: float, S: int, off_bytes: int = 4):
+    """Bytes the 64-source BFS must move (one launch), from its output levels
+    lv[S, n].  Per level: top-down reads the frontier words (8n) and, for each
+    vertex whose word is non-empty, its offsets, its neighbour ids and their
+    seen words (off + 12 per neighbour); bottom-up reads the seen words (8n)
+    and, for each vertex with sources still unseen, neighbours in order until
+    every missing source is found (all of them when some source cannot reach
+    it), 12 bytes each; every level then rewrites the three words (24n) and
+    writes 4 bytes per newly reached (vertex, source) pair.  The direction of
+    each level follows the launch's own rule (top-down while the frontier's
+    edges x alpha < the edges of vertices never in a frontier), applied to the
+    same counts.  Plus 24n + 4Sn to initialise."""
+    n = lv.shape[1]
+    m = int(off[-1])
+    L = lv.long() & INF
+    deg = (off[1:] - off[:-1]).long()
+    big = 1 << 40
+    Lx = torch.where(L == INF, torch.full_like(L, big), L)
+    first = Lx.min(0).values           # first level any source reaches v
+    last = Lx.max(0).values            # level by which every source has reached v
+    top = int(Lx[Lx < big].max()) if (Lx < big).any() else 0   # the deepest (vertex, source) level
+    # union frontier per level: v is in it at level l iff some source reaches v at l
+    counts = torch.zeros(top + 2, dtype=torch.float64, device=L.device)
+    degsum = torch.zeros(top + 2, dtype=torch.float64, device=L.device)
+    pairs = torch.zeros(top + 2, dtype=torch.float64, device=L.device)
+    for j in range(S):
+        r = L[j] != INF
+        pairs += torch.bincount(L[j][r], minlength=top + 2).double()[:top + 2]
+    for lvl_ in range(top + 1):
+        inF = (L == lvl_).any(0)
+        counts[lvl_] = inF.sum()
+        degsum[lvl_] = deg[inF].sum()
+    # bottom-up scan length at the level before `last`: first neighbour of each
+    # source whose level at v is `last`, the latest of them
+    fpmax = torch.full((n,), -1, dtype=torch.long, device=L.device)
+    for j in range(S):
+        want = torch.where((Lx[j] == last) & (last < big) & (last > 0), last - 1, torch.full_like(last, -1))
+        fp = first_hit_positions(torch, off, col, want, L[j])
+        fpmax = torch.maximum(fpmax, fp)
+    counts, degsum, pairs = (x.cpu().tolist() for x in (counts, degsum, pairs))
+    total = 24.0 * n + 4.0 * S * n
+    mseen = 0.0
+    for lvl_ in range(top + 1):
+        nf, mf = counts[lvl_], degsum[lvl_]
+        if nf == 0:
+            break
+        mseen += mf
+        top_down = mf * alpha < max(m - mseen, 0) or lvl_ == 0
+        if top_down:
+            b = 8.0 * n + off_bytes * nf + 12.0 * mf
+        else:
+            pend = last > lvl_
+            exact = pend & (last == lvl_ + 1)
+            whole = pend & (last > lvl_ + 1)
+            b = (8.0 * n + off_bytes * float(pend.sum()) + 12.0 * float((fpmax[exact] + 1).sum())
+                 + 12.0 * float(deg[whole].sum()))
+        total += b + 24.0 * n + 4.0 * (pairs[lvl_ + 1] if lvl_ + 1 < len(pairs) else 0.0)
+    return total
+
+
+# ----------------------------------------------------------------------------- oracle samples
 
 def cpu_baseline(sample_scale: int, sources: int):
     """The serial oracle on a bounded sample of the same workload family."""
@@ -234,6 +389,44 @@ def cpu_baseline(sample_scale: int, sources: int):
             "sample": f"RMAT scale {sample_scale} ef16 (same a,b,c,d, ids permuted), {len(srcs)} BFS sources + "
                       f"CC + PR20 + TC, serial oracle, {dt:.2f} s",
             "seconds": dt, "host": platform.machine()}
+
+
+def cpu_baseline_batched(members, stride: int = 32):
+    """The oracle on every `stride`-th member of the batch: 64 BFS + CC each."""
+    import numpy as np
+
+    import oracle
+    picked = members[::stride]
+    t0 = time.perf_counter()
+    edges = 0
+    for n, s, d, srcs in picked:
+        g = oracle.csr_build(n, s, d)
+        deg = np.diff(g.off).astype(np.int64)
+        for x in srcs:
+            lv, _ = oracle.bfs(g, int(x))
+            edges += int(deg[lv != oracle.INF].sum()) // 2
+        oracle.cc(g)
+        edges += g.m // 2
+    dt = time.perf_counter() - t0
+    return {"value": edges / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"members 0, {stride}, {2 * stride}, ... ({len(picked)} of {len(members)}): 64 BFS + CC each, "
+                      f"serial oracle (CSR build untimed), {dt:.2f} s"}
+
+
+def cpu_baseline_dynamic(scale: int = 16, rounds: int = 3, batch: int = 16384):
+    """The oracle's edge set under the same kind of rounds on a smaller base."""
+    import graphgen
+    import oracle
+    n, src, dst = graphgen.rmat_small(scale, 16, graphgen.SEEDS["rmat24"])
+    dg = oracle.DynGraph(n, src, dst)
+    t0 = time.perf_counter()
+    for ins_s, ins_d, del_s, del_d in graphgen.dynamic_rounds(n, src, dst, rounds, batch, scale=scale):
+        dg.insert(ins_s, ins_d)
+        dg.delete(del_s, del_d)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * rounds * batch / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"RMAT-{scale} base, {rounds} rounds x ({batch} inserts + {batch} deletes), serial oracle, "
+                      f"{dt:.2f} s"}
 
 
 def run_reference(args):
@@ -262,6 +455,53 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- schedules
+
+def schedule_table(byo, torch, g, srcs, levels, parents, reps: int, stream):
+    """Median device time of the S-source BFS under each schedule."""
+    out = {}
+    for name in SCHEDULES:
+        mm = load_mlp(byo) if name == "learned" else None
+        if name == "learned" and mm is None:
+            continue
+        spx = sched_struct(byo, name, mm)
+        byo.byo_bfs(g, srcs, levels, parents, spx)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            byo.byo_bfs(g, srcs, levels, parents, spx)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        out[name] = {"median_ms": round(statistics.median(times), 4), "min_ms": round(min(times), 4), "runs": reps}
+        if mm:
+            byo.byo_mlp_destroy(mm)
+    if "learned" in out:
+        out["heuristic_over_learned"] = round(out["heuristic"]["median_ms"] / out["learned"]["median_ms"], 4)
+    return out
+
+
+def grid_schedules(byo, torch, reps: int, stream):
+    """The schedules on the high-diameter grid (4096 x 4096, 10 % dropped,
+    0.01 % shortcuts): the corner vertex plus seven seeded sources."""
+    import graphgen
+    n, src, dst = graphgen.workload("grid")
+    picked = [int(x) for x in graphgen.pick_sources(n, src, dst, 8, graphgen.SEEDS["grid"] + 1) if int(x) != 0]
+    srcs = [0] + picked[:7]
+    g = byo.Graph(n, dev_u32(torch, src), dev_u32(torch, dst), byo.BYO_CSR | byo.BYO_SYMMETRIZE)
+    lv = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+    par = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+    try:
+        tab = schedule_table(byo, torch, g.handle, srcs, lv, par, reps, stream)
+        corner = schedule_table(byo, torch, g.handle, [0], lv[:1], par[:1], reps, stream)
+    finally:
+        g.close()
+    return {"workload": "grid 4096x4096, 10% dropped, 0.01% shortcuts", "sources": srcs, "all_sources": tab,
+            "corner_only": corner}
+
+
 # ----------------------------------------------------------------------------- batched workload
 
 def run_batched(args, byo, torch):
@@ -272,18 +512,11 @@ def run_batched(args, byo, torch):
 
     import graphgen
     from paper_2405_11671_gb300 import autotune
-    params = graphgen.batched_params(256)
-    ns, ks, srcs_l, dsts_l, sources = [], [], [], [], []
-    for kind, n, k, sd in params:
-        s, d = graphgen.batched_member(kind, n, k, sd)
-        ns.append(n)
-        ks.append(k)
-        srcs_l.append(s)
-        dsts_l.append(d)
-        picked = graphgen.pick_sources(n, s, d, 64, sd + 1).tolist()
-        picked += [v % n for v in range(64 - len(picked))]
-        sources.append(picked[:64])
-    src, dst = np.concatenate(srcs_l), np.concatenate(dsts_l)
+    members = graphgen.batched_workload(256, 64)
+    ns = [mb[0] for mb in members]
+    ks = [len(mb[1]) for mb in members]
+    sources = [mb[3] for mb in members]
+    src, dst = np.concatenate([mb[1] for mb in members]), np.concatenate([mb[2] for mb in members])
     g = byo.byo_batch_build(ns, ks, dev_u32(torch, src), dev_u32(torch, dst))
     N, m = byo.byo_num_vertices(g), byo.byo_num_edges(g)
     levels = torch.empty((64, N), dtype=torch.int32, device="cuda")
@@ -318,69 +551,133 @@ def run_batched(args, byo, torch):
     deg = byo.byo_degree(g).to(torch.int64)
     ms_edges = int(((levels != -1).to(torch.int64) * deg.unsqueeze(0)).sum().item()) // 2
     edges = {"msbfs": ms_edges, "cc": m // 2}
+    step_edges = sum(edges.values())
     tot = sum(v[1] for v in prof.values()) or 1.0
-    line = {"metric": METRIC, "value": round(sum(edges.values()) / (ms / 1e3) / 1e9, 3), "unit": "GTEPS",
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if "msbfs_persistent" in prof:
+        nl, kms = prof["msbfs_persistent"]
+        off, col = byo.byo_graph_export_csr(g)
+        mb = msbfs_method_bytes(torch, off, col, levels, tuned["alpha"], 64, 8 if m >= 2 ** 32 else 4)
+        del off, col
+        roof = roof_entry("msbfs_persistent", mb, kms / nl, peak, peak_kind, kms / tot)
+
+    # end to end: pinned host pairs in, batch built, both algorithms, levels and labels out
+    e2e = None
+    if not args.no_e2e:
+        src_h, dst_h = pinned_u32(torch, src), pinned_u32(torch, dst)
+        lv_h = torch.empty((64, N), dtype=torch.int32).pin_memory()
+        lab_h = torch.empty(N, dtype=torch.int32).pin_memory()
+        byo.byo_graph_destroy(g)
+        g = None
+        torch.cuda.synchronize()
+        steps = max(1, args.e2e_steps)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            s_d, d_d = src_h.cuda(non_blocking=True), dst_h.cuda(non_blocking=True)
+            ge = byo.byo_batch_build(ns, ks, s_d, d_d)
+            byo.byo_msbfs(ge, sources, 64, levels, sched=sp)
+            byo.byo_cc(ge, labels)
+            lv_h.copy_(levels, non_blocking=True)
+            lab_h.copy_(labels, non_blocking=True)
+            torch.cuda.synchronize()
+            byo.byo_graph_destroy(ge)
+            del s_d, d_d
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / steps
+        e2e = {"value": round(step_edges / (e2e_ms / 1e3) / 1e9, 3), "unit": "GTEPS", "ms_per_step": round(e2e_ms, 3),
+               "h2d_bytes_per_step": int(8 * len(src)), "d2h_bytes_per_step": int(4 * (lv_h.numel() + lab_h.numel()))}
+    cb = None if args.no_cpu_baseline else cpu_baseline_batched(members)
+    line = {"metric": METRIC, "value": round(step_edges / (ms / 1e3) / 1e9, 3), "unit": "GTEPS",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
             "config": {"workload": "batched256", "graphs": 256, "n": N, "m": m, "sources_per_graph": 64,
-                       "msbfs_alpha": tuned["alpha"], "autotune_ms": tuned["table_ms"]},
-            "edges_per_step": edges,
+                       "msbfs_alpha": tuned["alpha"], "autotune_ms": tuned["table_ms"],
+                       "l2": "inputs larger than L2 (1.8 GB of neighbour ids)"},
+            "edges_per_step": edges, "roofline": roof,
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot, 4)}
                         for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
-            "gpu_launches": int(launches), "clocks": clk}
+            "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cb}
     print(json.dumps(line), flush=True)
-    byo.byo_graph_destroy(g)
+    if g is not None:
+        byo.byo_graph_destroy(g)
 
 
 # ----------------------------------------------------------------------------- dynamic workload
 
+def update_method_bytes(torch, ins_s, ins_d, deg_before, deg_after, lb: int):
+    """Bytes a batch update must move: the batch sorted in both directions
+    (8-byte keys read and written once per 8-bit radix pass over 2 lb key
+    bits) and, for every vertex the batch touches, its old list read, its new
+    list written and its 64-byte record rewritten."""
+    k = len(ins_s)
+    passes = (2 * lb + 7) // 8
+    sort_b = 2.0 * k * 8 * 2 * passes
+    touched = torch.unique(torch.cat([dev_u32(torch, ins_s), dev_u32(torch, ins_d)]).long())
+    merge_b = float(4 * (deg_before[touched] + deg_after[touched]).sum()) + 64.0 * touched.numel()
+    return sort_b + merge_b
+
+
 def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
     """RMAT-24 (ef 16) in the dynamic container, then `rounds` rounds of one
-    insert batch of RMAT pairs and one delete batch of uniformly drawn earlier
-    pairs, each followed by BFS (one source) + CC + PageRank.  Reported: batch
-    update throughput (pairs/s, before symmetrisation), the algorithms' time on
-    the dynamic container, and a full GPU CSR rebuild of the same edge set."""
-    import numpy as np
-
+    insert batch of RMAT pairs and one delete batch of earlier pairs
+    (graphgen.dynamic_rounds), each followed by BFS (one source) + CC +
+    PageRank.  Reported: batch update throughput (pairs/s, before
+    symmetrisation), the algorithms' time on the dynamic container, and a full
+    GPU CSR rebuild of the same edge set."""
     import graphgen
     seed = graphgen.SEEDS["rmat24"]
     n, src, dst = graphgen.workload("rmat24")
     g = byo.Graph(n, dev_u32(torch, src), dev_u32(torch, dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
-    pool_s, pool_d = [src], [dst]
     s0 = int(graphgen.pick_sources(n, src, dst, 1, seed + 1)[0])
     levels = torch.empty((1, n), dtype=torch.int32, device="cuda")
     labels = torch.empty(n, dtype=torch.int32, device="cuda")
     ranks = torch.empty(n, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    ins_ms, del_ms, alg_ms, csr_alg_ms, rebuild_ms = [], [], [], [], []
-    for r in range(rounds):
-        ins_s, ins_d = graphgen.rmat(24, batch, graphgen.stream(seed, 100 + r))
-        ps, pd = np.concatenate(pool_s), np.concatenate(pool_d)
-        pick = graphgen.pick_indices(len(ps), batch, graphgen.stream(seed, 200 + r))
-        del_s, del_d = ps[pick], pd[pick]
-        di, dd_ = dev_u32(torch, ins_s), dev_u32(torch, ins_d)
-        ds, dd = dev_u32(torch, del_s), dev_u32(torch, del_d)
+    ins_ms, del_ms, alg_ms, csr_alg_ms, rebuild_ms, e2e_ms, ins_bytes = [], [], [], [], [], [], []
+    lv_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    rk_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    lb = max(1, (n - 1).bit_length())
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = byo.byo_kernel_launches()
+    for r, (ins_s, ins_d, del_s, del_d) in enumerate(graphgen.dynamic_rounds(n, src, dst, rounds, batch)):
+        # end to end through the C ABI: the round's pairs from pinned host
+        # memory, the two updates, the three algorithms, their outputs back
+        hs = [pinned_u32(torch, x) for x in (ins_s, ins_d, del_s, del_d)]
+        deg_before = byo.byo_degree(g.handle).long()
         torch.cuda.synchronize()
-        a, b, c = ev(), ev(), ev()
+        a, b, c, c2, d = ev(), ev(), ev(), ev(), ev()
         a.record(stream)
-        byo.byo_insert_batch(g.handle, di, dd_)
+        di, dd_, ds, dd = (x.cuda(non_blocking=True) for x in hs)
         b.record(stream)
-        byo.byo_delete_batch(g.handle, ds, dd)
+        byo.byo_insert_batch(g.handle, di, dd_)
         c.record(stream)
-        torch.cuda.synchronize()
-        ins_ms.append(a.elapsed_time(b))
-        del_ms.append(b.elapsed_time(c))
-        pool_s.append(ins_s)
-        pool_d.append(ins_d)
-        a, b = ev(), ev()
-        a.record(stream)
+        deg_mid = byo.byo_degree(g.handle).long()  # for the byte model only, outside both update timings
+        c2.record(stream)
+        byo.byo_delete_batch(g.handle, ds, dd)
+        d.record(stream)
+        x0, x1 = ev(), ev()
+        x0.record(stream)
         byo.byo_bfs(g.handle, [s0], levels, None, None, want_parents=False)
         byo.byo_cc(g.handle, labels)
         byo.byo_pagerank(g.handle, DAMPING, PR_ITERS, ranks, want_residual=False)
-        b.record(stream)
+        x1.record(stream)
+        lv_h.copy_(levels[0], non_blocking=True)
+        lab_h.copy_(labels, non_blocking=True)
+        rk_h.copy_(ranks, non_blocking=True)
+        e = ev()
+        e.record(stream)
         torch.cuda.synchronize()
-        alg_ms.append(a.elapsed_time(b))
+        ins_ms.append(b.elapsed_time(c))
+        del_ms.append(c2.elapsed_time(d))
+        alg_ms.append(x0.elapsed_time(x1))
+        e2e_ms.append(a.elapsed_time(e) - c.elapsed_time(c2))
+        ins_bytes.append(update_method_bytes(torch, ins_s, ins_d, deg_before, deg_mid, lb))
         # the same edge set rebuilt as a static CSR, and the same algorithms on it
         off, col = byo.byo_graph_export_csr(g.handle)
         rows = torch.repeat_interleave(torch.arange(n, device="cuda", dtype=torch.int32), off.diff())
@@ -400,16 +697,32 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
         csr_alg_ms.append(a.elapsed_time(b))
         gc.close()
         del rows, off, col
+    launches = byo.byo_kernel_launches() - l0
+    clk = clocks.stop()
     med = statistics.median
-    line = {"metric": "dynamic container: batch updates/s and algorithm time vs CSR", "workload": "rmat24-dynamic",
-            "n": n, "m_final": g.m, "rounds": rounds, "batch_pairs": batch,
+    peak, peak_kind = measured_peaks()
+    round_ms = [i + d + x for i, d, x in zip(ins_ms, del_ms, alg_ms)]
+    line = {"metric": "dynamic container: batch updates/s and algorithm time vs CSR", "value":
+            round(2 * batch / (med([i + d for i, d in zip(ins_ms, del_ms)]) / 1e3), 1), "unit": "pairs/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": rounds, "warmup": 0,
+            "ms_per_step": round(med(round_ms), 3), "dtype": "u32+f32", "data": "synthetic", "scaling": "weak",
+            "vs_baseline": None,
+            "config": {"workload": "rmat24-dynamic", "n": n, "m_final": g.m, "rounds": rounds, "batch_pairs": batch,
+                       "l2": "inputs larger than L2 (2.1 GB of neighbour ids)"},
             "insert_ms_median": round(med(ins_ms), 3), "delete_ms_median": round(med(del_ms), 3),
             "insert_pairs_per_s": round(batch / (med(ins_ms) / 1e3), 1),
             "delete_pairs_per_s": round(batch / (med(del_ms) / 1e3), 1),
             "bfs_cc_pr_ms_dynamic": round(med(alg_ms), 3), "bfs_cc_pr_ms_csr": round(med(csr_alg_ms), 3),
             "dynamic_over_csr": round(med(alg_ms) / med(csr_alg_ms), 3),
             "csr_rebuild_ms_median": round(med(rebuild_ms), 3),
-            "update_round_vs_rebuild": round((med(ins_ms) + med(del_ms)) / med(rebuild_ms), 3)}
+            "update_round_vs_rebuild": round((med(ins_ms) + med(del_ms)) / med(rebuild_ms), 3),
+            "roofline": roof_entry("dyn_insert", med(ins_bytes), med(ins_ms), peak, peak_kind),
+            "e2e": {"value": round(2 * batch / (med(e2e_ms) / 1e3), 1), "unit": "pairs/s",
+                    "ms_per_step": round(med(e2e_ms), 3), "h2d_bytes_per_step": 16 * batch,
+                    "d2h_bytes_per_step": 12 * n,
+                    "note": "pairs in, both updates, BFS + CC + PageRank, their outputs out"},
+            "gpu_launches": int(launches), "clocks": clk,
+            "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_dynamic()}
     print(json.dumps(line), flush=True)
     g.close()
 
@@ -455,9 +768,6 @@ def main():
     def barrier():
         if dist:
             dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        return reduce_over_ranks(dist, x, "max", "cuda")
 
     # ---- inputs (seeded, synthetic; replicas use the same graph)
     n, src, dst = graphgen.workload(args.workload)
@@ -541,13 +851,20 @@ def main():
     per_algo = {a: {"ms": round(algo_ms[a], 4), "gteps": round(edges[a] / (algo_ms[a] / 1e3) / 1e9, 3)}
                 for a in algos}
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel (method bytes / CUDA-event time)
     peak, peak_kind = measured_peaks()
-    bfs_bytes = []
+    off_d, col_d = byo.byo_graph_export_csr(g.handle)
+    bfs_bytes, bfs_lv = [], []
+    examined = [0.0, 0.0]
     for s_ in srcs:  # one trace per source: the BFS launch processes one source
         byo.byo_bfs(g.handle, [int(s_)], levels[:1], parents[:1], sp)
-        bfs_bytes.append(algo_bytes("bfs_persistent", n, m, off_bytes, byo.byo_bfs_trace(g.handle)))
-    trace = byo.byo_bfs_trace(g.handle)
+        tr = byo.byo_bfs_trace(g.handle)
+        b, per_level = bfs_method_bytes(torch, off_d, col_d, levels[0], tr, off_bytes)
+        bfs_bytes.append(b)
+        bfs_lv += per_level
+        examined[0] += sum(4.0 * r.edges_examined for r in tr)
+        examined[1] += sum(x[2] for x in per_level)
+    del off_d, col_d
     tot = sum(v[1] for v in prof.values()) or 1.0
     # the two intersection kernels of one triangle count are one unit of work
     merged = dict(prof)
@@ -573,57 +890,37 @@ def main():
             b = algo_bytes(name, n, m, off_bytes)
         if b is None or nl == 0:
             continue
-        avg_ms = ms / nl
-        achieved = b / (avg_ms / 1e3) / 1e9
-        entry = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                 "frac": round(achieved / peak, 4), "traffic": ncu_traffic(name, args.workload),
-                 "algorithmic_bytes_per_launch": b, "avg_launch_ms": round(avg_ms, 4),
-                 "share": round(ms / tot, 4), "peak_kind": peak_kind}
+        entry = roof_entry(name, b, ms / nl, peak, peak_kind, ms / tot)
         if name == "tc_count":
             merge_b = 4.0 * (tc_work[0] + tc_work[1])
             entry["tc_ids_walked"] = tc_work[2]
             entry["merge_model_bytes"] = merge_b
-            entry["merge_model_frac"] = round(merge_b / (avg_ms / 1e3) / 1e9 / peak, 4)
+            entry["merge_model_frac"] = round(merge_b / (ms / nl / 1e3) / 1e9 / peak, 4)
             entry["note"] = ("bytes = shorter out-list of each DAG edge + partner ids and bounds + centre lists "
                              "(the walk-shorter/probe-set method, in-neighbour walks trimmed to the ids above the "
-                             "centre; issue bound at RMAT-22 where L2 serves most walks, walks from DRAM at RMAT-25). "
-                             "merge_model_* = both out-lists of every "
-                             "DAG edge (a sorted merge's reads)")
+                             "centre). merge_model_* = both out-lists of every DAG edge (a sorted merge's reads)")
+        if name == "bfs_persistent":
+            entry["ids_read_by_kernel_over_method"] = round(examined[0] / max(examined[1], 1.0), 4)
         if roof is None:
             roof = entry
         else:
             rooflines[name] = {k: entry[k] for k in ("achieved", "frac", "avg_launch_ms", "algorithmic_bytes_per_launch",
-                                                     "traffic")}
+                                                     "traffic", "share")}
     kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot, 4)}
                     for k, v in ranked}
+    bfs_levels = level_bandwidth(bfs_lv, peak)
 
-    # ---- schedules side by side (BFS only)
-    sched_cmp = None
-    if args.schedules:
-        sched_cmp = {}
-        cands = ["heuristic", "push", "pull"] + (["learned"] if os.path.exists(
-            os.path.join(ROOT, "paper_2405_11671_gb300", "sched_mlp.json")) else [])
-        for name in cands:
-            mm = load_mlp(byo) if name == "learned" else None
-            spx = sched_struct(byo, name, mm)
-            byo.byo_bfs(g.handle, srcs, levels, parents, spx)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(3):
-                byo.byo_bfs(g.handle, srcs, levels, parents, spx)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b) / 3
-            sched_cmp[name] = {"bfs_ms": round(ms, 4), "bfs_gteps": round(bfs_edges / (ms / 1e3) / 1e9, 3)}
-            if mm:
-                byo.byo_mlp_destroy(mm)
+    # ---- schedules side by side (BFS only), here and on the high-diameter grid
+    sched_cmp = grid_cmp = None
+    if not args.no_schedules and rank == 0:
+        sched_cmp = schedule_table(byo, torch, g.handle, srcs, levels, parents, args.sched_reps, stream)
+        if args.workload != "grid":
+            grid_cmp = grid_schedules(byo, torch, args.sched_reps, stream)
 
     # ---- end to end through the C ABI from host buffers
     e2e = None
     if not args.no_e2e:
-        src_h = torch.from_numpy(np.ascontiguousarray(src, np.uint32).view(np.int32)).pin_memory()
-        dst_h = torch.from_numpy(np.ascontiguousarray(dst, np.uint32).view(np.int32)).pin_memory()
+        src_h, dst_h = pinned_u32(torch, src), pinned_u32(torch, dst)
         lv_h = torch.empty((S, n), dtype=torch.int32).pin_memory()
         lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
         rk_h = torch.empty(n, dtype=torch.float32).pin_memory()
@@ -695,10 +992,12 @@ def main():
                            "l2": "inputs larger than L2 (graph >> 129 MB)", "build_s": round(build_s, 3),
                            "triangles": tri["count"]},
                 "algos": per_algo, "edges_per_step": edges, "roofline": roof, "other_rooflines": rooflines,
-                "kernels": kernel_share,
+                "bfs_levels": bfs_levels, "kernels": kernel_share,
                 "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cb}
         if sched_cmp is not None:
             line["schedules"] = sched_cmp
+        if grid_cmp is not None:
+            line["schedules_grid"] = grid_cmp
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

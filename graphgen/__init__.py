@@ -223,3 +223,34 @@ def batched_member(kind: str, n: int, k: int, seed: int):
     if kind == "er":
         return er(n, k, seed)
     return rmat(int(round(math.log2(n))), k, seed)
+
+
+def batched_workload(count: int = 256, sources: int = 64):
+    """The many-graphs workload: per member (n, src, dst) with LOCAL ids and
+    ``sources`` BFS sources (distinct non-isolated vertices where the member
+    has that many, then 0, 1, 2, ... to fill the row)."""
+    members = []
+    for kind, n, k, sd in batched_params(count):
+        s, d = batched_member(kind, n, k, sd)
+        picked = pick_sources(n, s, d, sources, sd + 1).tolist()
+        picked += [v % n for v in range(sources - len(picked))]
+        members.append((n, s, d, picked[:sources]))
+    return members
+
+
+def dynamic_rounds(n: int, src: np.ndarray, dst: np.ndarray, rounds: int = 10, batch: int = 1_000_000,
+                   seed: int | None = None, scale: int = 24):
+    """Update batches of the dynamic-container workload, one per round:
+    (insert_src, insert_dst, delete_src, delete_dst).  Inserts are ``batch``
+    RMAT draws; deletes are ``batch`` pairs drawn uniformly (with repetition)
+    from every pair inserted before this round, the base graph included."""
+    s = SEEDS["rmat24"] if seed is None else seed
+    pool_s, pool_d = [src], [dst]
+    for r in range(rounds):
+        ins_s, ins_d = rmat(scale, batch, stream(s, 100 + r))
+        ps, pd = np.concatenate(pool_s), np.concatenate(pool_d)
+        pick = pick_indices(len(ps), batch, stream(s, 200 + r))
+        yield ins_s, ins_d, ps[pick], pd[pick]
+        pool_s.append(ins_s)
+        pool_d.append(ins_d)
+

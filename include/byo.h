@@ -136,7 +136,7 @@ typedef struct byo_sched {
 
 /* ------------------------------------------------------------------------ */
 /* Schedule network (not in the paper: it only picks among equivalent       */
-/* execution paths, so results never depend on it).  A 12 -> 32 -> 32 -> 4  */
+/* execution paths, so results never depend on it).  A 12 -> 32 -> 32 -> 5  */
 /* ReLU MLP over the frontier features of one BFS iteration (the fields of   */
 /* byo_bfs_iter), outputs = scores of the BYO_NUM_ACTIONS schedule actions.   */
 /* Parameters are FP32, packed W1[32][12], b1[32], W2[32][32], b2[32],        */
@@ -182,7 +182,11 @@ byo_sched byo_sched_default(void);
  * order.  sources is a HOST array.  sched NULL = byo_sched_default().
  * The whole traversal of one source runs in one persistent cooperative launch:
  * no host round trip per iteration.  Synchronises the stream.
- * Errors: INVALID_ARG (source >= n, NULL levels), TIMEOUT, CUDA.
+ * Errors: INVALID_ARG (source >= n, NULL levels), TIMEOUT (a device-side wait
+ * or the traversal itself exceeded BYO_TIMEOUT_MS), CUDA.  The status is the
+ * one the first failing source's kernel wrote; the sources after it are not
+ * traversed and their rows of levels/parents are unspecified.  The graph's
+ * BFS state is reset before the call returns, so the next call runs normally.
  */
 byo_status byo_bfs(const byo_graph* g, const uint32_t* host_sources, uint32_t num_sources, uint32_t* levels,
                    uint32_t* parents, const byo_sched* sched, void* stream);
@@ -314,9 +318,13 @@ byo_status byo_msbfs(const byo_graph* g, const uint32_t* host_sources, uint32_t 
 /*   sched    as for byo_bfs (NULL = default)                               */
 /* The first call on a device looks up the array's device address (with     */
 /* that device current) and caches it; make that first call before any     */
-/* stream capture.  Every call shares the one array: calls that overlap on  */
-/* the GPU (other streams, other host threads) race and must not be issued. */
-/* Synchronises the stream.  Errors: INVALID_ARG, TIMEOUT, CUDA.            */
+/* stream capture begins.  cudaDeviceReset discards the array, so the      */
+/* cached address is stale afterwards: do not call this entry point on a   */
+/* device after resetting it.  Every call shares the one array: calls that  */
+/* overlap on the GPU (other streams, other host threads) race and must not */
+/* be issued.  Every call ends by reading the kernel's status word back to  */
+/* the host, so it synchronises the stream.                                 */
+/* Errors: INVALID_ARG, TIMEOUT, CUDA (the status the kernel reported).     */
 #define BYO_NOALLOC_MAX_VERTICES (1u << 20)
 byo_status byo_bfs_noalloc(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* col, uint32_t source,
                            uint32_t* levels, uint32_t* parents, const byo_sched* sched, void* stream);

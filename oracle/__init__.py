@@ -70,6 +70,10 @@ def _load():
         lib.ora_bytecode_decode.argtypes = [ctypes.c_uint32, _u64p, _u64p, _u8p, _u32p]
         lib.ora_tc.restype = ctypes.c_uint64
         lib.ora_tc.argtypes = [ctypes.c_uint32, _u64p, _u32p]
+        lib.ora_tc_dag_build.restype = None
+        lib.ora_tc_dag_build.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u64p, _u32p]
+        lib.ora_tc_dag_count.restype = ctypes.c_uint64
+        lib.ora_tc_dag_count.argtypes = [_u64p, _u32p, ctypes.c_uint32, ctypes.c_uint32]
         lib.ora_dyn_create.restype = ctypes.c_void_p
         lib.ora_dyn_create.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint64]
         lib.ora_dyn_destroy.restype = None
@@ -191,6 +195,34 @@ def bytecode_decode(n: int, off: np.ndarray, boff: np.ndarray, data: np.ndarray)
 def tc(g: CSR) -> int:
     col = g.col if len(g.col) else np.zeros(1, np.uint32)
     return int(_load().ora_tc(g.n, _p(g.off), _p(col)))
+
+
+def tc_dag(g: CSR):
+    """Out-lists of the (degree, id)-ordered DAG: (dag_off uint64[n+1], dag_col uint32[m/2])."""
+    dag_off = np.zeros(g.n + 1, np.uint64)
+    dag_col = np.empty(max(g.m // 2, 1), np.uint32)
+    col = g.col if len(g.col) else np.zeros(1, np.uint32)
+    _load().ora_tc_dag_build(g.n, _p(g.off), _p(col), _p(dag_off), _p(dag_col))
+    return dag_off, dag_col
+
+
+def tc_dag_count(dag_off: np.ndarray, dag_col: np.ndarray, lo: int, hi: int) -> int:
+    """Triangles counted at the DAG edges whose centre lies in [lo, hi)."""
+    return int(_load().ora_tc_dag_count(_p(dag_off), _p(dag_col), lo, hi))
+
+
+def tc_ordered(g: CSR, threads: int = 1, chunks: int = 1) -> int:
+    """Triangle count through the degree-ordered DAG; the sum over centre
+    ranges may be split across host threads (each range runs the serial C
+    routine, which releases the GIL), for the full-size reference values."""
+    dag_off, dag_col = tc_dag(g)
+    if threads <= 1 or g.n < 2:
+        return tc_dag_count(dag_off, dag_col, 0, g.n)
+    import concurrent.futures as cf
+    bounds = [g.n * i // chunks for i in range(chunks + 1)]
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = ex.map(lambda i: tc_dag_count(dag_off, dag_col, bounds[i], bounds[i + 1]), range(chunks))
+        return sum(parts)
 
 
 class DynGraph:

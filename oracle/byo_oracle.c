@@ -327,6 +327,46 @@ uint64_t ora_tc(uint32_t n, const uint64_t* off, const uint32_t* col) {
   return total;
 }
 
+/*
+ * The same count through the filter step of Section 4.4 (keep each edge in one
+ * direction, then intersect): every edge {u,v} is kept as u -> v when u
+ * precedes v in the order (degree, id), giving out-lists N+(u) in ascending id
+ * order.  A triangle a < b < c in that order is then counted exactly once, at
+ * the DAG edge a -> b, by c in N+(a) and N+(b).  ora_tc_dag_build writes the
+ * out-lists (dag_off[n+1], dag_col[m/2]); ora_tc_dag_count sums
+ * |N+(u) intersect N+(v)| over the DAG edges u -> v with lo <= u < hi (a range
+ * of centres, so that a test driver may split the sum); both serial.
+ */
+void ora_tc_dag_build(uint32_t n, const uint64_t* off, const uint32_t* col, uint64_t* dag_off, uint32_t* dag_col) {
+  dag_off[0] = 0;
+  for (uint32_t u = 0; u < n; ++u) {
+    uint64_t du = off[u + 1] - off[u];
+    uint64_t w = dag_off[u];
+    for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = col[e];
+      uint64_t dv = off[v + 1] - off[v];
+      if (du < dv || (du == dv && u < v)) dag_col[w++] = v;
+    }
+    dag_off[u + 1] = w;
+  }
+}
+
+uint64_t ora_tc_dag_count(const uint64_t* dag_off, const uint32_t* dag_col, uint32_t lo, uint32_t hi) {
+  uint64_t total = 0;
+  for (uint32_t u = lo; u < hi; ++u) {
+    for (uint64_t e = dag_off[u]; e < dag_off[u + 1]; ++e) {
+      uint32_t v = dag_col[e];
+      uint64_t i = dag_off[u], j = dag_off[v];
+      while (i < dag_off[u + 1] && j < dag_off[v + 1]) {
+        if (dag_col[i] < dag_col[j]) ++i;
+        else if (dag_col[i] > dag_col[j]) ++j;
+        else { ++total; ++i; ++j; }
+      }
+    }
+  }
+  return total;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dynamic graph: the edge set itself, as sorted unique keys (u<<32|v).     */
 /* Batch semantics follow the set model (Section 3.1) and the batch update */

@@ -391,6 +391,15 @@ def byo_bfs_noalloc(n: int, m: int, offsets: torch.Tensor, col: torch.Tensor, so
     _u32t(levels, "levels")
     if parents is not None:
         _u32t(parents, "parents")
+    # the kernel trusts these sizes: check them here, before the call
+    if offsets.numel() < n + 1:
+        raise ValueError(f"offsets has {offsets.numel()} entries, needs n+1 = {n + 1}")
+    if col.numel() < m + 4:
+        raise ValueError(f"col has {col.numel()} entries, needs m+4 = {m + 4} (16-byte vector reads of the tail)")
+    if col.data_ptr() % 16:
+        raise ValueError("col must start on a 16-byte boundary")
+    if levels.numel() < n or (parents is not None and parents.numel() < n):
+        raise ValueError(f"levels/parents need n = {n} entries")
     sp = ctypes.byref(sched) if sched is not None else None
     _check(load().byo_bfs_noalloc(n, m, offsets.data_ptr(), col.data_ptr(), source, levels.data_ptr(),
                                   parents.data_ptr() if parents is not None else None, sp, _stream(stream)))

@@ -729,6 +729,8 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
   const uint32_t n = a.g.num_vertices();
   BfsCtl* ctl = a.ctl;
   const bool owner = blockIdx.x == 0;
+  // an earlier source of the same call failed: its status stands, nothing runs
+  if (ld_cg(&ctl->err) != 0) return;
   const Workers grid_wk{blockIdx.x, gridDim.x, (uint32_t)(gtid >> 5), (uint32_t)(gthreads >> 5)};
   const Workers solo_wk{0, 1, tid >> 5, blockDim.x >> 5};
 
@@ -933,6 +935,16 @@ byo_status ensure_bfs_work(byo_graph* g) {
   return BYO_OK;
 }
 
+// The status a BFS launch left in its control block, as the call's result.
+byo_status bfs_device_status(uint32_t err, const char* who) {
+  if (err == (uint32_t)BYO_ERR_TIMEOUT) {
+    set_error("%s: a device-side wait exceeded BYO_TIMEOUT_MS", who);
+    return BYO_ERR_TIMEOUT;
+  }
+  set_error("%s: the kernel reported status %u (a frontier queue region overflowed)", who, err);
+  return err <= (uint32_t)BYO_ERR_NOT_SYMMETRIC ? (byo_status)err : BYO_ERR_CUDA;
+}
+
 }  // namespace
 }  // namespace byo
 
@@ -941,7 +953,7 @@ using namespace byo;
 extern "C" byo_status byo_bfs(const byo_graph* gc, const uint32_t* host_sources, uint32_t num_sources,
                               uint32_t* levels, uint32_t* parents, const byo_sched* sched, void* stream) {
   clear_error();
-  BYO_RETURN_IF(check_graph(gc));
+  BYO_RETURN_IF(ready_graph(gc, static_cast<cudaStream_t>(stream)));
   byo_graph* g = const_cast<byo_graph*>(gc);
   if (num_sources == 0) return BYO_OK;
   if (!host_sources || !levels) {
@@ -966,11 +978,11 @@ extern "C" byo_status byo_bfs(const byo_graph* gc, const uint32_t* host_sources,
   BYO_CUDA(cudaMemcpyAsync(&err, &g->bfs->ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   BYO_CUDA(cudaStreamSynchronize(s));
   if (err) {
+    // the next call starts from a clean control block
     cudaMemsetAsync(&g->bfs->ctl->err, 0, sizeof(uint32_t), s);
     cudaMemsetAsync(&g->bfs->ctl->bar, 0, sizeof(GridBar), s);
     cudaStreamSynchronize(s);
-    set_error("byo_bfs: a device-side wait exceeded BYO_TIMEOUT_MS");
-    return BYO_ERR_TIMEOUT;
+    return bfs_device_status(err, "byo_bfs");
   }
   return BYO_OK;
 }
@@ -1123,9 +1135,6 @@ extern "C" byo_status byo_bfs_noalloc(uint32_t n, uint64_t m, const uint64_t* of
   uint32_t err = 0;
   BYO_CUDA(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   BYO_CUDA(cudaStreamSynchronize(s));
-  if (err) {
-    set_error("byo_bfs_noalloc: a device-side wait exceeded BYO_TIMEOUT_MS");
-    return BYO_ERR_TIMEOUT;
-  }
+  if (err) return bfs_device_status(err, "byo_bfs_noalloc");
   return BYO_OK;
 }

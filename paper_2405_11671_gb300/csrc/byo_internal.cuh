@@ -85,6 +85,7 @@ struct byo_graph {
   uint32_t n = 0;
   uint64_t m = 0;
   uint64_t version = 0;  // bumped whenever the structure changes (cached launch plans depend on it)
+  bool buckets_stale = false;  // vorder/bstart lag the degrees (see ready_graph)
   uint32_t flags = 0;
   bool off64 = false;
   int device = 0;
@@ -114,6 +115,9 @@ void pr_free(PrWork* w);
 void tc_free(TcWork* w);
 void dyn_free(DynStore* d);
 byo_status check_graph(const byo_graph* g);
+// check_graph, then re-derive the degree buckets on stream s if a batch update
+// could not (it ran out of memory after applying the batch).
+byo_status ready_graph(const byo_graph* g, cudaStream_t s);
 // Sorted, unique (row, col) pairs of k raw pairs (both directions when sym,
 // self-loops dropped).  *rows and *cols are stream-ordered temporaries of
 // *count + 4 entries that the caller releases with tmp_free.  Ids >= n give

@@ -267,7 +267,7 @@ using namespace byo;
 
 extern "C" byo_status byo_cc(const byo_graph* g, uint32_t* labels, void* stream) {
   clear_error();
-  BYO_RETURN_IF(check_graph(g));
+  BYO_RETURN_IF(ready_graph(g, static_cast<cudaStream_t>(stream)));
   if (g->n == 0) return BYO_OK;
   if (!labels) {
     set_error("byo_cc: NULL labels");

@@ -449,7 +449,13 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
   tmp_free(free_cls, s);
   tmp_free(d_stacks, s);
   tmp_free(d_cap, s);
-  if (st == BYO_OK) st = rebuild_buckets(g, s);
+  // the batch is applied; if the buckets cannot be re-derived now (no memory
+  // for the sort), the next call that reads them does it
+  if (st == BYO_OK) {
+    g->buckets_stale = true;
+    st = rebuild_buckets(g, s);
+    if (st == BYO_OK) g->buckets_stale = false;
+  }
   return st;
 }
 

@@ -18,6 +18,8 @@ namespace byo {
 
 // ---------------------------------------------------------------- errors
 static thread_local char g_err[512] = "";
+// device allocations made by the current public call (see inject_alloc_failure)
+static thread_local long long t_allocs_in_call = 0;
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -25,7 +27,10 @@ void set_error(const char* fmt, ...) {
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
 }
-void clear_error() { g_err[0] = 0; }
+void clear_error() {
+  g_err[0] = 0;
+  t_allocs_in_call = 0;
+}
 
 byo_status cuda_status(cudaError_t e, const char* what) {
   set_error("%s: %s", what, cudaGetErrorString(e));
@@ -33,8 +38,24 @@ byo_status cuda_status(cudaError_t e, const char* what) {
   return BYO_ERR_CUDA;
 }
 
+// Allocation-failure injection for tests of the error paths: with
+// BYO_FAULT_INJECT=alloc:K in the environment, the K-th device allocation
+// (cudaMalloc or cudaMallocAsync) that a public call makes is not made and
+// reports OUT_OF_MEMORY, as a full device would.  The count restarts at every
+// public call (clear_error).  Only the host side is involved.
+static bool inject_alloc_failure() {
+  const char* e = getenv("BYO_FAULT_INJECT");
+  if (!e || strncmp(e, "alloc:", 6) != 0) return false;
+  const long long k = atoll(e + 6);
+  return k > 0 && ++t_allocs_in_call == k;
+}
+
 byo_status dev_alloc(void** p, size_t bytes, const char* what) {
   *p = nullptr;
+  if (inject_alloc_failure()) {
+    set_error("cudaMalloc(%zu bytes) for %s: injected failure (BYO_FAULT_INJECT)", bytes, what);
+    return BYO_ERR_OUT_OF_MEMORY;
+  }
   cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -73,6 +94,10 @@ static void keep_pool_warm() {
 
 byo_status tmp_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
   *p = nullptr;
+  if (inject_alloc_failure()) {
+    set_error("cudaMallocAsync(%zu bytes) for %s: injected failure (BYO_FAULT_INJECT)", bytes, what);
+    return BYO_ERR_OUT_OF_MEMORY;
+  }
   keep_pool_warm();
   cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
   if (e != cudaSuccess) {
@@ -109,6 +134,15 @@ byo_status check_graph(const byo_graph* g) {
     set_error("graph handle is NULL");
     return BYO_ERR_INVALID_ARG;
   }
+  return BYO_OK;
+}
+
+byo_status ready_graph(const byo_graph* gc, cudaStream_t s) {
+  BYO_RETURN_IF(check_graph(gc));
+  byo_graph* g = const_cast<byo_graph*>(gc);
+  if (!g->buckets_stale) return BYO_OK;
+  BYO_RETURN_IF(rebuild_buckets(g, s));
+  g->buckets_stale = false;
   return BYO_OK;
 }
 

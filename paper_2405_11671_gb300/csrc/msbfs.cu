@@ -300,7 +300,7 @@ extern "C" byo_status byo_batch_member_base(const byo_graph* g, uint32_t i, uint
 extern "C" byo_status byo_msbfs(const byo_graph* gc, const uint32_t* host_sources, uint32_t num_sources,
                                 uint32_t* levels, const byo_sched* sched, void* stream) {
   clear_error();
-  BYO_RETURN_IF(check_graph(gc));
+  BYO_RETURN_IF(ready_graph(gc, static_cast<cudaStream_t>(stream)));
   byo_graph* g = const_cast<byo_graph*>(gc);
   const uint32_t members = g->members ? g->members : 1;
   if (num_sources == 0 || num_sources > 64 || !host_sources || !levels) {

@@ -573,7 +573,7 @@ using namespace byo;
 extern "C" byo_status byo_pagerank(const byo_graph* gc, float damping, uint32_t iters, float* ranks,
                                    double* host_residual, void* stream) {
   clear_error();
-  BYO_RETURN_IF(check_graph(gc));
+  BYO_RETURN_IF(ready_graph(gc, static_cast<cudaStream_t>(stream)));
   byo_graph* g = const_cast<byo_graph*>(gc);
   if (!(damping >= 0.0f && damping <= 1.0f)) {
     set_error("byo_pagerank: damping must be in [0, 1]");

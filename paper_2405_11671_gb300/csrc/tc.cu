@@ -1032,7 +1032,7 @@ using namespace byo;
 
 extern "C" byo_status byo_tc(const byo_graph* gc, uint64_t* host_count, void* stream) {
   clear_error();
-  BYO_RETURN_IF(check_graph(gc));
+  BYO_RETURN_IF(ready_graph(gc, static_cast<cudaStream_t>(stream)));
   if (!host_count) {
     set_error("byo_tc: NULL output");
     return BYO_ERR_INVALID_ARG;
@@ -1046,7 +1046,7 @@ extern "C" byo_status byo_tc(const byo_graph* gc, uint64_t* host_count, void* st
 
 extern "C" byo_status byo_tc_work(const byo_graph* gc, uint64_t* host_work3, void* stream) {
   clear_error();
-  BYO_RETURN_IF(check_graph(gc));
+  BYO_RETURN_IF(ready_graph(gc, static_cast<cudaStream_t>(stream)));
   if (!host_work3) {
     set_error("byo_tc_work: NULL output");
     return BYO_ERR_INVALID_ARG;

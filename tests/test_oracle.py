@@ -308,6 +308,42 @@ def test_tc_trace_a3():
     assert oracle.tc(g) * 6 == int(np.trace(A @ A @ A))
 
 
+def test_tc_ordered_closed_forms_and_brute_force():
+    # the degree-ordered DAG count (used for the full-size reference values)
+    # against the same closed forms and brute force as the plain count
+    for n in (3, 4, 9, 25):
+        assert oracle.tc_ordered(oracle.csr_build(n, *_complete(n))) == math.comb(n, 3)
+    assert oracle.tc_ordered(oracle.csr_build(64, *_grid_full(8, 8))) == 0
+    for n in (4, 7, 30):                                      # wheel: a hub of higher degree
+        rim = np.arange(1, n + 1, dtype=np.uint32)
+        src = np.concatenate([np.zeros(n, np.uint32), rim])
+        dst = np.concatenate([rim, np.roll(rim, -1)])
+        assert oracle.tc_ordered(oracle.csr_build(n + 1, src, dst)) == n
+    for seed in range(3):
+        n = 60
+        src, dst = _random_graph(n, 0.2, seed)
+        g = oracle.csr_build(n, src, dst)
+        A = _dense(g).astype(bool)
+        cnt = sum(int(np.count_nonzero(A[i, j + 1:] & A[j, j + 1:]))
+                  for i in range(n) for j in range(i + 1, n) if A[i, j])
+        assert oracle.tc_ordered(g) == cnt
+
+
+def test_tc_ordered_dag_and_split_sum():
+    n, src, dst = graphgen.rmat_small(11, 16, 21)               # hubs and many equal degrees
+    g = oracle.csr_build(n, src, dst)
+    dag_off, dag_col = oracle.tc_dag(g)
+    deg = np.diff(g.off.astype(np.int64))
+    assert int(dag_off[-1]) * 2 == g.m                          # every edge kept once
+    rows = np.repeat(np.arange(n), np.diff(dag_off.astype(np.int64)))
+    d = dag_col[:int(dag_off[-1])].astype(np.int64)
+    assert np.all((deg[rows] < deg[d]) | ((deg[rows] == deg[d]) & (rows < d)))   # (degree, id) order
+    A = _dense(g).astype(np.float64)                            # exact: counts stay far below 2^53
+    want = int(round(np.trace(A @ A @ A))) // 6
+    assert oracle.tc_ordered(g) == want == oracle.tc(g)
+    assert oracle.tc_ordered(g, threads=3, chunks=17) == want   # centre ranges sum to the whole
+
+
 # ----------------------------------------------------------------------------- betweenness
 
 def test_bc_path_star_complete():

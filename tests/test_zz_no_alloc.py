@@ -59,10 +59,24 @@ def test_noalloc_matches_byo_bfs_twice(byo, mode):
 
 
 def test_noalloc_rejects_oversize_graph(byo):
+    # straight through the C ABI: the library itself refuses n above the
+    # size of its built-in array, before touching any pointer
     n = byo.BYO_NOALLOC_MAX_VERTICES + 1
     off = torch.zeros(2, dtype=torch.int64, device="cuda")
     col = torch.zeros(4, dtype=torch.int32, device="cuda")
     lv = torch.zeros(2, dtype=torch.int32, device="cuda")
-    with pytest.raises(byo.ByoError) as e:
-        byo.byo_bfs_noalloc(n, 0, off, col, 0, lv)
-    assert e.value.status == byo.BYO_ERR_INVALID_ARG
+    st = byo.load().byo_bfs_noalloc(n, 0, off.data_ptr(), col.data_ptr(), 0, lv.data_ptr(), None, None,
+                                    torch.cuda.current_stream().cuda_stream)
+    assert st == byo.BYO_ERR_INVALID_ARG
+
+
+def test_noalloc_wrapper_rejects_short_buffers(byo):
+    n, m = 8, 12
+    off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    col = torch.zeros(m + 4, dtype=torch.int32, device="cuda")
+    lv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    for bad in (dict(offsets=off[:n]), dict(col=col[:m]), dict(levels=lv[:n - 1]), dict(col=col[1:])):
+        kw = dict(offsets=off, col=col, levels=lv)
+        kw.update(bad)
+        with pytest.raises(ValueError):
+            byo.byo_bfs_noalloc(n, m, kw["offsets"], kw["col"], 0, kw["levels"])
