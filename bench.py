@@ -247,7 +247,8 @@ def bfs_method_bytes(torch, off, col, lv, trace, off_bytes: int):
       pull level: sum over unvisited v of (offset + 4 scanned(v)) + 3n/8 (frontier,
                   visited and next bit arrays) + 8|F'|, where scanned(v) counts
                   v's neighbours in ascending order up to and including the first
-                  one in the frontier (all of them when none is)
+                  one in the frontier (all of them when none is); a vertex without
+                  neighbours has nothing to scan and is not counted
       plus 8n + n/8 to initialise levels, parents and visited bits.
     The direction of each level is the one the traversal took (trace).
     Returns (total bytes, [(level, direction, bytes, t_ns), ...])."""
@@ -265,9 +266,11 @@ def bfs_method_bytes(torch, off, col, lv, trace, off_bytes: int):
     degL = torch.bincount(Lr, weights=deg[reached].double(), minlength=top + 2)
     sel = reached & (L > 0)
     fpL = torch.bincount(L[sel], weights=(fp[sel] + 1).double(), minlength=top + 2)
-    cum_cnt = torch.cumsum(cnt, 0)
+    pos = reached & (deg > 0)
+    cum_pos = torch.cumsum(torch.bincount(L[pos], minlength=top + 2).double(), 0)   # reached, with neighbours
+    n_pos = int((deg > 0).sum())
     cum_deg = torch.cumsum(degL, 0)
-    cnt, degL, fpL, cum_cnt, cum_deg = (x.cpu().tolist() for x in (cnt, degL, fpL, cum_cnt, cum_deg))
+    cnt, degL, fpL, cum_pos, cum_deg = (x.cpu().tolist() for x in (cnt, degL, fpL, cum_pos, cum_deg))
     out = []
     total = 8.0 * n + n / 8.0
     for r in trace:
@@ -277,7 +280,7 @@ def bfs_method_bytes(torch, off, col, lv, trace, off_bytes: int):
         if r.direction == 1:
             b = off_bytes * F + 4.0 * degL[lvl_] + 4.0 * F + 12.0 * Fn + n / 8.0
         else:
-            unvis = n - cum_cnt[lvl_]
+            unvis = n_pos - cum_pos[lvl_]
             deg_beyond = m - (cum_deg[lvl_ + 1] if lvl_ + 1 < len(cum_deg) else cum_deg[-1])
             scanned = (fpL[lvl_ + 1] if lvl_ + 1 < len(fpL) else 0.0) + deg_beyond
             b = off_bytes * unvis + 4.0 * scanned + 3.0 * n / 8.0 + 8.0 * Fn

@@ -263,6 +263,24 @@ byo_status byo_tc(const byo_graph* g, uint64_t* host_count, void* stream);
  * the other endpoint when that list is sorted).  Synchronises. */
 byo_status byo_tc_work(const byo_graph* g, uint64_t* host_work3, void* stream);
 
+/*
+ * Single-source betweenness centrality (BC in the table of algorithms of
+ * Section 6.2), by Brandes' accumulation: the BFS of byo_bfs from `source`
+ * gives the levels; sigma[v] = number of shortest source-v paths (sigma of the
+ * source = 1, summed over the neighbours one level closer, level by level);
+ * delta[v] = sum over the neighbours w one level deeper of
+ * sigma[v] / sigma[w] * (1 + delta[w]), from the deepest level up: the
+ * dependency of the source on v.  delta[source] = 0; unreached vertices get
+ * sigma = delta = 0 and level INF.  sigma, delta: device FP64 arrays of n
+ * entries; levels: device uint32[n] (nullable: then library scratch).  Both
+ * sweeps gather over each vertex's own list (no floating-point atomics), so
+ * the results do not depend on scheduling; path counts are exact while below
+ * 2^53.  Synchronises the stream.
+ * Errors: INVALID_ARG (source >= n, NULL sigma/delta), OUT_OF_MEMORY,
+ * TIMEOUT, CUDA.
+ */
+byo_status byo_bc(const byo_graph* g, uint32_t source, uint32_t* levels, double* sigma, double* delta, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Many graphs at once.  byo_batch_build stores num_graphs graphs as one      */
 /* container over their disjoint union: member i owns the global ids          */

@@ -86,6 +86,7 @@ SIGNATURES = [
     ("byo_pagerank", _st, [_vp, ctypes.c_float, _u32, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     ("byo_tc", _st, [_vp, ctypes.POINTER(_u64), _vp]),
     ("byo_tc_work", _st, [_vp, ctypes.POINTER(_u64), _vp]),
+    ("byo_bc", _st, [_vp, _u32, _vp, _vp, _vp, _vp]),
     ("byo_mlp_num_params", _u32, []),
     ("byo_mlp_create", _st, [_u64, ctypes.POINTER(_vp)]),
     ("byo_mlp_destroy", _st, [_vp]),
@@ -287,6 +288,18 @@ def byo_tc_work(g: int, stream=None):
     w = (_u64 * 3)()
     _check(load().byo_tc_work(g, w, _stream(stream)))
     return int(w[0]), int(w[1]), int(w[2])
+
+
+def byo_bc(g: int, source: int, levels: torch.Tensor | None = None, stream=None):
+    """(levels int32[n], sigma float64[n], delta float64[n]) of single-source betweenness."""
+    n = byo_num_vertices(g)
+    sigma = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    delta = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    if levels is None:
+        levels = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    _check(load().byo_bc(g, source, _u32t(levels, "levels").data_ptr(), sigma.data_ptr(), delta.data_ptr(),
+                         _stream(stream)))
+    return levels[:n], sigma[:n], delta[:n]
 
 
 # ----------------------------------------------------------------------------- schedule network

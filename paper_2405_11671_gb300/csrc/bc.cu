@@ -1,0 +1,254 @@
+// bc.cu -- single-source betweenness centrality (BC in the paper's table of
+// algorithms, Section 6.2), by Brandes' accumulation (U. Brandes, "A faster
+// algorithm for betweenness centrality", J. Math. Sociology 25(2), 2001):
+//   levels    the BFS of bfs.cu from the source (hop distances);
+//   forward   sigma(v) = sum of sigma(u) over the neighbours u one level
+//             closer (sigma(s) = 1): the number of shortest s-v paths;
+//   backward  delta(v) = sum over the neighbours w one level deeper of
+//             sigma(v) / sigma(w) * (1 + delta(w)), from the deepest level up;
+//             delta(s) = 0.
+// Both sweeps are pulls over the container's neighbour lists, level by level:
+// every vertex gathers from its own list, so no value is accumulated by
+// atomics and the result does not depend on scheduling.  The vertices of a
+// level are grouped first (a counting sort by level), split into light
+// (degree < kHeavy: eight lanes per vertex) and heavy vertices (a whole CTA
+// per vertex).  FP64 throughout: path counts are exact below 2^53.
+#include <vector>
+
+#include "byo_internal.cuh"
+#include "container.cuh"
+#include "prof.cuh"
+
+namespace byo {
+namespace {
+
+constexpr int kBcThreads = 256;
+constexpr uint32_t kHeavy = 256;  // degree at which a vertex gets a whole CTA
+constexpr int kGroup = 8;         // lanes per light vertex
+
+__global__ void bc_init_kernel(uint32_t n, uint32_t src, const uint32_t* __restrict__ level, double* sigma,
+                               double* delta, uint32_t* maxl) {
+  uint32_t mx = 0;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    sigma[v] = v == src ? 1.0 : 0.0;
+    delta[v] = 0.0;
+    const uint32_t l = level[v];
+    if (l != kInf && l > mx) mx = l;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xFFFFFFFFu, mx, o));
+  if (lane_id() == 0 && mx) atomicMax(maxl, mx);
+}
+
+// per level: how many vertices (cnt) and how many of them are light (lcnt)
+template <typename G>
+__global__ void bc_hist_kernel(G g, const uint32_t* __restrict__ level, uint32_t* cnt, uint32_t* lcnt) {
+  const uint32_t n = g.num_vertices();
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t l = level[v];
+    if (l == kInf) continue;
+    atomicAdd(cnt + l, 1u);
+    if (g.degree((uint32_t)v) < kHeavy) atomicAdd(lcnt + l, 1u);
+  }
+}
+
+// vertices grouped by level: light ones from the start of their level's range,
+// heavy ones from its end
+template <typename G>
+__global__ void bc_scatter_kernel(G g, const uint32_t* __restrict__ level, const uint64_t* __restrict__ lstart,
+                                  uint32_t* lcur, uint32_t* hcur, uint32_t* order) {
+  const uint32_t n = g.num_vertices();
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t l = level[v];
+    if (l == kInf) continue;
+    uint64_t at;
+    if (g.degree((uint32_t)v) < kHeavy) at = lstart[l] + atomicAdd(lcur + l, 1u);
+    else at = lstart[l + 1] - 1 - atomicAdd(hcur + l, 1u);
+    order[at] = (uint32_t)v;
+  }
+}
+
+// The gathered term of neighbour u of v at level l: forward, sigma(u) if u is
+// one level closer; backward, (1 + delta(u)) / sigma(u) if u is one deeper.
+template <bool kForward>
+__device__ __forceinline__ double bc_term(uint32_t u, uint32_t want, const uint32_t* __restrict__ level,
+                                          const double* __restrict__ sigma, const double* __restrict__ delta) {
+  if (__ldg(level + u) != want) return 0.0;
+  if (kForward) return __ldcg(sigma + u);
+  return (1.0 + __ldcg(delta + u)) / __ldcg(sigma + u);
+}
+
+template <bool kForward>
+__device__ __forceinline__ void bc_store(uint32_t v, double acc, double* sigma, double* delta) {
+  if (kForward) sigma[v] = acc;
+  else delta[v] = __ldcg(sigma + v) * acc;
+}
+
+// One level of a sweep.  Blocks [0, light_blocks) take the level's light
+// vertices, eight lanes each; the remaining blocks take its heavy vertices,
+// one CTA each.
+template <typename G, bool kForward>
+__global__ void __launch_bounds__(kBcThreads) bc_level_kernel(G g, const uint32_t* __restrict__ order,
+                                                              const uint64_t* __restrict__ lstart,
+                                                              const uint32_t* __restrict__ lcnt, uint32_t l,
+                                                              uint32_t light_blocks, const uint32_t* __restrict__ level,
+                                                              double* sigma, double* delta) {
+  const uint64_t begin = lstart[l], end = lstart[l + 1];
+  const uint64_t mid = begin + lcnt[l];
+  const uint32_t want = kForward ? l - 1 : l + 1;
+  if (blockIdx.x < light_blocks) {
+    const uint32_t lane = threadIdx.x & (kGroup - 1);
+    const uint64_t grp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+    const uint64_t ngrp = (uint64_t)light_blocks * blockDim.x / kGroup;
+    // every group runs the same number of rounds (the shuffles need all lanes)
+    for (uint64_t i0 = begin; i0 < mid; i0 += ngrp) {
+      const uint64_t i = i0 + grp;
+      double acc = 0.0;
+      uint32_t v = 0;
+      if (i < mid) {
+        v = order[i];
+        const Seg s = g.seg(v);
+        for (uint32_t k = lane; k < s.len; k += kGroup)
+          acc += bc_term<kForward>(__ldg(s.p + k), want, level, sigma, delta);
+      }
+#pragma unroll
+      for (int o = kGroup / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o, kGroup);
+      if (i < mid && lane == 0) bc_store<kForward>(v, acc, sigma, delta);
+    }
+  } else {
+    __shared__ double red[kBcThreads / 32];
+    for (uint64_t i = mid + (blockIdx.x - light_blocks); i < end; i += gridDim.x - light_blocks) {
+      const uint32_t v = order[i];
+      const Seg s = g.seg(v);
+      double acc = 0.0;
+      for (uint32_t k = threadIdx.x; k < s.len; k += blockDim.x)
+        acc += bc_term<kForward>(__ldg(s.p + k), want, level, sigma, delta);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+      if (lane_id() == 0) red[threadIdx.x >> 5] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kBcThreads / 32; ++w) t += red[w];
+        bc_store<kForward>(v, t, sigma, delta);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename G>
+byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, double* sigma, double* delta,
+                  cudaStream_t s) {
+  const uint32_t n = g->n;
+  uint32_t* maxl = nullptr;
+  BYO_RETURN_IF(tmp_alloc_t(&maxl, 1, s, "BC depth"));
+  byo_status st = BYO_OK;
+  uint32_t depth = 0;
+  {
+    ProfScope ps("bc_init", s);
+    cudaMemsetAsync(maxl, 0, sizeof(uint32_t), s);
+    bc_init_kernel<<<grid_for(n, kBcThreads), kBcThreads, 0, s>>>(n, src, level, sigma, delta, maxl);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&depth, maxl, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "bc_init_kernel");
+  }
+  tmp_free(maxl, s);
+  BYO_RETURN_IF(st);
+  if (depth == 0) return BYO_OK;  // the source reaches nothing
+  const uint64_t L = (uint64_t)depth + 1;
+  uint32_t *cnt = nullptr, *lcnt = nullptr, *cur = nullptr, *order = nullptr;
+  uint64_t* lstart = nullptr;
+  st = tmp_alloc_t(&cnt, L + 1, s, "BC level counts");
+  if (st == BYO_OK) st = tmp_alloc_t(&lcnt, L, s, "BC light counts");
+  if (st == BYO_OK) st = tmp_alloc_t(&cur, 2 * L, s, "BC cursors");
+  if (st == BYO_OK) st = tmp_alloc_t(&lstart, L + 1, s, "BC level starts");
+  if (st == BYO_OK) st = tmp_alloc_t(&order, n, s, "BC level order");
+  std::vector<uint64_t> hstart;
+  if (st == BYO_OK) {
+    ProfScope ps("bc_group", s);
+    cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (L + 1), s);
+    cudaMemsetAsync(lcnt, 0, sizeof(uint32_t) * L, s);
+    cudaMemsetAsync(cur, 0, sizeof(uint32_t) * 2 * L, s);
+    bc_hist_kernel<G><<<grid_for(n, kBcThreads), kBcThreads, 0, s>>>(view, level, cnt, lcnt);
+    note_launch();
+    st = scan_u32_to_u64(cnt, lstart, L + 1, nullptr, s);
+    if (st == BYO_OK) {
+      bc_scatter_kernel<G><<<grid_for(n, kBcThreads), kBcThreads, 0, s>>>(view, level, lstart, cur, cur + L, order);
+      note_launch();
+      hstart.resize(L + 1);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hstart.data(), lstart, sizeof(uint64_t) * (L + 1), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = cuda_status(e, "bc grouping");
+    }
+  }
+  if (st == BYO_OK) {
+    const uint32_t cap = (uint32_t)sm_count() * 8;
+    auto blocks = [&](uint64_t c) {
+      uint64_t want = (c * kGroup + kBcThreads - 1) / kBcThreads;
+      return (uint32_t)(want < cap ? (want ? want : 1) : cap);
+    };
+    {
+      ProfScope ps("bc_forward", s);
+      for (uint32_t l = 1; l < L; ++l) {
+        const uint64_t c = hstart[l + 1] - hstart[l];
+        const uint32_t lb = blocks(c);
+        bc_level_kernel<G, true><<<lb + (uint32_t)sm_count(), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
+                                                                                   level, sigma, delta);
+        note_launch();
+      }
+    }
+    {
+      ProfScope ps("bc_backward", s);
+      for (uint32_t l = depth; l-- > 1;) {  // the deepest level has no deeper neighbour; delta(s) stays 0
+        const uint64_t c = hstart[l + 1] - hstart[l];
+        const uint32_t lb = blocks(c);
+        bc_level_kernel<G, false><<<lb + (uint32_t)sm_count(), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
+                                                                                    level, sigma, delta);
+        note_launch();
+      }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "bc sweeps");
+  }
+  tmp_free(cnt, s);
+  tmp_free(lcnt, s);
+  tmp_free(cur, s);
+  tmp_free(lstart, s);
+  tmp_free(order, s);
+  return st;
+}
+
+}  // namespace
+}  // namespace byo
+
+using namespace byo;
+
+extern "C" byo_status byo_bc(const byo_graph* gc, uint32_t source, uint32_t* levels, double* sigma, double* delta,
+                             void* stream) {
+  clear_error();
+  BYO_RETURN_IF(ready_graph(gc, static_cast<cudaStream_t>(stream)));
+  if (!sigma || !delta) {
+    set_error("byo_bc: NULL sigma or delta");
+    return BYO_ERR_INVALID_ARG;
+  }
+  if (source >= gc->n) {
+    set_error("byo_bc: source %u is >= n (%u)", source, gc->n);
+    return BYO_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t* lv = levels;
+  if (!lv) BYO_RETURN_IF(tmp_alloc_t(&lv, gc->n, s, "BC levels"));
+  byo_status st = byo_bfs(gc, &source, 1, lv, nullptr, nullptr, stream);
+  if (st == BYO_OK) {
+    clear_error();
+    st = with_view(gc, [&](auto view) { return run_bc(gc, view, source, lv, sigma, delta, s); });
+  }
+  if (!levels) tmp_free(lv, s);
+  return st;
+}

@@ -38,7 +38,7 @@
 namespace byo {
 
 constexpr int kBfsThreads = 256;
-constexpr int kPullThreadMax = 32;  // pull: degrees above this are scanned by a whole warp
+constexpr int kPullThreadMax = 32;  // pull: each lane scans this many ids of its own vertex; the rest, by the warp
 constexpr uint32_t kChunk = 2048;   // push: edges per CTA work item in the CTA bin
 static_assert(kChunk == 1u << 11, "bucket b >= 12 splits into 2^(b - 11) CTA work items");
 constexpr uint32_t kTraceCap = 1u << 16;
@@ -60,6 +60,8 @@ struct BfsWork {
   uint32_t n = 0;
   uint32_t nw = 0;
   uint32_t* vis = nullptr;
+  uint32_t* zmask = nullptr;        // bit per degree-0 vertex (never reached, never scanned)
+  uint64_t zmask_version = ~0ull;   // graph version zmask was computed for
   uint32_t* fb = nullptr;  // 2 * nw words
   uint32_t* queue = nullptr;
   BfsCtl* ctl = nullptr;
@@ -69,6 +71,7 @@ struct BfsWork {
 void bfs_free(BfsWork* w) {
   if (!w) return;
   dev_free(w->vis);
+  dev_free(w->zmask);
   dev_free(w->fb);
   dev_free(w->queue);
   dev_free(w->ctl);
@@ -83,6 +86,7 @@ struct BfsArgs {
   uint32_t* level;
   uint32_t* parent;
   uint32_t* vis;
+  const uint32_t* zmask;  // nullable: the visited bits start as these (degree-0 vertices)
   uint32_t* fb;
   uint32_t* queue;
   const uint64_t* bstart;
@@ -108,6 +112,7 @@ struct BfsShared {
   int fb_valid;
   uint64_t t_top;
   uint32_t t_level;  // level whose start time t_top is
+  unsigned long long red[2];  // this CTA's share of the next frontier's degree sum and ids read
 };
 
 __device__ __forceinline__ int find_bucket(const uint64_t* pre, int lo, int hi, uint64_t i) {
@@ -260,122 +265,233 @@ __device__ __forceinline__ bool in_frontier(const uint32_t* fb, uint32_t u) {
   return (ld_cg(fb + (u >> 5)) >> (u & 31)) & 1u;
 }
 
+// The outputs of the vertices a warp found in one pull step (`found` lanes,
+// vertex v with parent par and degree len): level and parent, their visited
+// and next-frontier bits (grouped by word: one read-modify-write per word,
+// the words being the calling warp's own) and their queue slots (one atomic
+// per degree bucket).  Warp-collective.
 template <typename G, bool kParents>
-__device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, uint32_t L, int nxt, uint64_t& acc_deg,
-                           uint64_t& acc_scan) {
+__device__ __forceinline__ void pull_emit(const BfsArgs<G>& a, const BfsShared& S, uint32_t* fbn, bool found,
+                                          uint32_t v, uint32_t par, uint32_t len, uint32_t L, int nxt,
+                                          uint64_t& acc_deg) {
+  const uint32_t lane = lane_id();
+  if (__ballot_sync(0xFFFFFFFFu, found) == 0) return;
+  uint32_t b = 0xFFFFFFFFu;
+  if (found) {
+    a.level[v] = L + 1;
+    if (kParents) a.parent[v] = par;
+    acc_deg += len;
+    b = (uint32_t)degree_bucket(len);
+  }
+  const uint32_t same_w = __match_any_sync(0xFFFFFFFFu, found ? (v >> 5) : 0xFFFFFFFFu);
+  const uint32_t bits = __reduce_or_sync(same_w, found ? (1u << (v & 31)) : 0u);
+  if (found && (same_w & lanemask_lt()) == 0) {
+    // L2 reads: another SM may have written these lines in earlier levels
+    a.vis[v >> 5] = ld_cg(a.vis + (v >> 5)) | bits;
+    fbn[v >> 5] = ld_cg(fbn + (v >> 5)) | bits;
+  }
+  const uint32_t same_b = __match_any_sync(0xFFFFFFFFu, b);
+  const uint32_t bl = __ffs(same_b) - 1;
+  unsigned long long pos = 0;
+  if (found && lane == bl) pos = atomicAdd(&a.ctl->cnt[nxt][b], (unsigned long long)__popc(same_b));
+  pos = __shfl_sync(0xFFFFFFFFu, pos, bl);
+  if (found) {
+    const uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + pos + __popc(same_b & lanemask_lt());
+    if (at < S.bstart[b + 1]) a.queue[at] = v;
+    else atomicCAS(&a.ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is found once
+  }
+  __syncwarp();  // the word updates are seen by the warp's later readers
+}
+
+// Position of the r-th (0-based, from the least significant) set bit of m,
+// r < popc(m): the largest p with fewer than r + 1 set bits below p, by a
+// binary search over p.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
+  uint32_t p = 0;
+#pragma unroll
+  for (uint32_t s = 16; s > 0; s >>= 1)
+    if ((uint32_t)__popc(m & ((1u << (p + s)) - 1u)) <= r) p += s;
+  return p;
+}
+
+// Deferred long scans of one warp: vertices whose first kPullThreadMax ids
+// hold no frontier neighbour; the whole warp continues each from there.
+constexpr uint32_t kPullDefer = 32;
+
+struct PullDefer {
+  uint32_t v[kPullDefer];
+  uint32_t from[kPullDefer];  // first id (index in the list) not scanned yet
+};
+
+template <typename G, bool kParents>
+__device__ void pull_long(const BfsArgs<G>& a, const BfsShared& S, uint32_t* fbn, const uint32_t* fb,
+                          PullDefer& D, uint32_t cnt, uint32_t L, int nxt, uint64_t& acc_deg, uint64_t& acc_scan) {
+  const uint32_t lane = lane_id();
+  for (uint32_t d = 0; d < cnt; ++d) {
+    const uint32_t v = D.v[d];
+    const Seg sg = a.g.seg(v);
+    const uint32_t* al = align16_down(sg.p);
+    const uint32_t head = (uint32_t)(sg.p - al);
+    const uint32_t end = head + sg.len;
+    const uint32_t from = head + D.from[d];
+    uint32_t got = kInf;
+    for (uint32_t i0 = from & ~3u; i0 < end; i0 += 128) {
+      const uint32_t i = i0 + lane * 4;
+      uint32_t hit = kInf;
+      if (i < end) {
+        const uint4 q = ld_nc_v4(al + i);
+        const uint32_t x[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t idx = i + c;
+          if (hit == kInf && idx >= from && idx < end && in_frontier(fb, x[c])) hit = x[c];
+        }
+      }
+      const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit != kInf);
+      if (lane == 0) acc_scan += min(end, i0 + 128) - max(from, i0);  // upper bound of ids read
+      if (hm) {
+        got = __shfl_sync(0xFFFFFFFFu, hit, __ffs(hm) - 1);
+        break;
+      }
+    }
+    pull_emit<G, kParents>(a, S, fbn, lane == 0 && got != kInf, v, got, sg.len, L, nxt, acc_deg);
+  }
+}
+
+template <typename G, bool kParents>
+__device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, uint32_t L, int nxt,
+                           uint64_t& acc_deg, uint64_t& acc_scan) {
+  // Each warp owns a contiguous range of 32-vertex words of the bit arrays, so
+  // it is the only writer of those words of `vis` and of the next frontier.
+  // Its lanes work as a pool: a lane scans one unvisited vertex at a time,
+  // eight ids per step, and takes the next pending vertex of the warp's range
+  // as soon as it is done, so a long scan in one lane does not hold the
+  // others (no warp-wide wait on the slowest vertex of a word).  A vertex
+  // still without a frontier neighbour after kPullThreadMax ids is deferred
+  // and later scanned by the whole warp, 128 ids per step.
   const uint32_t lane = lane_id();
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  PullDefer& D = defer[threadIdx.x >> 5];
   const uint32_t* fb = a.fb + (size_t)(L & 1) * a.nw;
   uint32_t* fbn = a.fb + (size_t)((L + 1) & 1) * a.nw;
   const uint32_t n = a.g.num_vertices();
-  // the visited bits of a warp's next word are loaded while it works on the current one
-  uint32_t vw_next = gwarp < a.nw ? ld_cg(a.vis + gwarp) : ~0u;
-  for (uint32_t w = gwarp; w < a.nw; w += nwarps) {
-    const uint32_t vw = vw_next;
-    uint32_t v = w * 32 + lane;
-    bool todo = v < n && !((vw >> lane) & 1u);
-    Seg s{nullptr, 0};
-    if (todo) s = a.g.seg(v);
-    vw_next = w + nwarps < a.nw ? ld_cg(a.vis + w + nwarps) : ~0u;
-    if (__ballot_sync(0xFFFFFFFFu, todo) == 0) {
-      if (lane == 0) fbn[w] = 0;
-      continue;
+  const uint32_t per = (a.nw + nwarps - 1) / nwarps;
+  const uint32_t w_lo = min(a.nw, gwarp * per), w_hi = min(a.nw, w_lo + per);
+  for (uint32_t w = w_lo + lane; w < w_hi; w += 32) fbn[w] = 0;  // this warp's words only
+  __syncwarp();
+  // 32 words of pending (unvisited) bits are loaded at a time, one per lane
+  uint32_t batch = w_lo;        // first word of the loaded batch
+  uint32_t pend_lane = 0;       // pending bits of word batch + lane
+  uint32_t k = 32;              // next word of the batch to open (32 = load a new batch)
+  uint32_t P = 0, Pw = 0;       // pending vertices of the open word, and its index
+  uint32_t ndef = 0;            // deferred vertices
+  uint32_t v = kInf;            // this lane's vertex
+  const uint32_t* al = nullptr;
+  uint32_t head = 0, end = 0, i = 0, len = 0;
+  bool fresh = false;           // v was just taken: its list location is not loaded yet
+  while (true) {
+    // free lanes take pending vertices, opening words as needed
+    uint32_t freeL = __ballot_sync(0xFFFFFFFFu, v == kInf);
+    while (freeL) {
+      if (P == 0) {
+        if (k == 32) {
+          if (batch >= w_hi) break;
+          const uint32_t w = batch + lane;
+          uint32_t vw = w < w_hi ? ld_cg(a.vis + w) : ~0u;
+          if (w < w_hi && w == a.nw - 1 && (n & 31)) vw |= ~0u << (n & 31);  // past n: not a vertex
+          pend_lane = ~vw;
+          k = 0;
+        }
+        const uint32_t any = __ballot_sync(0xFFFFFFFFu, pend_lane != 0 && lane >= k);
+        if (any == 0) {
+          batch += 32;
+          k = 32;
+          continue;
+        }
+        k = __ffs(any) - 1;
+        P = __shfl_sync(0xFFFFFFFFu, pend_lane, k);
+        Pw = batch + k;
+        ++k;
+        if (k == 32) batch += 32;
+      }
+      // the free lane of rank r takes the r-th pending vertex (lowest first)
+      const uint32_t r = __popc(freeL & lanemask_lt());
+      const uint32_t np = __popc(P);
+      if (v == kInf && r < np) {
+        v = Pw * 32 + nth_set_bit(P, r);
+        fresh = true;
+      }
+      const uint32_t taken = min((uint32_t)__popc(freeL), np);
+      P = taken >= np ? 0u : P & ~((1u << nth_set_bit(P, taken)) - 1u);  // drop the lowest `taken`
+      freeL = __ballot_sync(0xFFFFFFFFu, v == kInf);
     }
-    bool found = false;
+    const bool active = v != kInf;
+    if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
+    if (fresh) {
+      const Seg sg = a.g.seg(v);
+      al = align16_down(sg.p);
+      head = (uint32_t)(sg.p - al);
+      len = sg.len;
+      end = head + sg.len;
+      i = 0;
+      fresh = false;
+    }
+    // one step: eight ids and their eight frontier words in flight; the
+    // lowest hit is the parent (the first frontier neighbour in ascending order)
+    bool found = false, done = false, defer_it = false;
     uint32_t par = kInf;
-    if (todo && s.len <= (uint32_t)kPullThreadMax && s.len > 0) {
-      // eight ids (two 16-byte loads) and their eight frontier words in flight
-      // per step; the scan stops at the first frontier neighbour
-      const uint32_t* al = align16_down(s.p);
-      uint32_t head = (uint32_t)(s.p - al);
-      uint32_t end = head + s.len;
-      for (uint32_t i = 0; i < end && !found; i += 8) {
+    if (active) {
+      if (i < end) {
         const uint4 q0 = ld_nc_v4(al + i);
         const uint4 q1 = i + 4 < end ? ld_nc_v4(al + i + 4) : make_uint4(0u, 0u, 0u, 0u);
         const uint32_t x[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-        uint32_t hit = kInf, hf = 8;
+        uint32_t hf = 8;
 #pragma unroll
-        for (int c = 7; c >= 0; --c) {  // the lowest hit wins
+        for (int c = 7; c >= 0; --c) {
           const uint32_t idx = i + c;
           if (idx >= head && idx < end && in_frontier(fb, x[c])) {
-            hit = x[c];
+            par = x[c];
             hf = (uint32_t)c;
           }
         }
         const uint32_t lo = head > i ? head : i;
         if (hf < 8) {
           found = true;
-          par = hit;
           acc_scan += i + hf + 1 - lo;  // ids up to and including the hit
         } else {
           acc_scan += (end < i + 8 ? end : i + 8) - lo;
         }
+        i += 8;
       }
+      done = found || i >= end;
+      defer_it = !done && i >= head + kPullThreadMax;
     }
-    uint32_t big = __ballot_sync(0xFFFFFFFFu, todo && s.len > (uint32_t)kPullThreadMax);
-    while (big) {
-      int l = __ffs(big) - 1;
-      big &= big - 1;
-      const uint32_t* p = reinterpret_cast<const uint32_t*>(
-          __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(s.p), l));
-      uint32_t len = __shfl_sync(0xFFFFFFFFu, s.len, l);
-      const uint32_t* al = align16_down(p);
-      uint32_t head = (uint32_t)(p - al);
-      uint32_t end = head + len;
-      uint32_t got = kInf;
-      for (uint32_t i0 = 0; i0 < end; i0 += 128) {
-        uint32_t i = i0 + lane * 4;
-        uint32_t hit = kInf;
-        if (i < end) {
-          uint4 q = ld_nc_v4(al + i);
-          uint32_t x[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            uint32_t idx = i + c;
-            if (hit == kInf && idx >= head && idx < end && in_frontier(fb, x[c])) hit = x[c];
-          }
-        }
-        uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit != kInf);
-        if (hm) {
-          int fl = __ffs(hm) - 1;
-          got = __shfl_sync(0xFFFFFFFFu, hit, fl);
-          if (lane == 0) acc_scan += min(end, i0 + 128) - max(head, i0);  // upper bound of ids read
-          break;
-        }
-        if (lane == 0) acc_scan += min(end, i0 + 128) - max(head, i0);
+    pull_emit<G, kParents>(a, S, fbn, found, v, par, len, L, nxt, acc_deg);
+    // long scans go to the warp's deferred list (scanned when it fills up,
+    // and at the end)
+    const uint32_t dm = __ballot_sync(0xFFFFFFFFu, defer_it);
+    if (dm) {
+      if (ndef + __popc(dm) > kPullDefer) {
+        __syncwarp();
+        pull_long<G, kParents>(a, S, fbn, fb, D, ndef, L, nxt, acc_deg, acc_scan);
+        ndef = 0;
+        __syncwarp();
       }
-      if (lane == (uint32_t)l && got != kInf) {
-        found = true;
-        par = got;
+      if (defer_it) {
+        const uint32_t slot = ndef + __popc(dm & lanemask_lt());
+        D.v[slot] = v;
+        D.from[slot] = i - head;
       }
+      ndef += __popc(dm);
+      __syncwarp();
     }
-    uint32_t fm = __ballot_sync(0xFFFFFFFFu, found);
-    if (lane == 0) {
-      a.vis[w] = vw | fm;
-      fbn[w] = fm;
-    }
-    uint32_t b = 0xFFFFFFFFu;
-    if (found) {
-      a.level[v] = L + 1;
-      if (kParents) a.parent[v] = par;
-      acc_deg += s.len;
-      b = (uint32_t)degree_bucket(s.len);
-    }
-    if (fm == 0) continue;
-    uint32_t same_b = __match_any_sync(0xFFFFFFFFu, b);
-    uint32_t bl = __ffs(same_b) - 1;
-    unsigned long long pos = 0;
-    if (found && lane == bl) pos = atomicAdd(&a.ctl->cnt[nxt][b], (unsigned long long)__popc(same_b));
-    pos = __shfl_sync(0xFFFFFFFFu, pos, bl);
-    if (found) {
-      uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + pos + __popc(same_b & lanemask_lt());
-      if (at < S.bstart[b + 1]) a.queue[at] = v;
-      else atomicCAS(&a.ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);
-    }
+    if (done || defer_it) v = kInf;
   }
+  if (ndef) pull_long<G, kParents>(a, S, fbn, fb, D, ndef, L, nxt, acc_deg, acc_scan);
 }
 
+// warp sum of v into a shared-memory accumulator of the CTA
 __device__ __forceinline__ void flush_acc(unsigned long long* dst, uint64_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
@@ -465,11 +581,17 @@ __device__ uint32_t level_top(const BfsArgs<G>& a, BfsShared& S, uint32_t L, boo
 template <typename G>
 __device__ __forceinline__ void level_end(const BfsArgs<G>& a, BfsShared& S, int nxt, uint64_t acc_deg,
                                           uint64_t acc_scan) {
-  flush_acc(&a.ctl->sdeg[nxt], acc_deg);
-  flush_acc(&a.ctl->scanned[nxt], acc_scan);
+  // warps add into the CTA's accumulators, the CTA into the control block
+  // (one global atomic per counter and CTA)
+  flush_acc(&S.red[0], acc_deg);
+  flush_acc(&S.red[1], acc_scan);
   __syncthreads();
   if (threadIdx.x < (uint32_t)kBuckets) S.base[threadIdx.x] += S.cnt[threadIdx.x];
   if (threadIdx.x == 0) {
+    if (S.red[0]) atomicAdd(&a.ctl->sdeg[nxt], S.red[0]);
+    if (S.red[1]) atomicAdd(&a.ctl->scanned[nxt], S.red[1]);
+    S.red[0] = 0;
+    S.red[1] = 0;
     S.nvis += S.nf;
     S.mvis += S.mf;
     S.prev_dir = S.dir;
@@ -721,6 +843,7 @@ template <typename G, bool kParents>
 __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
   __shared__ BfsShared S;
   __shared__ SoloShared Q;
+  __shared__ PullDefer defer[kBfsThreads / 32];
   __shared__ float wsm[kMlpParams];
   sched_stage_weights(a.sp, wsm);
   const uint32_t tid = threadIdx.x;
@@ -739,7 +862,9 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
     a.level[v] = kInf;
     if (kParents) a.parent[v] = kInf;
   }
-  for (uint64_t w = gtid; w < a.nw; w += gthreads) a.vis[w] = 0;
+  // a vertex without neighbours is never reached (unless it is the source) and
+  // has nothing to scan: it starts as visited, so that pulls skip it
+  for (uint64_t w = gtid; w < a.nw; w += gthreads) a.vis[w] = a.zmask ? __ldg(a.zmask + w) : 0u;
   if (owner) {
     for (int i = tid; i < 3 * kBuckets; i += blockDim.x) (&ctl->cnt[0][0])[i] = 0;
     if (tid < 3) {
@@ -751,6 +876,8 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
   if (tid < (uint32_t)kBuckets) S.base[tid] = 0;
   if (tid == 0) {
     S.nvis = 0;
+    S.red[0] = 0;
+    S.red[1] = 0;
     S.mvis = 0;
     S.prev_dir = 1;
     S.fb_valid = 0;
@@ -763,7 +890,7 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
     int b = degree_bucket(d);
     a.level[s] = 0;
     if (kParents) a.parent[s] = s;
-    a.vis[s >> 5] = 1u << (s & 31);
+    a.vis[s >> 5] = ld_cg(a.vis + (s >> 5)) | (1u << (s & 31));
     a.queue[S.bstart[b]] = s;
     ctl->cnt[0][b] = 1;
     ctl->sdeg[0] = d;
@@ -857,13 +984,25 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
         }
         if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
       }
-      pull_phase<G, kParents>(a, S, L, nxt, acc_deg, acc_scan);
+      pull_phase<G, kParents>(a, S, defer, L, nxt, acc_deg, acc_scan);
     } else {
       push_phase<G, kParents>(a, S, grid_wk, L, nxt, acc_deg, acc_scan);
     }
     level_end(a, S, nxt, acc_deg, acc_scan);
     ++L;
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
+  }
+}
+
+template <typename G>
+__global__ void bfs_zmask_kernel(G g, uint32_t* zmask) {
+  const uint32_t n = g.num_vertices();
+  const uint64_t nw = ((uint64_t)n + 31) / 32;
+  for (uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w0 < nw;
+       w0 += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint64_t v = w0 * 32 + lane_id();
+    const uint32_t z = __ballot_sync(0xFFFFFFFFu, v < n && g.degree((uint32_t)v) == 0);
+    if (lane_id() == 0) zmask[w0] = z;
   }
 }
 
@@ -888,9 +1027,16 @@ template <typename G>
 byo_status run_bfs(const byo_graph* g, G view, const uint32_t* sources, uint32_t ns, uint32_t* levels, uint32_t* parents,
                    const SchedParams& sp, cudaStream_t s) {
   BfsWork* w = g->bfs;
+  if (w->zmask_version != g->version) {
+    bfs_zmask_kernel<G><<<grid_for(g->n, 256), 256, 0, s>>>(view, w->zmask);
+    note_launch();
+    BYO_CHECK_LAUNCH("bfs_zmask_kernel");
+    w->zmask_version = g->version;
+  }
   BfsArgs<G> args;
   args.g = view;
   args.vis = w->vis;
+  args.zmask = w->zmask;
   args.fb = w->fb;
   args.queue = w->queue;
   args.bstart = g->d_bstart;
@@ -919,6 +1065,7 @@ byo_status ensure_bfs_work(byo_graph* g) {
   w->n = g->n;
   w->nw = (g->n + 31) / 32;
   byo_status st = dev_alloc_t(&w->vis, w->nw, "BFS visited bits");
+  if (st == BYO_OK) st = dev_alloc_t(&w->zmask, w->nw, "BFS degree-0 bits");
   if (st == BYO_OK) st = dev_alloc_t(&w->fb, 2ull * w->nw, "BFS frontier bits");
   if (st == BYO_OK) st = dev_alloc_t(&w->queue, g->n, "BFS queue");
   if (st == BYO_OK) st = dev_alloc_t(&w->ctl, 1, "BFS control");
@@ -1122,6 +1269,7 @@ extern "C" byo_status byo_bfs_noalloc(uint32_t n, uint64_t m, const uint64_t* of
   args.level = levels;
   args.parent = parents;
   args.vis = reinterpret_cast<uint32_t*>(b + kNaVis);
+  args.zmask = nullptr;
   args.fb = reinterpret_cast<uint32_t*>(b + kNaFb);
   args.queue = reinterpret_cast<uint32_t*>(b + kNaQueue);
   args.bstart = bstart;

@@ -131,13 +131,18 @@ __device__ __forceinline__ void finish_reduction(double res, double dang, double
   }
   __syncthreads();
   if (!last) return;
+  // the whole block folds the partials: thread t the blocks t, t + T, ... in
+  // order, then a fixed tree over the threads (deterministic; one thread
+  // alone would take thousands of dependent L2 round trips)
+  __threadfence();
+  double R = 0.0, D = 0.0;
+  for (uint32_t b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    R += __ldcg(partials + 2 * b);
+    D += __ldcg(partials + 2 * b + 1);
+  }
+  R = block_sum_f64(R, sh);
+  D = block_sum_f64(D, sh);
   if (threadIdx.x == 0) {
-    __threadfence();
-    double R = 0.0, D = 0.0;
-    for (uint32_t b = 0; b < gridDim.x; ++b) {
-      R += __ldcg(partials + 2 * b);
-      D += __ldcg(partials + 2 * b + 1);
-    }
     scal[0] = D;
     scal[1] = R;
     scal[2] = (1.0 - (double)damping) / (double)n + (double)damping * D / (double)n;
@@ -160,6 +165,38 @@ __global__ void __launch_bounds__(kPrThreads) pr_init_kernel(G g, float* ranks, 
   finish_reduction(0.0, dang, partials, scal, ticket, damping, n);
 }
 
+// L2 eviction priorities: the neighbour ids stream through once per
+// iteration (4 bytes per stored edge, gigabytes), the contributions are
+// gathered at random (4 bytes per vertex, tens of megabytes): the ids are
+// marked evict-first so that they do not push the contributions out of L2,
+// and the contributions evict-last.  (The policy registers are pure values;
+// the compiler hoists their creation out of the loops.)
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Neighbour ids are read once per iteration: keep them out of L1, which is
+// left to the contributions, and first in line for eviction from L2.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
+  uint32_t x;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(x) : "l"(p), "l"(l2_evict_first()));
+  return x;
+}
+
+// A contribution: kept in L2 as long as possible.
+__device__ __forceinline__ float ld_contrib(const float* p) {
+  float x;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(x) : "l"(p), "l"(l2_evict_last()));
+  return x;
+}
+
 template <typename G>
 __device__ __forceinline__ void pr_store(G& g, uint32_t v, uint32_t deg, Comp acc, float d, float base,
                                          float* ranks, float* cn, double& res, double& dang) {
@@ -167,18 +204,13 @@ __device__ __forceinline__ void pr_store(G& g, uint32_t v, uint32_t deg, Comp ac
   float pn = fmaf(d, s, base);
   float old = ranks[v];
   ranks[v] = pn;
-  cn[v] = deg ? pn / (float)deg : 0.0f;
+  // a degree-0 vertex is in no neighbour list, so its contribution is never
+  // gathered and is not written
+  if (deg) cn[v] = pn / (float)deg;
   res += fabs((double)pn - (double)old);
   if (deg == 0) dang += (double)pn;
 }
 
-// Neighbour ids are read once per iteration: keep them out of L1, which is
-// left to the contributions.
-__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
-  uint32_t x;
-  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(x) : "l"(p));
-  return x;
-}
 
 // Compensated sum of c[ids[k]] for k = first, first+stride, ... < len, with
 // eight independent id loads and eight independent gathers in flight per step
@@ -192,7 +224,7 @@ __device__ __forceinline__ void gather_sum(Comp& acc, const uint32_t* __restrict
     for (int j = 0; j < 8; ++j) u[j] = ld_stream(ids + k + j * stride);
     float x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = __ldg(c + u[j]);
+    for (int j = 0; j < 8; ++j) x[j] = ld_contrib(c + u[j]);
 #pragma unroll
     for (int j = 0; j < 8; ++j) neumaier_add(acc, x[j]);
   }
@@ -202,19 +234,19 @@ __device__ __forceinline__ void gather_sum(Comp& acc, const uint32_t* __restrict
     for (int j = 0; j < 4; ++j) u[j] = ld_stream(ids + k + j * stride);
     float x[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) x[j] = __ldg(c + u[j]);
+    for (int j = 0; j < 4; ++j) x[j] = ld_contrib(c + u[j]);
 #pragma unroll
     for (int j = 0; j < 4; ++j) neumaier_add(acc, x[j]);
     k += 4 * stride;
   }
   if (k + stride < len) {
     const uint32_t u0 = ld_stream(ids + k), u1 = ld_stream(ids + k + stride);
-    const float x0 = __ldg(c + u0), x1 = __ldg(c + u1);
+    const float x0 = ld_contrib(c + u0), x1 = ld_contrib(c + u1);
     neumaier_add(acc, x0);
     neumaier_add(acc, x1);
     k += 2 * stride;
   }
-  if (k < len) neumaier_add(acc, __ldg(c + ld_stream(ids + k)));
+  if (k < len) neumaier_add(acc, ld_contrib(c + ld_stream(ids + k)));
 }
 
 // Low-degree vertices (degree < small_lim) are processed in id order, 32 per
@@ -268,7 +300,7 @@ __device__ __forceinline__ void pr_stream_warp(const G& g, uint32_t v0, uint32_t
       id[j] = e < total ? ld_stream(op + (e - oex)) : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < kU; ++j) x[j] = key[j] < 32 ? __ldg(c + id[j]) : 0.f;
+    for (int j = 0; j < kU; ++j) x[j] = key[j] < 32 ? ld_contrib(c + id[j]) : 0.f;
     for (int j = 0; j < kU; ++j) {
       const uint32_t e0 = e00 + 32 * j;
       if (e0 >= total) break;  // warp-uniform
@@ -335,20 +367,27 @@ __global__ void __launch_bounds__(kPrThreads, 8) pr_iter_kernel(G g, VBins bins,
       if (threadIdx.x < 32) {
         Comp a = lane < (blockDim.x >> 5) ? sh[lane] : Comp{0.f, 0.f};
         a = warp_comp_sum(a);
-        if (threadIdx.x == 0) {
-          if (it.K == 1) {
-            pr_store(g, v, s.len, a, damping, base, ranks, cn, res, dang);
-          } else {
+        if (it.K == 1) {
+          if (threadIdx.x == 0) pr_store(g, v, s.len, a, damping, base, ranks, cn, res, dang);
+        } else {
+          uint32_t* t = hub_ticket + (it.vidx - hubs.vbegin);
+          bool last_chunk = false;
+          if (threadIdx.x == 0) {
             part[j] = make_float2(a.s, a.c);
             __threadfence();
-            uint32_t* t = hub_ticket + (it.vidx - hubs.vbegin);
-            if (atomicAdd(t, 1u) == it.K - 1) {
-              __threadfence();
-              Comp tot{0.f, 0.f};
-              for (uint32_t q = 0; q < it.K; ++q) {
-                float2 pq = __ldcg(part + it.first + q);
-                tot = comp_merge(tot, Comp{pq.x, pq.y});
-              }
+            last_chunk = atomicAdd(t, 1u) == it.K - 1;
+          }
+          // the last chunk to finish folds the vertex's chunk partials: lane
+          // l the chunks l, l + 32, ... in order, then the warp's fixed tree
+          if (__shfl_sync(0xFFFFFFFFu, last_chunk, 0)) {
+            __threadfence();
+            Comp tot{0.f, 0.f};
+            for (uint32_t q = lane; q < it.K; q += 32) {
+              const float2 pq = __ldcg(part + it.first + q);
+              tot = comp_merge(tot, Comp{pq.x, pq.y});
+            }
+            tot = warp_comp_sum(tot);
+            if (threadIdx.x == 0) {
               pr_store(g, v, s.len, tot, damping, base, ranks, cn, res, dang);
               *t = 0;
             }

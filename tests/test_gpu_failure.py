@@ -102,7 +102,7 @@ def _free_bytes():
     return torch.cuda.mem_get_info()[0]
 
 
-def _fail_every_allocation(byo, monkeypatch, call, max_k=64):
+def _fail_every_allocation(byo, monkeypatch, call, max_k=2000):
     """Run call() with its K-th allocation failing, K = 1, 2, ... until it
     succeeds; every failing run must report OUT_OF_MEMORY.  Returns how many
     allocations the call makes."""
@@ -121,19 +121,19 @@ def _fail_every_allocation(byo, monkeypatch, call, max_k=64):
 
 
 def test_build_allocation_failures_release_memory(byo, monkeypatch):
-    n, src, dst = graphgen.rmat_small(18, 16, 4242)
+    n, src, dst = graphgen.rmat_small(16, 16, 4242)
     ref = oracle.csr_build(n, src, dst)
     s_d, d_d = dev(src), dev(dst)
     for flags in (byo.BYO_CSR | byo.BYO_SYMMETRIZE, byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE):
         byo.Graph(n, s_d, d_d, flags).close()  # warm the scratch pool
         before = _free_bytes()
-        for _ in range(3):
+        for _ in range(2):
             made = []
             allocs = _fail_every_allocation(byo, monkeypatch, lambda: made.append(byo.Graph(n, s_d, d_d, flags)))
             assert allocs >= 3
             for g in made:
                 g.close()
-        # the failed builds leaked nothing: the CSR alone is ~67 MB
+        # the failed builds leaked nothing (each failed build held up to ~17 MB of CSR)
         assert before - _free_bytes() < (8 << 20)
         with byo.Graph(n, s_d, d_d, flags) as g:
             off, col = byo.byo_graph_export_csr(g.handle)
@@ -196,4 +196,4 @@ def test_batch_update_allocation_failures(byo, monkeypatch):
             if not failed:
                 break
         k += 1
-        assert k < 80
+        assert k < 2000

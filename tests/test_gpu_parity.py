@@ -373,3 +373,35 @@ def test_mlp_train_and_predict(byo):
     assert np.array_equal(pred[clear], np.argmax(logits, axis=1)[clear])
     assert np.mean(pred == y) > 0.9
     byo.byo_mlp_destroy(m)
+
+
+# ----------------------------------------------------------------------------- betweenness
+
+def _bc_check(byo, ref, g, s):
+    lv, sigma, delta = byo.byo_bc(g.handle, s)
+    wl, ws, wd = oracle.bc(ref, s)
+    assert np.array_equal(host_u32(lv), wl)
+    gs, gd = sigma.cpu().numpy(), delta.cpu().numpy()
+    exact = ws < 2.0 ** 53            # path counts are integers, exact in FP64 below 2^53
+    assert np.array_equal(gs[exact], ws[exact])
+    assert np.all(np.abs(gs[~exact] - ws[~exact]) <= 1e-12 * ws[~exact])
+    assert np.all(np.abs(gd - wd) <= 1e-12 * np.maximum(np.abs(wd), 1.0))
+
+
+def test_bc_sigma_and_delta(byo, case):
+    name, n, src, dst, ref, g = case
+    if n == 0:
+        return
+    deg = np.diff(ref.off.astype(np.int64))
+    for s in [int(np.argmax(deg)), int(graphgen.pick_sources(n, src, dst, 1, 9)[0]) if ref.m else 0]:
+        _bc_check(byo, ref, g, s)
+
+
+def test_bc_dynamic_container_and_invalid_source(byo):
+    n, src, dst = graphgen.rmat_small(12, 16, 33)
+    ref = oracle.csr_build(n, src, dst)
+    with byo.Graph(n, dev_u32(src), dev_u32(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE) as g:
+        _bc_check(byo, ref, g, int(graphgen.pick_sources(n, src, dst, 1, 5)[0]))
+        with pytest.raises(byo.ByoError) as e:
+            byo.byo_bc(g.handle, n)
+        assert e.value.status == byo.BYO_ERR_INVALID_ARG
