@@ -23,7 +23,7 @@ pull levels.  Byte counts are the method's (what the algorithm must move, from
 its outputs), never a kernel's own counters.
 
   python bench.py [--gpus N --steps K --warmup W --workload rmat25 --sources 8]
-  python bench.py --workload batched | dynamic
+  python bench.py --workload batched | dynamic | ablation
   python bench.py --impl reference ...   # the serial CPU oracle, bounded sample
 
 N > 1 (torchrun, one rank per GPU) runs independent replicas: the path does not
@@ -730,6 +730,53 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
     g.close()
 
 
+# ----------------------------------------------------------------------------- API ablation
+
+def run_ablation(args, byo, torch):
+    """The paper's API-components study (Section 6.3) on the GPU path: BFS
+    from the benchmark sources with the full API, without the early-exit map
+    (pull iterations read whole lists), without the parallel map (a list is
+    only ever walked by one thread) and without both, on RMAT-22 and the grid
+    (heuristic schedule).  Results are identical; only the time changes."""
+    import graphgen
+    stream = torch.cuda.current_stream()
+    out = {}
+    variants = {"full": 0, "no_early_exit": byo.BYO_SCHED_NO_EARLY_EXIT,
+                "sequential_maps": byo.BYO_SCHED_SEQUENTIAL_MAPS,
+                "neither": byo.BYO_SCHED_NO_EARLY_EXIT | byo.BYO_SCHED_SEQUENTIAL_MAPS}
+    for name in ("rmat22", "grid"):
+        n, src, dst = graphgen.workload(name)
+        srcs = graphgen.pick_sources(n, src, dst, args.sources, graphgen.SEEDS[name] + 1)
+        flags = byo.BYO_CSR | byo.BYO_SYMMETRIZE | (byo.BYO_OFFSETS64 if name.startswith("rmat") else 0)
+        g = byo.Graph(n, dev_u32(torch, src), dev_u32(torch, dst), flags)
+        lv = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+        par = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+        ref = None
+        res = {}
+        for vname, fl in variants.items():
+            sp = byo.make_sched(byo.BYO_SCHED_HEURISTIC, flags=fl)
+            byo.byo_bfs(g.handle, srcs, lv, par, sp)
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = lv.clone()
+            same = bool(torch.equal(lv, ref))
+            times = []
+            for _ in range(max(1, args.sched_reps)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                byo.byo_bfs(g.handle, srcs, lv, par, sp)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            res[vname] = {"median_ms": round(statistics.median(times), 3), "levels_identical": same}
+        for vname in variants:
+            res[vname]["slowdown"] = round(res[vname]["median_ms"] / res["full"]["median_ms"], 3)
+        out[name] = res
+        g.close()
+    print(json.dumps({"metric": "BFS time without API components (Section 6.3 ablation)", "unit": "ms",
+                      "sources": args.sources, "sched": "heuristic", "results": out}), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -766,6 +813,9 @@ def main():
         return
     if args.workload == "dynamic":
         run_dynamic(args, byo, torch)
+        return
+    if args.workload == "ablation":
+        run_ablation(args, byo, torch)
         return
 
     def barrier():

@@ -45,6 +45,7 @@ typedef enum byo_status {
 #define BYO_DYNAMIC 0x2u    /* dynamic blocked-adjacency container (batch updates) */
 #define BYO_SYMMETRIZE 0x4u /* store every input pair (u,v) also as (v,u) */
 #define BYO_OFFSETS64 0x8u  /* CSR offsets as uint64 even when m < 2^32 */
+#define BYO_DYN_NO_INLINE 0x10u /* BYO_DYNAMIC without the inline head: every list in pool blocks */
 
 typedef struct byo_graph byo_graph;
 
@@ -56,7 +57,9 @@ const char* byo_last_error(void);
  * BYO_CSR builds the static CSR; BYO_DYNAMIC the blocked adjacency (a 64-byte
  * record per vertex with up to 12 neighbours inline -- the inline optimisation
  * of Section 4.1 -- else a run of 128-byte blocks from a device pool), which
- * accepts byo_insert_batch / byo_delete_batch.
+ * accepts byo_insert_batch / byo_delete_batch.  BYO_DYN_NO_INLINE (with
+ * BYO_DYNAMIC only) keeps every non-empty list in pool blocks, for the
+ * inline-head ablation.
  * Follows the graph model of Section 3 (vertices 0..n-1, a neighbour SET per
  * vertex, Section 3.1) and the CSR layout named in Section 4.2: duplicate
  * pairs collapse, self-loops are dropped, neighbours are stored ascending.
@@ -70,6 +73,14 @@ const char* byo_last_error(void);
  */
 byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t k, uint32_t flags,
                            void* stream, byo_graph** out);
+
+/* Bytes the container itself occupies (the space measure of the paper's
+ * container comparison, Section 6.5): for the CSR, the offsets and the
+ * neighbour ids ((n+1) x 4 or 8 + 4m); for the dynamic container, the 64-byte
+ * vertex records and the 128-byte blocks of the runs its lists hold (free pool
+ * capacity is not counted).  Library scratch is not included.  Synchronises
+ * the stream.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+byo_status byo_space(const byo_graph* g, uint64_t* host_bytes, void* stream);
 
 /* Free a handle and everything it owns (NULL is accepted).  Synchronises the device. */
 byo_status byo_graph_destroy(byo_graph* g);
@@ -132,7 +143,20 @@ typedef struct byo_sched {
   float beta;          /* heuristic: pull -> push when frontier vertices < n / beta */
   const byo_mlp* mlp;  /* LEARNED only */
   uint32_t action;     /* FIXED only: 0 .. BYO_NUM_ACTIONS-1 */
+  uint32_t flags;      /* BYO_SCHED_NO_EARLY_EXIT | BYO_SCHED_SEQUENTIAL_MAPS (API ablations) */
 } byo_sched;
+
+/* API ablations (Section 6.3 measures BYO without the early-exit map and
+ * without the parallel map): results are the same, only the work changes.
+ *   BYO_SCHED_NO_EARLY_EXIT    dense (pull) iterations read every neighbour of
+ *                              an unvisited vertex instead of stopping at the
+ *                              first one in the frontier (the parent is still
+ *                              that first one);
+ *   BYO_SCHED_SEQUENTIAL_MAPS  a vertex's neighbour list is only ever walked
+ *                              by one thread (no warp- or CTA-wide map of one
+ *                              list, no single-CTA push levels). */
+#define BYO_SCHED_NO_EARLY_EXIT 0x1u
+#define BYO_SCHED_SEQUENTIAL_MAPS 0x2u
 
 /* ------------------------------------------------------------------------ */
 /* Schedule network (not in the paper: it only picks among equivalent       */
@@ -169,7 +193,7 @@ byo_status byo_mlp_train(byo_mlp* m, const float* X, const int32_t* y, const flo
 /* actions[i] = argmax of the network output for X[i] (device arrays). */
 byo_status byo_mlp_predict(const byo_mlp* m, const float* X, uint32_t B, int32_t* actions, void* stream);
 
-/* Defaults: HEURISTIC, thr_thread 16, thr_warp 1024, alpha 15, beta 18, action 1. */
+/* Defaults: HEURISTIC, thr_thread 16, thr_warp 1024, alpha 15, beta 18, action 1, flags 0. */
 byo_sched byo_sched_default(void);
 
 /*

@@ -30,6 +30,7 @@ BYO_CSR = 0x1
 BYO_DYNAMIC = 0x2
 BYO_SYMMETRIZE = 0x4
 BYO_OFFSETS64 = 0x8
+BYO_DYN_NO_INLINE = 0x10
 
 BYO_SCHED_HEURISTIC = 0
 BYO_SCHED_LEARNED = 1
@@ -37,6 +38,8 @@ BYO_SCHED_PUSH = 2
 BYO_SCHED_PULL = 3
 BYO_SCHED_FIXED = 4
 BYO_NUM_ACTIONS = 5
+BYO_SCHED_NO_EARLY_EXIT = 0x1
+BYO_SCHED_SEQUENTIAL_MAPS = 0x2
 
 
 class ByoError(RuntimeError):
@@ -48,7 +51,7 @@ class ByoError(RuntimeError):
 class byo_sched(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("thr_thread", ctypes.c_uint32), ("thr_warp", ctypes.c_uint32),
                 ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("mlp", ctypes.c_void_p),
-                ("action", ctypes.c_uint32)]
+                ("action", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class byo_bfs_iter(ctypes.Structure):
@@ -73,6 +76,7 @@ SIGNATURES = [
     ("byo_last_error", ctypes.c_char_p, []),
     ("byo_graph_build", _st, [_u32, _vp, _vp, _u64, _u32, _vp, ctypes.POINTER(_vp)]),
     ("byo_graph_destroy", _st, [_vp]),
+    ("byo_space", _st, [_vp, ctypes.POINTER(_u64), _vp]),
     ("byo_num_vertices", _st, [_vp, ctypes.POINTER(_u32)]),
     ("byo_num_edges", _st, [_vp, ctypes.POINTER(_u64)]),
     ("byo_degree", _st, [_vp, _vp, _u64, _vp, _vp]),
@@ -179,6 +183,13 @@ def byo_graph_destroy(g: int) -> None:
     _check(load().byo_graph_destroy(g))
 
 
+def byo_space(g: int, stream=None) -> int:
+    """Bytes the container occupies (CSR arrays, or records + held pool blocks)."""
+    v = _u64()
+    _check(load().byo_space(g, ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
 def byo_num_vertices(g: int) -> int:
     v = _u32()
     _check(load().byo_num_vertices(g, ctypes.byref(v)))
@@ -231,8 +242,8 @@ def byo_sched_default() -> byo_sched:
 
 
 def make_sched(mode: int = BYO_SCHED_HEURISTIC, thr_thread: int = 16, thr_warp: int = 1024, alpha: float = 15.0,
-               beta: float = 18.0, mlp: int | None = None, action: int = 1) -> byo_sched:
-    return byo_sched(mode, thr_thread, thr_warp, alpha, beta, mlp, action)
+               beta: float = 18.0, mlp: int | None = None, action: int = 1, flags: int = 0) -> byo_sched:
+    return byo_sched(mode, thr_thread, thr_warp, alpha, beta, mlp, action, flags)
 
 
 def byo_bfs(g: int, sources, levels: torch.Tensor | None = None, parents: torch.Tensor | None = None,

@@ -221,6 +221,27 @@ __device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, const Workers& wk,
   }
   // thread bin: 32 vertices per warp, their edges walked 32 at a time
   const uint64_t t1 = S.pre[bt + 1];
+  if (a.sp.flags & BYO_SCHED_SEQUENTIAL_MAPS) {
+    // ablation: every lane walks its own vertex's list, one id per step
+    for (uint64_t jb = (uint64_t)gwarp * 32; jb < t1; jb += (uint64_t)nwarps * 32) {
+      const uint64_t j = jb + lane;
+      uint32_t u = 0;
+      Seg s{nullptr, 0};
+      if (j < t1) {
+        const int b = find_bucket(S.pre, 0, bt, j);
+        u = frontier_vertex(a, S, b, j - S.pre[b]);
+        s = a.g.seg(u);
+      }
+      const uint32_t kmax = __reduce_max_sync(0xFFFFFFFFu, s.len);
+      for (uint32_t k = 0; k < kmax; ++k) {
+        const bool ok = k < s.len;
+        const uint32_t v = ok ? __ldg(s.p + k) : 0u;
+        if (ok) ++acc_scan;
+        claim_emit<G, kParents>(a, S, ok, v, u, L + 1, nxt, acc_deg);
+      }
+    }
+    return;
+  }
   for (uint64_t jb = (uint64_t)gwarp * 32; jb < t1; jb += (uint64_t)nwarps * 32) {
     uint64_t j = jb + lane;
     uint32_t u = 0;
@@ -321,12 +342,15 @@ constexpr uint32_t kPullDefer = 32;
 struct PullDefer {
   uint32_t v[kPullDefer];
   uint32_t from[kPullDefer];  // first id (index in the list) not scanned yet
+  uint32_t par[kPullDefer];   // no early exit: the first frontier neighbour already found, else INF
 };
 
 template <typename G, bool kParents>
 __device__ void pull_long(const BfsArgs<G>& a, const BfsShared& S, uint32_t* fbn, const uint32_t* fb,
-                          PullDefer& D, uint32_t cnt, uint32_t L, int nxt, uint64_t& acc_deg, uint64_t& acc_scan) {
+                          PullDefer& D, uint32_t cnt, uint32_t L, int nxt, bool no_exit, uint64_t& acc_deg,
+                          uint64_t& acc_scan) {
   const uint32_t lane = lane_id();
+  uint32_t sink = 0;
   for (uint32_t d = 0; d < cnt; ++d) {
     const uint32_t v = D.v[d];
     const Seg sg = a.g.seg(v);
@@ -334,28 +358,28 @@ __device__ void pull_long(const BfsArgs<G>& a, const BfsShared& S, uint32_t* fbn
     const uint32_t head = (uint32_t)(sg.p - al);
     const uint32_t end = head + sg.len;
     const uint32_t from = head + D.from[d];
-    uint32_t got = kInf;
+    uint32_t got = D.par[d];
     for (uint32_t i0 = from & ~3u; i0 < end; i0 += 128) {
       const uint32_t i = i0 + lane * 4;
       uint32_t hit = kInf;
       if (i < end) {
         const uint4 q = ld_nc_v4(al + i);
         const uint32_t x[4] = {q.x, q.y, q.z, q.w};
+        sink ^= q.x ^ q.w;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const uint32_t idx = i + c;
-          if (hit == kInf && idx >= from && idx < end && in_frontier(fb, x[c])) hit = x[c];
+          if (hit == kInf && got == kInf && idx >= from && idx < end && in_frontier(fb, x[c])) hit = x[c];
         }
       }
       const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit != kInf);
       if (lane == 0) acc_scan += min(end, i0 + 128) - max(from, i0);  // upper bound of ids read
-      if (hm) {
-        got = __shfl_sync(0xFFFFFFFFu, hit, __ffs(hm) - 1);
-        break;
-      }
+      if (hm) got = __shfl_sync(0xFFFFFFFFu, hit, __ffs(hm) - 1);
+      if (got != kInf && !no_exit) break;  // without the ablation: stop at the first frontier neighbour
     }
     pull_emit<G, kParents>(a, S, fbn, lane == 0 && got != kInf, v, got, sg.len, L, nxt, acc_deg);
   }
+  asm volatile("" ::"r"(sink));
 }
 
 template <typename G, bool kParents>
@@ -390,6 +414,10 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
   const uint32_t* al = nullptr;
   uint32_t head = 0, end = 0, i = 0, len = 0;
   bool fresh = false;           // v was just taken: its list location is not loaded yet
+  const bool no_exit = (a.sp.flags & BYO_SCHED_NO_EARLY_EXIT) != 0;
+  const bool seq = (a.sp.flags & BYO_SCHED_SEQUENTIAL_MAPS) != 0;
+  uint32_t hit_par = kInf;      // no early exit: the first frontier neighbour found so far
+  uint32_t sink = 0;
   while (true) {
     // free lanes take pending vertices, opening words as needed
     uint32_t freeL = __ballot_sync(0xFFFFFFFFu, v == kInf);
@@ -442,7 +470,7 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
     bool found = false, done = false, defer_it = false;
     uint32_t par = kInf;
     if (active) {
-      if (i < end) {
+      if (i < end && !(no_exit && hit_par != kInf)) {
         const uint4 q0 = ld_nc_v4(al + i);
         const uint4 q1 = i + 4 < end ? ld_nc_v4(al + i + 4) : make_uint4(0u, 0u, 0u, 0u);
         const uint32_t x[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
@@ -463,9 +491,26 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
           acc_scan += (end < i + 8 ? end : i + 8) - lo;
         }
         i += 8;
+      } else if (i < end) {
+        // no early exit (ablation): the rest of the list is read all the same
+        const uint4 q0 = ld_nc_v4(al + i);
+        const uint4 q1 = i + 4 < end ? ld_nc_v4(al + i + 4) : make_uint4(0u, 0u, 0u, 0u);
+        sink ^= q0.x ^ q0.y ^ q0.z ^ q0.w ^ q1.x ^ q1.y ^ q1.z ^ q1.w;
+        acc_scan += (end < i + 8 ? end : i + 8) - (head > i ? head : i);
+        i += 8;
       }
-      done = found || i >= end;
-      defer_it = !done && i >= head + kPullThreadMax;
+      if (no_exit) {
+        if (found && hit_par == kInf) hit_par = par;
+        found = false;
+        done = i >= end;
+        if (done && hit_par != kInf) {
+          found = true;
+          par = hit_par;
+        }
+      } else {
+        done = found || i >= end;
+      }
+      defer_it = !done && !seq && i >= head + kPullThreadMax;
     }
     pull_emit<G, kParents>(a, S, fbn, found, v, par, len, L, nxt, acc_deg);
     // long scans go to the warp's deferred list (scanned when it fills up,
@@ -474,7 +519,7 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
     if (dm) {
       if (ndef + __popc(dm) > kPullDefer) {
         __syncwarp();
-        pull_long<G, kParents>(a, S, fbn, fb, D, ndef, L, nxt, acc_deg, acc_scan);
+        pull_long<G, kParents>(a, S, fbn, fb, D, ndef, L, nxt, no_exit, acc_deg, acc_scan);
         ndef = 0;
         __syncwarp();
       }
@@ -482,13 +527,18 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
         const uint32_t slot = ndef + __popc(dm & lanemask_lt());
         D.v[slot] = v;
         D.from[slot] = i - head;
+        D.par[slot] = hit_par;
       }
       ndef += __popc(dm);
       __syncwarp();
     }
-    if (done || defer_it) v = kInf;
+    if (done || defer_it) {
+      v = kInf;
+      hit_par = kInf;
+    }
   }
-  if (ndef) pull_long<G, kParents>(a, S, fbn, fb, D, ndef, L, nxt, acc_deg, acc_scan);
+  if (ndef) pull_long<G, kParents>(a, S, fbn, fb, D, ndef, L, nxt, no_exit, acc_deg, acc_scan);
+  asm volatile("" ::"r"(sink));  // the ablation's reads are kept
 }
 
 // warp sum of v into a shared-memory accumulator of the CTA

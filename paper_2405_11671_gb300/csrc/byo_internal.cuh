@@ -128,6 +128,8 @@ byo_status sort_unique_pairs(uint32_t n, const uint32_t* src, const uint32_t* ds
 byo_status rebuild_buckets(byo_graph* g, cudaStream_t s);
 // Fill g->dyn from the CSR just built in g (then releases the CSR arrays).
 byo_status dyn_from_csr(byo_graph* g, cudaStream_t s);
+// Bytes of a dynamic container's records and held pool blocks (synchronises).
+byo_status dyn_space(const byo_graph* g, uint64_t* host_bytes, cudaStream_t s);
 unsigned grid_for(uint64_t work, int threads);
 }  // namespace byo
 

@@ -89,13 +89,14 @@ struct DynView {
   uint64_t m;
   const DynVertex* vtx;
   const uint32_t* pool;
+  uint32_t icap;  // lists of at most icap ids are inline (kInline, or 0 without the inline head)
 
   __device__ __forceinline__ uint32_t num_vertices() const { return n; }
   __device__ __forceinline__ uint64_t num_edges() const { return m; }
   __device__ __forceinline__ uint32_t degree(uint32_t v) const { return __ldg(&vtx[v].deg); }
   __device__ __forceinline__ Seg seg(uint32_t v) const {
     uint32_t d = __ldg(&vtx[v].deg);
-    const uint32_t* p = d <= kInline ? vtx[v].inl : pool + __ldg(&vtx[v].run) * kBlockIds;
+    const uint32_t* p = d <= icap ? vtx[v].inl : pool + __ldg(&vtx[v].run) * kBlockIds;
     return Seg{p, d};
   }
   template <typename F>
@@ -122,9 +123,10 @@ struct DynStore {
   uint32_t* stacks[kClasses] = {nullptr};  // free runs per class
   uint64_t stack_cap[kClasses] = {0};
   long long* tops = nullptr;       // kClasses stack tops (device)
+  uint32_t icap = kInline;         // inline capacity: kInline, or 0 (BYO_DYN_NO_INLINE)
 };
 
-inline DynView dyn_view(const byo_graph* g) { return DynView{g->n, g->m, g->dyn->vtx, g->dyn->pool}; }
+inline DynView dyn_view(const byo_graph* g) { return DynView{g->n, g->m, g->dyn->vtx, g->dyn->pool, g->dyn->icap}; }
 
 // Call f with the device view of g's container.
 template <typename F>

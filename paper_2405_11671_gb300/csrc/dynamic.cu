@@ -58,16 +58,17 @@ __device__ __forceinline__ uint32_t lower_bound(const uint32_t* a, uint32_t len,
 
 // ---------------------------------------------------------------- initial load
 template <typename OffT>
-__global__ void dyn_blocks_kernel(const OffT* __restrict__ off, uint32_t n, uint32_t* blocks) {
+__global__ void dyn_blocks_kernel(const OffT* __restrict__ off, uint32_t n, uint32_t icap, uint32_t* blocks) {
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t d = (uint32_t)(off[v + 1] - off[v]);
-    blocks[v] = d <= kInline ? 0u : (1u << run_class(d));
+    blocks[v] = d <= icap ? 0u : (1u << run_class(d));
   }
 }
 
 template <typename OffT>
 __global__ void dyn_load_kernel(const OffT* __restrict__ off, const uint32_t* __restrict__ col, uint32_t n,
-                                const uint64_t* __restrict__ first_block, DynVertex* vtx, uint32_t* pool) {
+                                uint32_t icap, const uint64_t* __restrict__ first_block, DynVertex* vtx,
+                                uint32_t* pool) {
   const uint32_t lane = lane_id();
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -75,7 +76,7 @@ __global__ void dyn_load_kernel(const OffT* __restrict__ off, const uint32_t* __
     uint64_t b = off[v];
     uint32_t d = (uint32_t)(off[v + 1] - b);
     DynVertex* r = vtx + v;
-    if (d <= kInline) {
+    if (d <= icap) {
       if (lane < kInline) r->inl[lane] = lane < d ? col[b + lane] : kInf;
       if (lane == 0) {
         r->deg = d;
@@ -188,8 +189,9 @@ __global__ void merge_kernel(DynView g, const uint32_t* __restrict__ cols, const
 // fix-up kernel clamps it.  Frees happen in a later kernel (no concurrent
 // push and pop).
 __global__ void alloc_kernel(DynVertex* vtx, const uint32_t* __restrict__ seg_v, const uint32_t* __restrict__ newdeg,
-                             uint64_t A, uint32_t* const* stacks, long long* tops, unsigned long long* bump,
-                             uint64_t* new_run, uint32_t* new_cls, uint64_t* free_run, uint32_t* free_cls) {
+                             uint64_t A, uint32_t icap, uint32_t* const* stacks, long long* tops,
+                             unsigned long long* bump, uint64_t* new_run, uint32_t* new_cls, uint64_t* free_run,
+                             uint32_t* free_cls) {
   for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x) {
     const DynVertex r = vtx[seg_v[a]];
     const uint32_t nd = newdeg[a];
@@ -197,7 +199,7 @@ __global__ void alloc_kernel(DynVertex* vtx, const uint32_t* __restrict__ seg_v,
     uint64_t orun = r.run;
     free_run[a] = ~0ull;
     free_cls[a] = kNoRun;
-    if (nd <= kInline) {
+    if (nd <= icap) {
       new_cls[a] = kNoRun;
       new_run[a] = 0;
       if (oc != kNoRun) {
@@ -232,7 +234,7 @@ __global__ void clamp_tops_kernel(long long* tops) {
 __global__ void copyback_kernel(DynVertex* vtx, uint32_t* pool, const uint32_t* __restrict__ seg_v,
                                 const uint32_t* __restrict__ newdeg, const uint64_t* __restrict__ new_run,
                                 const uint32_t* __restrict__ new_cls, const uint64_t* __restrict__ toff,
-                                const uint32_t* __restrict__ buf, uint64_t A) {
+                                const uint32_t* __restrict__ buf, uint64_t A, uint32_t icap) {
   const uint32_t lane = lane_id();
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -240,7 +242,7 @@ __global__ void copyback_kernel(DynVertex* vtx, uint32_t* pool, const uint32_t* 
     DynVertex* r = vtx + seg_v[a];
     const uint32_t nd = newdeg[a];
     const uint32_t* src = buf + toff[a];
-    if (nd <= kInline) {
+    if (nd <= icap) {
       if (lane < kInline) r->inl[lane] = lane < nd ? src[lane] : kInf;
     } else {
       uint32_t* dst = pool + new_run[a] * kBlockIds;
@@ -250,7 +252,7 @@ __global__ void copyback_kernel(DynVertex* vtx, uint32_t* pool, const uint32_t* 
     if (lane == 0) {
       r->deg = nd;
       r->cls = new_cls[a];
-      r->run = nd <= kInline ? 0 : new_run[a];
+      r->run = nd <= icap ? 0 : new_run[a];
     }
   }
 }
@@ -267,10 +269,10 @@ __global__ void free_kernel(const uint64_t* __restrict__ free_run, const uint32_
 }
 
 // worst-case pool blocks a batch may bump-allocate
-__global__ void need_kernel(const uint32_t* __restrict__ newdeg, uint64_t A, unsigned long long* need) {
+__global__ void need_kernel(const uint32_t* __restrict__ newdeg, uint64_t A, uint32_t icap, unsigned long long* need) {
   unsigned long long s = 0;
   for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x)
-    if (newdeg[a] > kInline) s += 1ull << run_class(newdeg[a]);
+    if (newdeg[a] > icap) s += 1ull << run_class(newdeg[a]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
   if (lane_id() == 0 && s) atomicAdd(need, s);
@@ -309,7 +311,7 @@ byo_status load_from_csr(byo_graph* g, DynStore* d, cudaStream_t s) {
   byo_status st = tmp_alloc_t(&blocks, g->n + 1ull, s, "run sizes");
   if (st == BYO_OK) st = tmp_alloc_t(&first, g->n + 1ull, s, "run starts");
   if (st == BYO_OK) {
-    dyn_blocks_kernel<OffT><<<grid_for(g->n, 256), 256, 0, s>>>(off, g->n, blocks);
+    dyn_blocks_kernel<OffT><<<grid_for(g->n, 256), 256, 0, s>>>(off, g->n, d->icap, blocks);
     note_launch();
     st = scan_u32_to_u64(blocks, first, g->n, &total, s);
   }
@@ -323,8 +325,8 @@ byo_status load_from_csr(byo_graph* g, DynStore* d, cudaStream_t s) {
     cudaMemsetAsync(d->tops, 0, sizeof(long long) * kClasses, s);
     cudaMemcpyAsync(d->bump, &total, sizeof(total), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(d->vtx + g->n, 0, sizeof(DynVertex), s);
-    dyn_load_kernel<OffT><<<grid_for((uint64_t)g->n * 32, 256), 256, 0, s>>>(off, g->col, g->n, first, d->vtx,
-                                                                               d->pool);
+    dyn_load_kernel<OffT><<<grid_for((uint64_t)g->n * 32, 256), 256, 0, s>>>(off, g->col, g->n, d->icap, first,
+                                                                               d->vtx, d->pool);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -398,7 +400,7 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
   if (st == BYO_OK) st = tmp_alloc_t(&need, 1, s, "need");
   if (st == BYO_OK) {
     cudaMemsetAsync(need, 0, sizeof(unsigned long long), s);
-    need_kernel<<<grid_for(A, 256), 256, 0, s>>>(newdeg, A, need);
+    need_kernel<<<grid_for(A, 256), 256, 0, s>>>(newdeg, A, d->icap, need);
     note_launch();
     unsigned long long hneed = 0, hbump = 0;
     cudaError_t e = cudaMemcpyAsync(&hneed, need, sizeof(hneed), cudaMemcpyDeviceToHost, s);
@@ -416,11 +418,11 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
   if (st == BYO_OK) {
     cudaMemcpyAsync(d_stacks, d->stacks, sizeof(uint32_t*) * kClasses, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_cap, d->stack_cap, sizeof(uint64_t) * kClasses, cudaMemcpyHostToDevice, s);
-    alloc_kernel<<<grid_for(A, 256), 256, 0, s>>>(d->vtx, seg_v, newdeg, A, d_stacks, d->tops, d->bump, new_run,
-                                                   new_cls, free_run, free_cls);
+    alloc_kernel<<<grid_for(A, 256), 256, 0, s>>>(d->vtx, seg_v, newdeg, A, d->icap, d_stacks, d->tops, d->bump,
+                                                   new_run, new_cls, free_run, free_cls);
     clamp_tops_kernel<<<1, 32, 0, s>>>(d->tops);
     copyback_kernel<<<grid_for(A * 32, 256), 256, 0, s>>>(d->vtx, d->pool, seg_v, newdeg, new_run, new_cls, toff, buf,
-                                                           A);
+                                                           A, d->icap);
     free_kernel<<<grid_for(A, 256), 256, 0, s>>>(free_run, free_cls, A, d_stacks, d->tops, d_cap);
     note_launch(4);
     long long hdelta = 0;
@@ -461,12 +463,40 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
 
 }  // namespace
 
+__global__ void dyn_space_kernel(const DynVertex* __restrict__ vtx, uint32_t n, unsigned long long* blocks) {
+  unsigned long long b = 0;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = vtx[v].cls;
+    if (c != kNoRun) b += 1ull << c;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+  if (lane_id() == 0 && b) atomicAdd(blocks, b);
+}
+
+byo_status dyn_space(const byo_graph* g, uint64_t* host_bytes, cudaStream_t s) {
+  unsigned long long* blocks = nullptr;
+  BYO_RETURN_IF(tmp_alloc_t(&blocks, 1, s, "space counter"));
+  unsigned long long hb = 0;
+  cudaMemsetAsync(blocks, 0, sizeof(unsigned long long), s);
+  dyn_space_kernel<<<grid_for(g->n, 256), 256, 0, s>>>(g->dyn->vtx, g->n, blocks);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, blocks, sizeof(hb), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  tmp_free(blocks, s);
+  if (e != cudaSuccess) return cuda_status(e, "byo_space");
+  *host_bytes = sizeof(DynVertex) * ((uint64_t)g->n + 1) + (uint64_t)hb * kBlockIds * sizeof(uint32_t);
+  return BYO_OK;
+}
+
 byo_status dyn_from_csr(byo_graph* g, cudaStream_t s) {
   DynStore* d = new (std::nothrow) DynStore();
   if (!d) {
     set_error("host allocation failed");
     return BYO_ERR_OUT_OF_MEMORY;
   }
+  d->icap = (g->flags & BYO_DYN_NO_INLINE) ? 0u : kInline;
   byo_status st = dev_alloc_t(&d->vtx, g->n + 1ull, "vertex records");
   if (st == BYO_OK) st = dev_alloc_t(&d->bump, 1, "pool cursor");
   if (st == BYO_OK) st = dev_alloc_t(&d->tops, kClasses, "stack tops");

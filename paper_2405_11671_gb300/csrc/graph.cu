@@ -612,6 +612,7 @@ byo_sched byo_sched_default(void) {
   s.beta = 18.0f;
   s.mlp = nullptr;
   s.action = 1;
+  s.flags = 0;
   return s;
 }
 
@@ -625,6 +626,10 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
   *out = nullptr;
   if (k > 0 && (!src || !dst)) {
     set_error("byo_graph_build: NULL edge arrays with k = %llu", (unsigned long long)k);
+    return BYO_ERR_INVALID_ARG;
+  }
+  if ((flags & BYO_DYN_NO_INLINE) && !(flags & BYO_DYNAMIC)) {
+    set_error("byo_graph_build: BYO_DYN_NO_INLINE applies to BYO_DYNAMIC only");
     return BYO_ERR_INVALID_ARG;
   }
   if (!(flags & (BYO_CSR | BYO_DYNAMIC)) || (flags & BYO_CSR && flags & BYO_DYNAMIC)) {
@@ -668,6 +673,18 @@ byo_status byo_graph_destroy(byo_graph* g) {
   if (!g) return BYO_OK;
   cudaDeviceSynchronize();
   graph_free(g);
+  return BYO_OK;
+}
+
+byo_status byo_space(const byo_graph* g, uint64_t* host_bytes, void* stream) {
+  clear_error();
+  BYO_RETURN_IF(check_graph(g));
+  if (!host_bytes) {
+    set_error("byo_space: NULL output");
+    return BYO_ERR_INVALID_ARG;
+  }
+  if (g->dyn) return dyn_space(g, host_bytes, static_cast<cudaStream_t>(stream));
+  *host_bytes = (uint64_t)(g->n + 1ull) * (g->off64 ? 8u : 4u) + 4ull * g->m;
   return BYO_OK;
 }
 

@@ -253,6 +253,14 @@ byo_status sched_params(const byo_sched* s, SchedParams* out) {
     set_error("byo_sched: LEARNED needs a network");
     return BYO_ERR_INVALID_ARG;
   }
+  if (d.flags & ~(BYO_SCHED_NO_EARLY_EXIT | BYO_SCHED_SEQUENTIAL_MAPS)) {
+    set_error("byo_sched: unknown flags 0x%x", d.flags);
+    return BYO_ERR_INVALID_ARG;
+  }
+  if ((d.flags & BYO_SCHED_SEQUENTIAL_MAPS) && d.mode == BYO_SCHED_FIXED && d.action == (uint32_t)kActionSolo) {
+    set_error("byo_sched: the single-CTA action maps lists with many threads (BYO_SCHED_SEQUENTIAL_MAPS)");
+    return BYO_ERR_INVALID_ARG;
+  }
   out->mode = (int)d.mode;
   out->fixed_action = (int)d.action;
   out->bt = bt;
@@ -260,6 +268,7 @@ byo_status sched_params(const byo_sched* s, SchedParams* out) {
   out->alpha = d.alpha;
   out->beta = d.beta;
   out->w = d.mode == BYO_SCHED_LEARNED ? mlp_device_params(d.mlp) : nullptr;
+  out->flags = d.flags;
   return BYO_OK;
 }
 

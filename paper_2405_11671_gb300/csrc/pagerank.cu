@@ -511,7 +511,9 @@ byo_status run_pr(byo_graph* g, G view, float damping, uint32_t iters, float* ra
     uint64_t cap = (uint64_t)sm_count() * 8;
     bins.nbT = (uint32_t)(want < cap ? (want ? want : 1) : cap);
   }
-  CtaChunks hubs = make_cta_chunks(g, 11, 11);  // degrees >= 1024, chunks of <= 2048 ids
+  // degrees >= 1024 in chunks of at most 65,536 ids: a CTA sums a whole list
+  // (few partials and tickets), only the largest hubs are split over CTAs
+  CtaChunks hubs = make_cta_chunks(g, 11, 16);
   {
     uint64_t cap = (uint64_t)sm_count() * 8;
     bins.nbC = (uint32_t)(hubs.items < cap ? hubs.items : cap);

@@ -38,6 +38,7 @@ struct SchedParams {
   int bt, bw;  // log2 of thr_thread / thr_warp
   float alpha, beta;
   const float* w;  // MLP parameters (LEARNED): global on the host side, the CTA's staged copy in kernels
+  uint32_t flags;  // BYO_SCHED_NO_EARLY_EXIT | BYO_SCHED_SEQUENTIAL_MAPS
 };
 
 // A CTA's shared-memory copy of the network, read once per launch so that
@@ -91,6 +92,11 @@ __host__ __device__ inline void sched_feature_vector(const SchedFeatures& f, flo
 }
 
 __device__ __forceinline__ void sched_bins(const SchedParams& sp, int action, int* bt, int* bw) {
+  if (sp.flags & BYO_SCHED_SEQUENTIAL_MAPS) {  // every frontier vertex in the thread bin
+    *bt = kBuckets - 1;
+    *bw = kBuckets - 1;
+    return;
+  }
   switch (action) {
     case 2: *bt = 2; *bw = 7; break;
     case 3: *bt = 6; *bw = 12; break;
@@ -132,7 +138,7 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
   for (int k = 0; k < kHidden; ++k)
     a2[k & 3] = fmaf(W2[k * kHidden + lane], __shfl_sync(0xFFFFFFFFu, h1, k), a2[k & 3]);
   const float h2 = fmaxf((a2[0] + a2[1]) + (a2[2] + a2[3]), 0.0f);
-  const bool solo_ok = f.mf <= kSoloMaxEdges && f.nf <= kSoloMaxVertices;
+  const bool solo_ok = f.mf <= kSoloMaxEdges && f.nf <= kSoloMaxVertices && !(sp.flags & BYO_SCHED_SEQUENTIAL_MAPS);
   const bool pull_ok = sched_pull_allowed(sp, f);
   int best = -1;  // action 1 is always allowed
   float bestz = 0.0f;

@@ -77,8 +77,10 @@ def forced_sched(byo, action: int):
     return byo.make_sched(byo.BYO_SCHED_FIXED, 16, 1024, action=action)
 
 
-def time_actions(byo, g, sources, repeats: int = 2):
-    """Per-iteration device times of every forced action for each source.
+def time_actions(byo, g, sources, repeats: int = 3):
+    """Per-iteration device times of every forced action for each source: the
+    median over `repeats` traversals (after one untimed warm-up traversal), so
+    that the labels depend as little as possible on timing noise.
 
     Returns a list of (features [L, 12], times [L, NUM_ACTIONS] in ns,
     frontier edges [L], (|F|, frontier edges, unvisited edges, n) per level)."""
@@ -88,17 +90,17 @@ def time_actions(byo, g, sources, repeats: int = 2):
         feats, times, mf, stats = None, [], None, None
         for a in range(NUM_ACTIONS):
             sp = forced_sched(byo, a)
-            best = None
+            byo.byo_bfs(g, [int(s)], sched=sp, want_parents=False)
+            runs = []
             for _ in range(repeats):
                 byo.byo_bfs(g, [int(s)], sched=sp, want_parents=False)
                 tr = byo.byo_bfs_trace(g)
-                t = np.array([r.t_ns for r in tr], np.float64)
-                best = t if best is None else np.minimum(best, t)
+                runs.append(np.array([r.t_ns for r in tr], np.float64))
                 if feats is None:
                     feats = trace_features(tr, n, m)
                     mf = np.array([r.frontier_edges for r in tr], np.float64)
                     stats = [(r.frontier, r.frontier_edges, r.unvisited_edges, n) for r in tr]
-            times.append(best)
+            times.append(np.median(np.stack(runs), axis=0))
         out.append((feats, np.stack(times, axis=1), mf, stats))
     return out
 

@@ -47,4 +47,4 @@ def test_binding_struct_layouts():
     assert ctypes.sizeof(_byo.byo_bfs_iter) == 72
     assert _byo.byo_bfs_iter.t_ns.offset == 64
     assert ctypes.sizeof(_byo.byo_sched) == 40 and _byo.byo_sched.mlp.offset == 24
-    assert _byo.byo_sched.action.offset == 32
+    assert _byo.byo_sched.action.offset == 32 and _byo.byo_sched.flags.offset == 36

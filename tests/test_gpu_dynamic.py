@@ -151,3 +151,39 @@ def test_batch_errors(byo):
     assert e.value.status == byo.BYO_ERR_INVALID_ARG
     byo.byo_insert_batch(g.handle, dev([]), dev([]))  # empty batch is a no-op
     g.close()
+
+
+def test_inline_head_ablation_and_space(byo):
+    """The dynamic container without its inline head (every list in pool
+    blocks) holds the same lists and gives the same results; byo_space counts
+    the CSR arrays exactly, and for a freshly built dynamic container the
+    vertex records plus the power-of-two runs of 32-id blocks of the lists
+    longer than the inline capacity."""
+    n, src, dst = graphgen.rmat_small(13, 8, 77)
+    ref = oracle.csr_build(n, src, dst)
+    deg = np.diff(ref.off.astype(np.int64))
+
+    def runs(icap):
+        d = deg[deg > icap]
+        blocks = (d + 31) // 32
+        return int(np.sum(1 << np.ceil(np.log2(blocks)).astype(np.int64)))
+
+    with byo.Graph(n, dev(src), dev(dst)) as gc:
+        assert byo.byo_space(gc.handle) == (n + 1) * 4 + 4 * ref.m
+    got = {}
+    for flags, icap in ((byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE, 12),
+                        (byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE | byo.BYO_DYN_NO_INLINE, 0)):
+        with byo.Graph(n, dev(src), dev(dst), flags) as g:
+            assert byo.byo_space(g.handle) == 64 * (n + 1) + 128 * runs(icap)
+            off, col = byo.byo_graph_export_csr(g.handle)
+            assert np.array_equal(off.cpu().numpy().astype(np.uint64), ref.off)
+            assert np.array_equal(host(col), ref.col)
+            lv, _ = byo.byo_bfs(g.handle, [3])
+            assert np.array_equal(host(lv[0]), oracle.bfs(ref, 3)[0])
+            assert byo.byo_tc(g.handle) == oracle.tc(ref)
+            ins_s, ins_d = graphgen.rmat(13, 2000, 78)
+            byo.byo_insert_batch(g.handle, dev(ins_s), dev(ins_d))
+            got[icap] = byo.byo_graph_export_csr(g.handle)
+    assert torch.equal(got[12][0], got[0][0]) and torch.equal(got[12][1], got[0][1])
+    with pytest.raises(byo.ByoError):
+        byo.Graph(n, dev(src), dev(dst), byo.BYO_CSR | byo.BYO_DYN_NO_INLINE)

@@ -154,10 +154,14 @@ def test_empty_graph(byo):
 
 # ----------------------------------------------------------------------------- BFS
 
-SCHEDS = {"heuristic": (0, 16, 1024, 1), "push": (2, 16, 1024, 1), "pull": (3, 16, 1024, 1),
-          "push_thread_only": (2, 1 << 31, 1 << 31, 1), "push_cta_heavy": (2, 1, 2, 1),
-          "solo": (4, 16, 1024, 4), "solo_cta_heavy": (4, 1, 2, 4), "push_small_bins": (4, 16, 1024, 2),
-          "learned_random": (1, 16, 1024, 1)}
+# (mode, thr_thread, thr_warp, action, flags); flags 1 = no early exit, 2 = sequential maps (API ablations)
+SCHEDS = {"heuristic": (0, 16, 1024, 1, 0), "push": (2, 16, 1024, 1, 0), "pull": (3, 16, 1024, 1, 0),
+          "push_thread_only": (2, 1 << 31, 1 << 31, 1, 0), "push_cta_heavy": (2, 1, 2, 1, 0),
+          "solo": (4, 16, 1024, 4, 0), "solo_cta_heavy": (4, 1, 2, 4, 0), "push_small_bins": (4, 16, 1024, 2, 0),
+          "learned_random": (1, 16, 1024, 1, 0),
+          "pull_no_early_exit": (3, 16, 1024, 1, 1), "heuristic_no_early_exit": (0, 16, 1024, 1, 1),
+          "push_sequential": (2, 16, 1024, 1, 2), "pull_sequential": (3, 16, 1024, 1, 2),
+          "heuristic_both_ablations": (0, 16, 1024, 1, 3), "learned_random_sequential": (1, 16, 1024, 1, 2)}
 
 
 @pytest.fixture(scope="module")
@@ -170,8 +174,9 @@ def random_net(byo):
 @pytest.mark.parametrize("sched", sorted(SCHEDS))
 def test_bfs_levels_and_parents(byo, case, sched, random_net):
     name, n, src, dst, ref, g = case
-    mode, tt, tw, act = SCHEDS[sched]
-    sp = byo.make_sched(mode, tt, tw, mlp=random_net if mode == byo.BYO_SCHED_LEARNED else None, action=act)
+    mode, tt, tw, act, flags = SCHEDS[sched]
+    sp = byo.make_sched(mode, tt, tw, mlp=random_net if mode == byo.BYO_SCHED_LEARNED else None, action=act,
+                        flags=flags)
     srcs = _sources(n, src, dst, ref)
     lv, par = byo.byo_bfs(g.handle, srcs, sched=sp)
     for i, s in enumerate(srcs):
