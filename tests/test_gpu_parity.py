@@ -410,3 +410,20 @@ def test_bc_dynamic_container_and_invalid_source(byo):
         with pytest.raises(byo.ByoError) as e:
             byo.byo_bc(g.handle, n)
         assert e.value.status == byo.BYO_ERR_INVALID_ARG
+
+
+def test_pagerank_hub_split_over_chunks(byo):
+    # a hub of 150,000 neighbours is summed in several chunks (their partials
+    # folded by the last one) -- within the tolerance like every other vertex
+    k = 150000
+    n = k + 1
+    rng = np.random.default_rng(5)
+    extra = rng.integers(1, n, size=(40000, 2), dtype=np.int64)
+    src = np.concatenate([np.zeros(k, np.uint32), extra[:, 0].astype(np.uint32)])
+    dst = np.concatenate([np.arange(1, n, dtype=np.uint32), extra[:, 1].astype(np.uint32)])
+    ref = oracle.csr_build(n, src, dst)
+    with byo.Graph(n, dev_u32(src), dev_u32(dst)) as g:
+        p, _ = byo.byo_pagerank(g.handle, 0.85, 20)
+        w, _ = oracle.pagerank(ref, 0.85, 20)
+        got = p.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(got - w) / w) <= PR_MAX_REL and np.sum(np.abs(got - w)) <= PR_L1

@@ -6,8 +6,9 @@ on held-out graphs of the three workload shapes.  For every BFS level the
 device time of each of the five actions is measured with that action forced
 (frontiers do not depend on the schedule), and the per-level choices of the
 Beamer heuristic and of the network are scored by their regret: the time they
-lose over the best action of each level.  The network must lose no more than
-the heuristic (plus 5 % of the best total, for timing noise), and both must
+lose over the best action of each level.  Both choices are scored on the same
+timing table, so the comparison carries no run-to-run noise: the network's
+per-level total must not exceed the heuristic's on any shape, and both must
 give the same levels.
 """
 import os
@@ -73,7 +74,7 @@ def test_learned_schedule_regret(byo, shape):
             t_l += float(sum(t[i, c] for i, c in enumerate(cl)))
         print(f"\n{shape}: per-level time heuristic {t_h / 1e6:.3f} ms, learned {t_l / 1e6:.3f} ms "
               f"(gain {t_h / max(t_l, 1):.2f}x), best {best / 1e6:.3f} ms")
-        assert r_l <= r_h + 0.05 * best
+        assert t_l <= t_h and r_l <= r_h
     finally:
         g.close()
         byo.byo_mlp_destroy(net)
