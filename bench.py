@@ -289,6 +289,33 @@ def bfs_method_bytes(torch, off, col, lv, trace, off_bytes: int):
     return total, out
 
 
+def bc_method_bytes(torch, off, col, lv, off_bytes: int, chunk_edges=1 << 26):
+    """Bytes single-source betweenness must move after its BFS: every reached
+    vertex reads its list and the levels of its neighbours in both sweeps
+    (off + 8 deg each), the forward sweep reads the path counts of the
+    neighbours one level closer (8 each) and writes sigma (8), the backward
+    sweep reads sigma and delta of the neighbours one level deeper (16 each)
+    and writes delta (8); plus sigma/delta initialisation (16n) and the
+    grouping of the vertices by level (levels read twice, order written)."""
+    n = lv.numel()
+    L = lv.long() & INF
+    reached = L != INF
+    deg = (off[1:] - off[:-1]).long()
+    closer = 0
+    for v0, v1 in _vertex_chunks(torch, off, chunk_edges):
+        e0, e1 = int(off[v0]), int(off[v1])
+        if e1 == e0:
+            continue
+        rows = torch.repeat_interleave(torch.arange(v0, v1, device=L.device), deg[v0:v1])
+        nb = col[e0:e1].long() & INF
+        lr = L[rows]
+        closer += int(((lr != INF) & (lr > 0) & (L[nb] + 1 == lr)).sum())
+    r = int(reached.sum())
+    dsum = float(deg[reached].sum())
+    sweeps = 2.0 * (off_bytes * r + 8.0 * dsum)
+    return 16.0 * n + 8.0 * n + 4.0 * r + sweeps + 8.0 * closer + 8.0 * r + 16.0 * closer + 16.0 * r
+
+
 def level_bandwidth(levels, peak):
     """Bandwidth of the push and pull levels: the largest level of each
     direction (by bytes) and each direction's total bytes over total time."""
@@ -917,6 +944,31 @@ def main():
         bfs_lv += per_level
         examined[0] += sum(4.0 * r.edges_examined for r in tr)
         examined[1] += sum(x[2] for x in per_level)
+    # single-source betweenness from the first source (not part of the step):
+    # BFS + forward and backward sweeps, median of three calls
+    bc = None
+    if rank == 0:
+        s0 = int(srcs[0])
+        byo.byo_bc(g.handle, s0, levels[0])
+        torch.cuda.synchronize()
+        bt = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            byo.byo_bc(g.handle, s0, levels[0])
+            b.record(stream)
+            torch.cuda.synchronize()
+            bt.append(a.elapsed_time(b))
+        bc_ms = statistics.median(bt)
+        byo.byo_bfs(g.handle, [s0], levels[:1], parents[:1], byo.make_sched(byo.BYO_SCHED_HEURISTIC))
+        tr0 = byo.byo_bfs_trace(g.handle)
+        bfs_b, _ = bfs_method_bytes(torch, off_d, col_d, levels[0], tr0, off_bytes)
+        bc_b = bfs_b + bc_method_bytes(torch, off_d, col_d, levels[0], off_bytes)
+        deg_all = (off_d[1:] - off_d[:-1]).long()
+        comp_edges = int(deg_all[(levels[0].long() & INF) != INF].sum()) // 2
+        bc = {"source": s0, "ms": round(bc_ms, 3), "gteps": round(comp_edges / (bc_ms / 1e3) / 1e9, 3),
+              "roofline": roof_entry("bc (BFS + both sweeps)", bc_b, bc_ms, peak, peak_kind)}
+        del deg_all
     del off_d, col_d
     tot = sum(v[1] for v in prof.values()) or 1.0
     # the two intersection kernels of one triangle count are one unit of work
@@ -1051,6 +1103,8 @@ def main():
             line["schedules"] = sched_cmp
         if grid_cmp is not None:
             line["schedules_grid"] = grid_cmp
+        if bc is not None:
+            line["betweenness"] = bc
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

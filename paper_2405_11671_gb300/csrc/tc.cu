@@ -552,6 +552,99 @@ __device__ __forceinline__ uint32_t warp_count_group(const uint32_t* __restrict_
   return hits;
 }
 
+// 16-byte vector loads of the DAG (read-only during the count; the DAG
+// allocation is padded, so a vector that starts inside a list stays inside it)
+__device__ __forceinline__ uint4 ld_dag4(const uint32_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+
+// ids x[0..3] of a vector whose first id sits at list position `pos` (may be
+// negative at the list's start), counted if inside [0, len)
+template <typename Set>
+__device__ __forceinline__ uint32_t count_vec(const Set& set, uint4 q, int pos, int len) {
+  uint32_t h = 0;
+  h += set.contains(q.x) & (uint32_t)(pos >= 0 && pos < len);
+  h += set.contains(q.y) & (uint32_t)(pos + 1 >= 0 && pos + 1 < len);
+  h += set.contains(q.z) & (uint32_t)(pos + 2 >= 0 && pos + 2 < len);
+  h += set.contains(q.w) & (uint32_t)(pos + 3 >= 0 && pos + 3 < len);
+  return h;
+}
+
+constexpr uint32_t kWarpListMin = 1024;  // lists at least this long are walked by the whole warp
+constexpr int kVecU = 2;                 // vectors in flight per lane
+
+// warp_count_group for the light centres, whose partners' lists are mostly
+// short: the warp walks the lists dag_col[vb .. vb+len) held by its lanes
+// (len = 0 for lanes without a partner) and counts the ids the set contains.
+// Every list is read in aligned 16-byte vectors (4 ids).  Lists of kWarpListMin ids
+// or more are walked one at a time by the whole warp; all the others are
+// concatenated at vector granularity and walked together, each lane finding
+// the list its vector belongs to by a 5-step search over the lanes' prefix
+// sums, so the lists of a group are read in a few rounds instead of one round
+// each.
+template <typename Set>
+__device__ __forceinline__ uint32_t warp_count_group_vec(const uint32_t* __restrict__ dag_col, uint64_t vb,
+                                                         uint32_t len, const Set& set) {
+  const uint32_t lane = lane_id();
+  uint32_t hits = 0;
+  uint32_t longs = __ballot_sync(0xFFFFFFFFu, len >= kWarpListMin);
+  while (longs) {
+    const int l = __ffs(longs) - 1;
+    longs &= longs - 1;
+    const uint64_t b = __shfl_sync(0xFFFFFFFFu, vb, l);
+    const int ln = (int)__shfl_sync(0xFFFFFFFFu, len, l);
+    const uint32_t* al = dag_col + (b & ~3ull);
+    const int head = (int)(b & 3ull);
+    for (int v0 = 0; 4 * v0 < head + ln; v0 += 32 * 4) {
+      uint4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int vi = v0 + 32 * u + (int)lane;
+        q[u] = 4 * vi < head + ln ? ld_dag4(al + 4 * vi) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) hits += count_vec(set, q[u], 4 * (v0 + 32 * u + (int)lane) - head, ln);
+    }
+  }
+  const uint32_t slen = len >= kWarpListMin ? 0u : len;
+  const uint64_t a0 = vb & ~3ull;
+  const uint32_t head = (uint32_t)(vb - a0);
+  const uint32_t nv = slen ? (head + slen + 3) >> 2 : 0u;
+  uint32_t incl = nv;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  const uint32_t excl = incl - nv;
+  for (uint32_t e0 = 0; e0 < total; e0 += 32 * kVecU) {
+    uint4 q[kVecU];
+    int pos[kVecU], ln[kVecU];
+#pragma unroll
+    for (int u = 0; u < kVecU; ++u) {
+      const uint32_t e = e0 + 32 * u + lane;
+      int owner = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        int probe = owner + step;
+        uint32_t ex = __shfl_sync(0xFFFFFFFFu, excl, probe & 31);
+        if (probe < 32 && ex <= e) owner = probe;
+      }
+      const uint32_t oex = __shfl_sync(0xFFFFFFFFu, excl, owner);
+      const uint64_t oa = __shfl_sync(0xFFFFFFFFu, a0, owner);
+      const uint32_t oh = __shfl_sync(0xFFFFFFFFu, head, owner);
+      const uint32_t ol = __shfl_sync(0xFFFFFFFFu, slen, owner);
+      const uint32_t vi = e - oex;
+      const bool ok = e < total;
+      q[u] = ok ? ld_dag4(dag_col + oa + 4ull * vi) : make_uint4(0u, 0u, 0u, 0u);
+      pos[u] = (int)(4 * vi) - (int)oh;
+      ln[u] = ok ? (int)ol : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kVecU; ++u) hits += count_vec(set, q[u], pos[u], ln[u]);
+  }
+  return hits;
+}
+
 // A lane's partner p: its out-list, kept only on the side that walks the
 // shorter list (kind 0: d+(p) <= d+(c); kind 1: d+(p) < d+(c)).  A kind-1
 // partner's out-list holds c itself, which N+(c) does not, so one of length 1
@@ -606,7 +699,7 @@ __device__ __forceinline__ uint64_t walk_partners(const RowInfo* __restrict__ ro
     partner_list(row, dag_col, has1, p1, t.kind, t.c, dc, smax, &vb1, &len1);  // group k0 + step
     const bool has2 = k0 + 2 * step + lane < t.hi;
     const uint32_t p2 = has2 ? __ldg(partners + k0 + 2 * step + lane) : 0;
-    hits += warp_count_group(dag_col, vb, len, set);
+    hits += warp_count_group_vec(dag_col, vb, len, set);
     vb = vb1;
     len = len1;
     has1 = has2;

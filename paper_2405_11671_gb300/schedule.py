@@ -146,15 +146,19 @@ def regret(t, choices) -> float:
 
 
 def training_graphs(seed: int = 0xB10 + 50):
-    """Generated graphs of the three shapes at several sizes (never the benchmark graphs)."""
+    """Generated graphs of the three shapes at sizes up to those of the
+    benchmark configurations (RMAT up to scale 24, ER up to 2^21 vertices,
+    grids up to 4096 x 4096), drawn from their own seeds: never the benchmark
+    graphs themselves.  The network's size features must have seen sizes like
+    the ones it is used on."""
     import graphgen
     out = []
-    for sc in (14, 16, 18, 20, 21):
+    for sc in (14, 16, 18, 20, 22, 23, 24):
         out.append(("rmat%d" % sc, *graphgen.rmat_small(sc, 16, graphgen.stream(seed, sc))))
-    for sc, deg in ((15, 8), (17, 16), (19, 32)):
+    for sc, deg in ((15, 8), (17, 16), (19, 32), (21, 16)):
         n = 1 << sc
         out.append(("er%d" % sc, n, *graphgen.er(n, n * deg // 2, graphgen.stream(seed, 100 + sc))))
-    for side in (256, 512, 1024, 2048):
+    for side in (256, 512, 1024, 2048, 4096):
         out.append(("grid%d" % side, *graphgen.grid_small(side, side, 0.1, 1e-4, graphgen.stream(seed, side))))
     return out
 

@@ -103,3 +103,13 @@ def test_msbfs_bytes_two_sources():
     # level 2, bottom-up: every vertex has both sources; nothing found
     want += 8 * n + 24 * n
     assert got == want
+
+
+def test_bc_bytes_path():
+    # path 0-1-2 from 0: three reached vertices, degree sum 4, two edges to a
+    # vertex one level closer (1 -> 0, 2 -> 1); 8-byte offsets
+    g, off, col = _csr(3, [(0, 1), (1, 2)])
+    lv = torch.tensor([0, 1, 2], dtype=torch.int32)
+    n, r, dsum, closer = 3, 3, 4, 2
+    want = 16 * n + 8 * n + 4 * r + 2 * (8 * r + 8 * dsum) + 8 * closer + 8 * r + 16 * closer + 16 * r
+    assert bench.bc_method_bytes(torch, off, col, lv, 8) == want
