@@ -46,6 +46,7 @@ typedef enum byo_status {
 #define BYO_SYMMETRIZE 0x4u /* store every input pair (u,v) also as (v,u) */
 #define BYO_OFFSETS64 0x8u  /* CSR offsets as uint64 even when m < 2^32 */
 #define BYO_DYN_NO_INLINE 0x10u /* BYO_DYNAMIC without the inline head: every list in pool blocks */
+#define BYO_COMPRESSED 0x20u    /* BYO_CSR with difference-encoded, byte-coded lists (BFS, degree, export) */
 
 typedef struct byo_graph byo_graph;
 
@@ -59,7 +60,13 @@ const char* byo_last_error(void);
  * of Section 4.1 -- else a run of 128-byte blocks from a device pool), which
  * accepts byo_insert_batch / byo_delete_batch.  BYO_DYN_NO_INLINE (with
  * BYO_DYNAMIC only) keeps every non-empty list in pool blocks, for the
- * inline-head ablation.
+ * inline-head ablation.  BYO_COMPRESSED (with BYO_CSR only) keeps the CSR
+ * offsets and stores each list as the paper's compressed graphs do (Section 2,
+ * Section 6.5): the first neighbour relative to the vertex (2|u0 - v| +
+ * (u0 < v)), then the gaps, each in 7-bit groups least significant first with
+ * the 0x80 bit on all but a value's last byte.  A compressed container
+ * supports byo_bfs, byo_degree, byo_graph_export_csr and byo_space; the other
+ * algorithms return BYO_ERR_UNSUPPORTED.
  * Follows the graph model of Section 3 (vertices 0..n-1, a neighbour SET per
  * vertex, Section 3.1) and the CSR layout named in Section 4.2: duplicate
  * pairs collapse, self-loops are dropped, neighbours are stored ascending.
@@ -81,6 +88,12 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
  * capacity is not counted).  Library scratch is not included.  Synchronises
  * the stream.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
 byo_status byo_space(const byo_graph* g, uint64_t* host_bytes, void* stream);
+
+/* The byte codes of a BYO_COMPRESSED container: byte offsets boff[n+1] (device,
+ * uint64) and, when bytes is non-NULL, the boff[n] code bytes (device);
+ * *host_nbytes receives boff[n].  Synchronises the stream.  Errors:
+ * INVALID_ARG, UNSUPPORTED (not a compressed container), CUDA. */
+byo_status byo_export_codes(const byo_graph* g, uint64_t* boff, uint8_t* bytes, uint64_t* host_nbytes, void* stream);
 
 /* Free a handle and everything it owns (NULL is accepted).  Synchronises the device. */
 byo_status byo_graph_destroy(byo_graph* g);

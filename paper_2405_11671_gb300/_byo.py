@@ -31,6 +31,7 @@ BYO_DYNAMIC = 0x2
 BYO_SYMMETRIZE = 0x4
 BYO_OFFSETS64 = 0x8
 BYO_DYN_NO_INLINE = 0x10
+BYO_COMPRESSED = 0x20
 
 BYO_SCHED_HEURISTIC = 0
 BYO_SCHED_LEARNED = 1
@@ -77,6 +78,7 @@ SIGNATURES = [
     ("byo_graph_build", _st, [_u32, _vp, _vp, _u64, _u32, _vp, ctypes.POINTER(_vp)]),
     ("byo_graph_destroy", _st, [_vp]),
     ("byo_space", _st, [_vp, ctypes.POINTER(_u64), _vp]),
+    ("byo_export_codes", _st, [_vp, _vp, _vp, ctypes.POINTER(_u64), _vp]),
     ("byo_num_vertices", _st, [_vp, ctypes.POINTER(_u32)]),
     ("byo_num_edges", _st, [_vp, ctypes.POINTER(_u64)]),
     ("byo_degree", _st, [_vp, _vp, _u64, _vp, _vp]),
@@ -188,6 +190,17 @@ def byo_space(g: int, stream=None) -> int:
     v = _u64()
     _check(load().byo_space(g, ctypes.byref(v), _stream(stream)))
     return v.value
+
+
+def byo_export_codes(g: int, stream=None):
+    """(boff int64[n+1], bytes uint8[boff[n]]) of a compressed container (device tensors)."""
+    n = byo_num_vertices(g)
+    boff = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    nb = _u64()
+    _check(load().byo_export_codes(g, boff.data_ptr(), None, ctypes.byref(nb), _stream(stream)))
+    data = torch.empty(max(nb.value, 1), dtype=torch.uint8, device="cuda")
+    _check(load().byo_export_codes(g, boff.data_ptr(), data.data_ptr(), ctypes.byref(nb), _stream(stream)))
+    return boff, data[:nb.value]
 
 
 def byo_num_vertices(g: int) -> int:

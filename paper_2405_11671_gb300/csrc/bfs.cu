@@ -1150,6 +1150,22 @@ using namespace byo;
 extern "C" byo_status byo_bfs(const byo_graph* gc, const uint32_t* host_sources, uint32_t num_sources,
                               uint32_t* levels, uint32_t* parents, const byo_sched* sched, void* stream) {
   clear_error();
+  if (gc && gc->comp) {  // the compressed container has its own traversal
+    if (num_sources == 0) return BYO_OK;
+    if (!host_sources || !levels) {
+      set_error("byo_bfs: NULL sources or levels");
+      return BYO_ERR_INVALID_ARG;
+    }
+    for (uint32_t i = 0; i < num_sources; ++i) {
+      if (host_sources[i] >= gc->n) {
+        set_error("byo_bfs: source %u is >= n (%u)", host_sources[i], gc->n);
+        return BYO_ERR_INVALID_ARG;
+      }
+    }
+    SchedParams sp;
+    BYO_RETURN_IF(sched_params(sched, &sp));
+    return comp_bfs(gc, host_sources, num_sources, levels, parents, sp, static_cast<cudaStream_t>(stream));
+  }
   BYO_RETURN_IF(ready_graph(gc, static_cast<cudaStream_t>(stream)));
   byo_graph* g = const_cast<byo_graph*>(gc);
   if (num_sources == 0) return BYO_OK;

@@ -74,6 +74,8 @@ struct BfsWork;
 struct PrWork;
 struct TcWork;
 struct DynStore;
+struct CompStore;
+struct SchedParams;
 
 }  // namespace byo
 
@@ -98,6 +100,7 @@ struct byo_graph {
   byo::PrWork* pr = nullptr;
   byo::TcWork* tc = nullptr;
   byo::DynStore* dyn = nullptr;  // set for BYO_DYNAMIC (then off/col are unused)
+  byo::CompStore* comp = nullptr;  // set for BYO_COMPRESSED (then col is unused; off gives the degrees)
   // batch of graphs (byo_batch_build): member i owns ids [member_base[i], member_base[i+1])
   uint32_t members = 0;
   uint32_t* member_base = nullptr;       // device
@@ -114,6 +117,14 @@ void bfs_free(BfsWork* w);
 void pr_free(PrWork* w);
 void tc_free(TcWork* w);
 void dyn_free(DynStore* d);
+void comp_free(CompStore* c);
+// Compressed container (compressed.cu): encode g's CSR into byte codes and
+// release the neighbour ids; decode into col laid out by offsets; BFS.
+byo_status comp_from_csr(byo_graph* g, cudaStream_t s);
+byo_status comp_export(const byo_graph* g, const uint64_t* offsets, uint32_t* col, cudaStream_t s);
+byo_status comp_bfs(const byo_graph* g, const uint32_t* sources, uint32_t ns, uint32_t* levels, uint32_t* parents,
+                    const SchedParams& sp, cudaStream_t s);
+uint64_t comp_bytes(const byo_graph* g);
 byo_status check_graph(const byo_graph* g);
 // check_graph, then re-derive the degree buckets on stream s if a batch update
 // could not (it ran out of memory after applying the batch).

@@ -139,6 +139,10 @@ byo_status check_graph(const byo_graph* g) {
 
 byo_status ready_graph(const byo_graph* gc, cudaStream_t s) {
   BYO_RETURN_IF(check_graph(gc));
+  if (gc->comp) {
+    set_error("a compressed container supports BFS, degree, export and space queries only");
+    return BYO_ERR_UNSUPPORTED;
+  }
   byo_graph* g = const_cast<byo_graph*>(gc);
   if (!g->buckets_stale) return BYO_OK;
   BYO_RETURN_IF(rebuild_buckets(g, s));
@@ -497,6 +501,7 @@ void graph_free(byo_graph* g) {
   pr_free(g->pr);
   tc_free(g->tc);
   dyn_free(g->dyn);
+  comp_free(g->comp);
   if (g->member_base) cudaFree(g->member_base);
   delete[] g->member_base_host;
   dev_free(g->ms_seen);
@@ -628,6 +633,10 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
     set_error("byo_graph_build: NULL edge arrays with k = %llu", (unsigned long long)k);
     return BYO_ERR_INVALID_ARG;
   }
+  if ((flags & BYO_COMPRESSED) && !(flags & BYO_CSR)) {
+    set_error("byo_graph_build: BYO_COMPRESSED applies to BYO_CSR only");
+    return BYO_ERR_INVALID_ARG;
+  }
   if ((flags & BYO_DYN_NO_INLINE) && !(flags & BYO_DYNAMIC)) {
     set_error("byo_graph_build: BYO_DYN_NO_INLINE applies to BYO_DYNAMIC only");
     return BYO_ERR_INVALID_ARG;
@@ -658,6 +667,7 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
     ProfScope ps("csr_build", s);
     st = build_csr(g, src, dst, k, (flags & BYO_SYMMETRIZE) != 0, s);
     if (st == BYO_OK && (flags & BYO_DYNAMIC)) st = dyn_from_csr(g, s);
+    if (st == BYO_OK && (flags & BYO_COMPRESSED)) st = comp_from_csr(g, s);
   }
   if (st != BYO_OK) {
     cudaStreamSynchronize(s);
@@ -684,6 +694,10 @@ byo_status byo_space(const byo_graph* g, uint64_t* host_bytes, void* stream) {
     return BYO_ERR_INVALID_ARG;
   }
   if (g->dyn) return dyn_space(g, host_bytes, static_cast<cudaStream_t>(stream));
+  if (g->comp) {  // degree offsets, byte offsets and the code bytes
+    *host_bytes = (uint64_t)(g->n + 1ull) * ((g->off64 ? 8u : 4u) + 8u) + comp_bytes(g);
+    return BYO_OK;
+  }
   *host_bytes = (uint64_t)(g->n + 1ull) * (g->off64 ? 8u : 4u) + 4ull * g->m;
   return BYO_OK;
 }
@@ -761,11 +775,15 @@ byo_status byo_graph_export_csr(const byo_graph* g, uint64_t* offsets, uint32_t*
   if (st == BYO_OK) {
     set_last_u64_kernel<<<1, 1, 0, s>>>(offsets, g->n, g->m);
     ::byo::note_launch();
-    st = with_view(g, [&](auto view) {
-      export_col_kernel<<<grid_for((uint64_t)g->n * 32, 256), 256, 0, s>>>(view, offsets, col);
-      ::byo::note_launch();
-      return BYO_OK;
-    });
+    if (g->comp) {
+      st = comp_export(g, offsets, col, s);
+    } else {
+      st = with_view(g, [&](auto view) {
+        export_col_kernel<<<grid_for((uint64_t)g->n * 32, 256), 256, 0, s>>>(view, offsets, col);
+        ::byo::note_launch();
+        return BYO_OK;
+      });
+    }
   }
   tmp_free(deg, s);
   BYO_RETURN_IF(st);
