@@ -23,7 +23,7 @@ pull levels.  Byte counts are the method's (what the algorithm must move, from
 its outputs), never a kernel's own counters.
 
   python bench.py [--gpus N --steps K --warmup W --workload rmat25 --sources 8]
-  python bench.py --workload batched | dynamic | ablation
+  python bench.py --workload batched | dynamic | ablation | space
   python bench.py --impl reference ...   # the serial CPU oracle, bounded sample
 
 N > 1 (torchrun, one rank per GPU) runs independent replicas: the path does not
@@ -804,6 +804,70 @@ def run_ablation(args, byo, torch):
                       "sources": args.sources, "sched": "heuristic", "results": out}), flush=True)
 
 
+# ----------------------------------------------------------------------------- containers: space and time
+
+def run_space(args, byo, torch):
+    """The container comparison of Section 6.5 on the GPU path: bytes per
+    stored edge of the CSR, the dynamic container with and without its inline
+    head, and the compressed CSR (byte codes), beside the paper's 4.1 / 5.1 /
+    10.6 bytes per edge (its CSR, min / mean / max over its graphs); BFS from
+    the benchmark sources on each, and BFS + CC + PageRank on the dynamic
+    container with and without the inline head.  Heuristic schedule."""
+    import graphgen
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return round(statistics.median(ts), 3)
+
+    out = {}
+    for name in ("rmat22", "rmat25"):
+        n, src, dst = graphgen.workload(name)
+        srcs = graphgen.pick_sources(n, src, dst, args.sources, graphgen.SEEDS[name] + 1)
+        s_d, d_d = dev_u32(torch, src), dev_u32(torch, dst)
+        sym = byo.BYO_SYMMETRIZE | byo.BYO_OFFSETS64
+        kinds = {"csr": byo.BYO_CSR | sym, "compressed": byo.BYO_CSR | sym | byo.BYO_COMPRESSED,
+                 "dynamic_inline": byo.BYO_DYNAMIC | sym, "dynamic_no_inline": byo.BYO_DYNAMIC | sym | byo.BYO_DYN_NO_INLINE}
+        lv = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+        par = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+        lab = torch.empty(n, dtype=torch.int32, device="cuda")
+        rk = torch.empty(n, dtype=torch.float32, device="cuda")
+        res = {}
+        ref = None
+        for kind, fl in kinds.items():
+            g = byo.Graph(n, s_d, d_d, fl)
+            m = g.m
+            e = {"bytes_per_edge": round(byo.byo_space(g.handle) / m, 3)}
+            e["bfs_ms"] = timed(lambda: byo.byo_bfs(g.handle, srcs, lv, par), args.sched_reps)
+            if ref is None:
+                ref = lv.clone()
+            e["levels_identical"] = bool(torch.equal(lv, ref))
+            if kind.startswith("dynamic") or kind == "csr":
+                def three():
+                    byo.byo_bfs(g.handle, srcs, lv, par)
+                    byo.byo_cc(g.handle, lab)
+                    byo.byo_pagerank(g.handle, DAMPING, PR_ITERS, rk, want_residual=False)
+                e["bfs_cc_pr_ms"] = timed(three, max(1, args.sched_reps // 2))
+            res[kind] = e
+            g.close()
+        res["m"] = m
+        out[name] = res
+        del s_d, d_d, lv, par
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "container space (bytes per stored edge) and time (Section 6.5 comparison)",
+                      "paper_csr_bytes_per_edge": {"min": 4.1, "mean": 5.1, "max": 10.6},
+                      "sources": args.sources, "sched": "heuristic", "results": out}), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -843,6 +907,9 @@ def main():
         return
     if args.workload == "ablation":
         run_ablation(args, byo, torch)
+        return
+    if args.workload == "space":
+        run_space(args, byo, torch)
         return
 
     def barrier():

@@ -68,20 +68,56 @@ __global__ void bc_scatter_kernel(G g, const uint32_t* __restrict__ level, const
   }
 }
 
-// The gathered term of neighbour u of v at level l: forward, sigma(u) if u is
-// one level closer; backward, (1 + delta(u)) / sigma(u) if u is one deeper.
+// The gathered value of neighbour u: forward sigma(u), backward
+// ratio(u) = (1 + delta(u)) / sigma(u) (kept per vertex, so that a gather
+// divides nothing).  Only neighbours at level `want` count.
 template <bool kForward>
-__device__ __forceinline__ double bc_term(uint32_t u, uint32_t want, const uint32_t* __restrict__ level,
-                                          const double* __restrict__ sigma, const double* __restrict__ delta) {
-  if (__ldg(level + u) != want) return 0.0;
-  if (kForward) return __ldcg(sigma + u);
-  return (1.0 + __ldcg(delta + u)) / __ldcg(sigma + u);
+__device__ __forceinline__ double bc_value(uint32_t u, const double* __restrict__ sigma,
+                                           const double* __restrict__ ratio) {
+  return kForward ? __ldcg(sigma + u) : __ldcg(ratio + u);
 }
 
+// Sum over the ids p[k], k = first, first + stride, ... < len, of the values
+// of those at level `want`: four ids, their four levels and then their values
+// in flight per step.
 template <bool kForward>
-__device__ __forceinline__ void bc_store(uint32_t v, double acc, double* sigma, double* delta) {
-  if (kForward) sigma[v] = acc;
-  else delta[v] = __ldcg(sigma + v) * acc;
+__device__ __forceinline__ double bc_gather(const uint32_t* __restrict__ p, uint32_t first, uint32_t len,
+                                            uint32_t stride, uint32_t want, const uint32_t* __restrict__ level,
+                                            const double* __restrict__ sigma, const double* __restrict__ ratio) {
+  double acc = 0.0;
+  uint32_t k = first;
+  for (; k + 3 * stride < len; k += 4 * stride) {
+    uint32_t u[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u[j] = __ldg(p + k + j * stride);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) l[j] = __ldg(level + u[j]);
+    double x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = l[j] == want ? bc_value<kForward>(u[j], sigma, ratio) : 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc += x[j];
+  }
+  for (; k < len; k += stride) {
+    const uint32_t u = __ldg(p + k);
+    if (__ldg(level + u) == want) acc += bc_value<kForward>(u, sigma, ratio);
+  }
+  return acc;
+}
+
+// forward: sigma(v), and the ratio a vertex without deeper neighbours keeps;
+// backward: delta(v) = sigma(v) * sum, and v's ratio for the level above
+template <bool kForward>
+__device__ __forceinline__ void bc_store(uint32_t v, double acc, double* sigma, double* delta, double* ratio) {
+  if (kForward) {
+    sigma[v] = acc;
+    ratio[v] = 1.0 / acc;
+  } else {
+    const double sv = __ldcg(sigma + v);
+    const double dv = sv * acc;
+    delta[v] = dv;
+    ratio[v] = (1.0 + dv) / sv;
+  }
 }
 
 // One level of a sweep.  Blocks [0, light_blocks) take the level's light
@@ -92,7 +128,7 @@ __global__ void __launch_bounds__(kBcThreads) bc_level_kernel(G g, const uint32_
                                                               const uint64_t* __restrict__ lstart,
                                                               const uint32_t* __restrict__ lcnt, uint32_t l,
                                                               uint32_t light_blocks, const uint32_t* __restrict__ level,
-                                                              double* sigma, double* delta) {
+                                                              double* sigma, double* delta, double* ratio) {
   const uint64_t begin = lstart[l], end = lstart[l + 1];
   const uint64_t mid = begin + lcnt[l];
   const uint32_t want = kForward ? l - 1 : l + 1;
@@ -108,21 +144,18 @@ __global__ void __launch_bounds__(kBcThreads) bc_level_kernel(G g, const uint32_
       if (i < mid) {
         v = order[i];
         const Seg s = g.seg(v);
-        for (uint32_t k = lane; k < s.len; k += kGroup)
-          acc += bc_term<kForward>(__ldg(s.p + k), want, level, sigma, delta);
+        acc = bc_gather<kForward>(s.p, lane, s.len, kGroup, want, level, sigma, ratio);
       }
 #pragma unroll
       for (int o = kGroup / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o, kGroup);
-      if (i < mid && lane == 0) bc_store<kForward>(v, acc, sigma, delta);
+      if (i < mid && lane == 0) bc_store<kForward>(v, acc, sigma, delta, ratio);
     }
   } else {
     __shared__ double red[kBcThreads / 32];
     for (uint64_t i = mid + (blockIdx.x - light_blocks); i < end; i += gridDim.x - light_blocks) {
       const uint32_t v = order[i];
       const Seg s = g.seg(v);
-      double acc = 0.0;
-      for (uint32_t k = threadIdx.x; k < s.len; k += blockDim.x)
-        acc += bc_term<kForward>(__ldg(s.p + k), want, level, sigma, delta);
+      double acc = bc_gather<kForward>(s.p, threadIdx.x, s.len, blockDim.x, want, level, sigma, ratio);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
       if (lane_id() == 0) red[threadIdx.x >> 5] = acc;
@@ -130,7 +163,7 @@ __global__ void __launch_bounds__(kBcThreads) bc_level_kernel(G g, const uint32_
       if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < kBcThreads / 32; ++w) t += red[w];
-        bc_store<kForward>(v, t, sigma, delta);
+        bc_store<kForward>(v, t, sigma, delta, ratio);
       }
       __syncthreads();
     }
@@ -161,7 +194,9 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
   const uint64_t L = (uint64_t)depth + 1;
   uint32_t *cnt = nullptr, *lcnt = nullptr, *cur = nullptr, *order = nullptr;
   uint64_t* lstart = nullptr;
+  double* ratio = nullptr;
   st = tmp_alloc_t(&cnt, L + 1, s, "BC level counts");
+  if (st == BYO_OK) st = tmp_alloc_t(&ratio, n, s, "BC ratios");
   if (st == BYO_OK) st = tmp_alloc_t(&lcnt, L, s, "BC light counts");
   if (st == BYO_OK) st = tmp_alloc_t(&cur, 2 * L, s, "BC cursors");
   if (st == BYO_OK) st = tmp_alloc_t(&lstart, L + 1, s, "BC level starts");
@@ -198,7 +233,7 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
         const uint64_t c = hstart[l + 1] - hstart[l];
         const uint32_t lb = blocks(c);
         bc_level_kernel<G, true><<<lb + (uint32_t)sm_count(), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
-                                                                                   level, sigma, delta);
+                                                                                   level, sigma, delta, ratio);
         note_launch();
       }
     }
@@ -208,7 +243,7 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
         const uint64_t c = hstart[l + 1] - hstart[l];
         const uint32_t lb = blocks(c);
         bc_level_kernel<G, false><<<lb + (uint32_t)sm_count(), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
-                                                                                    level, sigma, delta);
+                                                                                    level, sigma, delta, ratio);
         note_launch();
       }
     }
@@ -221,6 +256,7 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
   tmp_free(cur, s);
   tmp_free(lstart, s);
   tmp_free(order, s);
+  tmp_free(ratio, s);
   return st;
 }
 

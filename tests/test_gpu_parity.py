@@ -353,7 +353,7 @@ def test_mlp_gradient_matches_oracle(byo):
     X, y, w = _mlp_batch()
     loss, grad = byo.byo_mlp_loss_grad(m, torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(),
                                        torch.from_numpy(w).cuda())
-    L, g64, _ = oracle.mlp_loss(P.astype(np.float64), 12, 32, 32, 5, X.astype(np.float64), y, w.astype(np.float64))
+    L, g64, _ = oracle.mlp_loss(P.astype(np.float64), 12, 32, 32, byo.BYO_NUM_ACTIONS, X.astype(np.float64), y, w.astype(np.float64))
     assert abs(loss - L) <= 1e-4 * max(1.0, abs(L))
     g32 = grad.cpu().numpy().astype(np.float64)
     for a, b in zip(_split(g32), _split(g64)):
@@ -372,7 +372,7 @@ def test_mlp_train_and_predict(byo):
     assert l1 < 0.5 * l0
     pred = byo.byo_mlp_predict(m, Xd).cpu().numpy()
     P = byo.byo_mlp_get_params(m).astype(np.float64)
-    _, _, logits = oracle.mlp_loss(P, 12, 32, 32, 5, X.astype(np.float64), y, None, want_grad=False)
+    _, _, logits = oracle.mlp_loss(P, 12, 32, 32, byo.BYO_NUM_ACTIONS, X.astype(np.float64), y, None, want_grad=False)
     srt = np.sort(logits, axis=1)
     clear = (srt[:, -1] - srt[:, -2]) > 1e-3                      # skip near-ties (FP32 vs FP64)
     assert np.array_equal(pred[clear], np.argmax(logits, axis=1)[clear])
