@@ -15,16 +15,17 @@
 // Push (sparse edgeMap): degree-binned.  Small-degree vertices: a warp takes
 //   32 of them and walks their concatenated edges 32 at a time (edge-balanced
 //   inside the warp); mid-degree: one warp per vertex; high degree: CTA-wide
-//   chunks of at most kChunk edges.  A neighbour is claimed in the visited bit
-//   array with one atomicOr per distinct 32-bit word per warp (same-word claims
-//   merged with __match_any_sync and a warp OR).
-// Pull (dense edgeMap): a warp owns one 32-vertex word of the visited bit
-//   array; each unvisited vertex scans its sorted neighbour list with 16-byte
-//   vector loads until the first neighbour in the frontier bit-vector
-//   (map_neighbors_early_exit, Section 4.2); high-degree vertices are scanned
-//   by the whole warp, 128 ids per step.  The warp writes its visited and next-
-//   frontier words without atomics, and appends the discovered vertices to the
-//   queue (warp-scan compaction), so both representations of the next
+//   chunks of at most kChunk edges.  On small levels a warp takes fewer of the
+//   small-degree vertices, so that every warp has about one round of 32 edges.
+//   A neighbour is claimed in the visited bit array with one atomicOr per
+//   candidate (on large levels after a plain read of its bit).
+// Pull (dense edgeMap): a warp owns a contiguous range of words of the visited
+//   bit array; its lanes take the unvisited vertices one each and scan their
+//   sorted neighbour lists until the first neighbour in the frontier
+//   bit-vector (map_neighbors_early_exit, Section 4.2); lists with no hit in
+//   their first ids are finished by the whole warp, 128 ids per step.  The
+//   warp sets its own visited and next-frontier bits, and appends the
+//   discovered vertices to the queue, so both representations of the next
 //   frontier exist after a pull.
 #include <math.h>
 
@@ -42,6 +43,7 @@ constexpr int kPullThreadMax = 32;  // pull: each lane scans this many ids of it
 constexpr uint32_t kChunk = 2048;   // push: edges per CTA work item in the CTA bin
 static_assert(kChunk == 1u << 11, "bucket b >= 12 splits into 2^(b - 11) CTA work items");
 constexpr uint32_t kTraceCap = 1u << 16;
+constexpr uint64_t kPrecheckMinEdges = 1u << 15;  // push levels with fewer frontier edges claim directly
 
 struct BfsCtl {
   GridBar bar;
@@ -112,6 +114,10 @@ struct BfsShared {
   int fb_valid;
   uint64_t t_top;
   uint32_t t_level;  // level whose start time t_top is
+  uint64_t scan_prev;  // ids read during the level before (trace)
+  int precheck;        // push reads the visited bit before claiming
+  uint32_t tg_min;     // smallest thread-bin group: 32 / (lower bound of the bin's mean degree)
+  uint32_t err_seen;   // the control block's error word at the start of the level
   unsigned long long red[2];  // this CTA's share of the next frontier's degree sum and ids read
 };
 
@@ -125,44 +131,60 @@ __device__ __forceinline__ int find_bucket(const uint64_t* pre, int lo, int hi, 
   return lo;
 }
 
+// Appends the calling warp's winners (lanes with `won`, vertex v, degree
+// bucket b; wm = the ballot of `won`) to the next level's queue.  Lanes are
+// grouped by bucket with one ballot per distinct bucket (a few ALU steps; a
+// warp match instruction costs far more on the critical path of a small
+// level), then the lowest lane of every group reserves the group's slots with
+// one atomicAdd, all groups at once.  Warp-collective.
+template <typename G>
+__device__ __forceinline__ void queue_append(const BfsArgs<G>& a, const BfsShared& S, bool won, uint32_t v,
+                                             uint32_t b, int nxt, uint32_t wm) {
+  const uint32_t lane = lane_id();
+  uint32_t todo = wm, grp = 0;
+  while (todo) {
+    const uint32_t l = __ffs(todo) - 1;
+    const uint32_t bl = __shfl_sync(0xFFFFFFFFu, b, l);
+    const uint32_t g = __ballot_sync(0xFFFFFFFFu, won && b == bl);
+    if (won && b == bl) grp = g;
+    todo &= ~g;
+  }
+  const uint32_t leader = won ? __ffs(grp) - 1 : 0;
+  unsigned long long pos = 0;
+  if (won && lane == leader) pos = atomicAdd(&a.ctl->cnt[nxt][b], (unsigned long long)__popc(grp));
+  pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+  if (won) {
+    const uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + pos + __popc(grp & lanemask_lt());
+    if (at < S.bstart[b + 1]) a.queue[at] = v;
+    else atomicCAS(&a.ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is claimed once
+  }
+}
+
 // Warp-collective: claim v for every lane with `cand`, then record the
 // winners and append them to the next level's queue.  All 32 lanes call it.
+// Each candidate lane claims with its own atomicOr on the visited bits: the
+// word it returns decides the one winner of each vertex, also between lanes
+// of this warp that hold the same vertex.
 template <typename G, bool kParents>
 __device__ __forceinline__ void claim_emit(const BfsArgs<G>& a, BfsShared& S, bool cand, uint32_t v, uint32_t u,
                                            uint32_t next_level, int nxt, uint64_t& acc_deg) {
-  const uint32_t lane = lane_id();
-  if (cand) cand = !((ld_cg(a.vis + (v >> 5)) >> (v & 31)) & 1u);
+  // the plain read of the visited bit spares atomics where many neighbours are
+  // already visited; on small levels it is one more round trip and is skipped
+  if (cand && S.precheck) cand = !((ld_cg(a.vis + (v >> 5)) >> (v & 31)) & 1u);
   if (__ballot_sync(0xFFFFFFFFu, cand) == 0) return;
-  // one claim per distinct vertex, then one atomicOr per distinct word
-  uint32_t same_v = __match_any_sync(0xFFFFFFFFu, cand ? v : 0xFFFFFFFFu);
-  bool first = cand && (same_v & lanemask_lt()) == 0;
-  uint32_t same_w = __match_any_sync(0xFFFFFFFFu, first ? (v >> 5) : 0xFFFFFFFFu);
-  uint32_t bit = first ? (1u << (v & 31)) : 0u;
-  uint32_t orbits = __reduce_or_sync(same_w, bit);
-  uint32_t leader = __ffs(same_w) - 1;
-  uint32_t old = 0;
-  if (first && lane == leader) old = atomicOr(a.vis + (v >> 5), orbits);
-  old = __shfl_sync(0xFFFFFFFFu, old, leader);
-  bool won = first && !(old & bit);
+  const uint32_t bit = 1u << (v & 31);
+  const uint32_t d = cand ? a.g.degree(v) : 0u;  // read while the claim is in flight
+  const bool won = cand && !(atomicOr(a.vis + (v >> 5), bit) & bit);
+  const uint32_t wm = __ballot_sync(0xFFFFFFFFu, won);
+  if (wm == 0) return;
   uint32_t b = 0xFFFFFFFFu;
   if (won) {
     a.level[v] = next_level;
     if (kParents) a.parent[v] = u;
-    uint32_t d = a.g.degree(v);
     acc_deg += d;
     b = (uint32_t)degree_bucket(d);
   }
-  if (__ballot_sync(0xFFFFFFFFu, won) == 0) return;
-  uint32_t same_b = __match_any_sync(0xFFFFFFFFu, b);
-  uint32_t bl = __ffs(same_b) - 1;
-  unsigned long long pos = 0;
-  if (won && lane == bl) pos = atomicAdd(&a.ctl->cnt[nxt][b], (unsigned long long)__popc(same_b));
-  pos = __shfl_sync(0xFFFFFFFFu, pos, bl);
-  if (won) {
-    uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + pos + __popc(same_b & lanemask_lt());
-    if (at < S.bstart[b + 1]) a.queue[at] = v;
-    else atomicCAS(&a.ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is claimed once
-  }
+  queue_append(a, S, won, v, b, nxt, wm);
 }
 
 template <typename G>
@@ -242,11 +264,18 @@ __device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, const Workers& wk,
     }
     return;
   }
-  for (uint64_t jb = (uint64_t)gwarp * 32; jb < t1; jb += (uint64_t)nwarps * 32) {
+  // Vertices per warp: 32 once every warp has a group of its own, fewer on
+  // smaller levels (down to about one round of 32 edges per warp), because the
+  // rounds of one warp run one after another, each a chain of dependent memory
+  // operations.
+  const uint64_t spread = (t1 + nwarps - 1) / nwarps;
+  const uint32_t sp1 = spread >= 32 ? 32u : (spread ? (uint32_t)spread : 1u);
+  const uint32_t g = sp1 >= 32 ? 32u : max(S.tg_min, 1u << (31 - __clz(sp1 * 2 - 1)));  // pow2 >= sp1
+  for (uint64_t jb = (uint64_t)gwarp * g; jb < t1; jb += (uint64_t)nwarps * g) {
     uint64_t j = jb + lane;
     uint32_t u = 0;
     Seg s{nullptr, 0};
-    if (j < t1) {
+    if (lane < g && j < t1) {
       int b = find_bucket(S.pre, 0, bt, j);
       u = frontier_vertex(a, S, b, j - S.pre[b]);
       s = a.g.seg(u);
@@ -295,32 +324,20 @@ template <typename G, bool kParents>
 __device__ __forceinline__ void pull_emit(const BfsArgs<G>& a, const BfsShared& S, uint32_t* fbn, bool found,
                                           uint32_t v, uint32_t par, uint32_t len, uint32_t L, int nxt,
                                           uint64_t& acc_deg) {
-  const uint32_t lane = lane_id();
-  if (__ballot_sync(0xFFFFFFFFu, found) == 0) return;
+  const uint32_t wm = __ballot_sync(0xFFFFFFFFu, found);
+  if (wm == 0) return;
   uint32_t b = 0xFFFFFFFFu;
   if (found) {
     a.level[v] = L + 1;
     if (kParents) a.parent[v] = par;
     acc_deg += len;
     b = (uint32_t)degree_bucket(len);
+    // the warp's own words (no other warp writes them in this level): plain
+    // reductions, nothing to wait for
+    atomicOr(a.vis + (v >> 5), 1u << (v & 31));
+    atomicOr(fbn + (v >> 5), 1u << (v & 31));
   }
-  const uint32_t same_w = __match_any_sync(0xFFFFFFFFu, found ? (v >> 5) : 0xFFFFFFFFu);
-  const uint32_t bits = __reduce_or_sync(same_w, found ? (1u << (v & 31)) : 0u);
-  if (found && (same_w & lanemask_lt()) == 0) {
-    // L2 reads: another SM may have written these lines in earlier levels
-    a.vis[v >> 5] = ld_cg(a.vis + (v >> 5)) | bits;
-    fbn[v >> 5] = ld_cg(fbn + (v >> 5)) | bits;
-  }
-  const uint32_t same_b = __match_any_sync(0xFFFFFFFFu, b);
-  const uint32_t bl = __ffs(same_b) - 1;
-  unsigned long long pos = 0;
-  if (found && lane == bl) pos = atomicAdd(&a.ctl->cnt[nxt][b], (unsigned long long)__popc(same_b));
-  pos = __shfl_sync(0xFFFFFFFFu, pos, bl);
-  if (found) {
-    const uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + pos + __popc(same_b & lanemask_lt());
-    if (at < S.bstart[b + 1]) a.queue[at] = v;
-    else atomicCAS(&a.ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is found once
-  }
+  queue_append(a, S, found, v, b, nxt, wm);
   __syncwarp();  // the word updates are seen by the warp's later readers
 }
 
@@ -551,76 +568,120 @@ __device__ __forceinline__ void flush_acc(unsigned long long* dst, uint64_t v) {
 // Start of level L for the calling CTA: frontier counts and prefixes, the
 // trace, the schedule decision and the push bins.  `owner` (block 0) also
 // zeroes the counters of level L+2 and writes the trace.  Returns |F|.
+// The counters come in one round of loads; warp 0 then forms both bucket
+// prefixes with shuffle scans (lane b holds bucket b, the last bucket is added
+// on top) and decides, while other threads clear the counters of level L-1,
+// which no CTA reads any more (all passed the barrier that ended it) and
+// which level L+1 fills next.
 template <typename G>
 __device__ uint32_t level_top(const BfsArgs<G>& a, BfsShared& S, uint32_t L, bool owner) {
+  static_assert(kBuckets == 33, "warp 0 scans buckets 0..31 and adds bucket 32");
   const uint32_t tid = threadIdx.x;
   const uint32_t n = a.g.num_vertices();
   const uint64_t m = a.g.num_edges();
   BfsCtl* ctl = a.ctl;
   const int cur = L % 3, old = (L + 2) % 3;
   if (tid < (uint32_t)kBuckets) S.cnt[tid] = (uint32_t)ld_cg(&ctl->cnt[cur][tid]);
+  else if (tid == kBuckets) S.mf = ld_cg(&ctl->sdeg[cur]);
+  else if (tid == kBuckets + 1 && owner) S.scan_prev = ld_cg(&ctl->scanned[cur]);
+  else if (tid == kBuckets + 2) S.err_seen = ld_cg(&ctl->err);
   __syncthreads();
-  if (tid == 0) {
-    uint64_t now = globaltimer();
-    S.pre[0] = 0;
-    for (int b = 0; b < kBuckets; ++b) S.pre[b + 1] = S.pre[b] + S.cnt[b];
-    S.nf = (uint32_t)S.pre[kBuckets];
-    S.mf = ld_cg(&ctl->sdeg[cur]);
-    if (owner && L > 0 && L - 1 < kTraceCap && S.t_level == L - 1) {
-      byo_bfs_iter* r = a.trace + (L - 1);
-      r->t_ns = now - S.t_top;
-      r->edges_examined = ld_cg(&ctl->scanned[cur]);
+  if (S.err_seen != 0) return 0;  // another CTA failed: the caller stops
+  if (tid < 32) {
+    const uint32_t lane = tid;
+    uint64_t inc = S.cnt[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if ((int)lane >= o) inc += y;
     }
-    if (S.t_level != L) {
-      S.t_top = now;
-      S.t_level = L;
+    const uint64_t nf = __shfl_sync(0xFFFFFFFFu, inc, 31) + S.cnt[32];
+    S.pre[lane + 1] = inc;
+    if (lane == 0) {
+      S.pre[0] = 0;
+      S.pre[kBuckets] = nf;
+      S.nf = (uint32_t)nf;
+      const uint64_t now = globaltimer();
+      if (owner && L > 0 && L - 1 < kTraceCap && S.t_level == L - 1) {
+        byo_bfs_iter* r = a.trace + (L - 1);
+        r->t_ns = now - S.t_top;
+        r->edges_examined = S.scan_prev;
+      }
+      if (S.t_level != L) {
+        S.t_top = now;
+        S.t_level = L;
+      }
     }
-  }
-  __syncthreads();
-  if (S.nf == 0) return 0;
-  if (owner && tid < (uint32_t)kBuckets) ctl->cnt[old][tid] = 0;
-  if (owner && tid == 0) {
+    if (nf != 0) {
+      SchedFeatures f;
+      f.nf = (uint32_t)nf;
+      f.mf = S.mf;
+      f.nu = (uint64_t)n - S.nvis - nf;
+      f.mu = m - S.mvis - S.mf;
+      f.n = n;
+      f.m = m;
+      const uint64_t p3 = __shfl_sync(0xFFFFFFFFu, inc, 2), p6 = __shfl_sync(0xFFFFFFFFu, inc, 5),
+                     p9 = __shfl_sync(0xFFFFFFFFu, inc, 8);
+      f.h[0] = (uint32_t)p3;
+      f.h[1] = (uint32_t)(p6 - p3);
+      f.h[2] = (uint32_t)(p9 - p6);
+      f.h[3] = (uint32_t)(nf - p9);
+      const int action = sched_decide(a.sp, f, S.prev_dir);  // warp-collective
+      int bt, bw;
+      sched_bins(a.sp, action, &bt, &bw);
+      // CTA-bin work items: vertices * chunks per vertex, for buckets above bw
+      auto items = [&](int b) -> uint64_t {
+        return b > bw ? (uint64_t)S.cnt[b] * ((b >= 12) ? (1ull << (b - 11)) : 1ull) : 0ull;
+      };
+      uint64_t c = items((int)lane);
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, c, o);
+        if ((int)lane >= o) c += y;
+      }
+      S.preC[lane + 1] = c;
+      const uint64_t totC = __shfl_sync(0xFFFFFFFFu, c, 31) + items(32);
+      // thread bin (buckets 1..bt; bucket b holds degrees >= 2^(b-1)): vertices
+      // and a lower bound of their degree sum
+      uint64_t tv = (lane >= 1 && (int)lane <= bt) ? S.cnt[lane] : 0ull;
+      uint64_t te = tv << (lane >= 1 ? lane - 1 : 0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        tv += __shfl_xor_sync(0xFFFFFFFFu, tv, o);
+        te += __shfl_xor_sync(0xFFFFFFFFu, te, o);
+      }
+      const uint64_t mean = tv ? (te + tv - 1) / tv : 1;  // >= 1
+      const uint32_t tg = mean >= 32 ? 1u : 1u << (31 - __clz((uint32_t)(32 / mean)));
+      if (lane == 0) {
+        S.preC[0] = 0;
+        S.preC[kBuckets] = totC;
+        S.action = action;
+        S.dir = action == 0 ? 0 : 1;
+        S.bt = bt;
+        S.bw = bw;
+        S.precheck = f.mf >= kPrecheckMinEdges;
+        S.tg_min = tg;
+        if (owner && L < kTraceCap) {
+          byo_bfs_iter* r = a.trace + L;
+          r->level = L;
+          r->direction = (uint32_t)S.dir;
+          r->action = (uint32_t)action;
+          r->frontier = (uint32_t)nf;
+          r->frontier_edges = f.mf;
+          r->unvisited = (uint32_t)f.nu;
+          r->unvisited_edges = f.mu;
+          for (int k = 0; k < 4; ++k) r->hist[k] = f.h[k];
+          r->reserved = 0;
+          r->edges_examined = 0;
+          r->t_ns = 0;
+        }
+      }
+    }
+  } else if (owner && tid >= 64 && tid < 64 + (uint32_t)kBuckets) {
+    ctl->cnt[old][tid - 64] = 0;
+  } else if (owner && tid == 64 + (uint32_t)kBuckets) {
     ctl->sdeg[old] = 0;
     ctl->scanned[old] = 0;
-  }
-  if (tid < 32) {
-    SchedFeatures f;
-    f.nf = S.nf;
-    f.mf = S.mf;
-    f.nu = (uint64_t)n - S.nvis - S.nf;
-    f.mu = m - S.mvis - S.mf;
-    f.n = n;
-    f.m = m;
-    f.h[0] = (uint32_t)(S.pre[3]);
-    f.h[1] = (uint32_t)(S.pre[6] - S.pre[3]);
-    f.h[2] = (uint32_t)(S.pre[9] - S.pre[6]);
-    f.h[3] = (uint32_t)(S.pre[kBuckets] - S.pre[9]);
-    int action = sched_decide(a.sp, f, S.prev_dir);  // warp-collective
-    if (tid == 0) {
-      S.action = action;
-      S.dir = action == 0 ? 0 : 1;
-      sched_bins(a.sp, action, &S.bt, &S.bw);
-      if (owner && L < kTraceCap) {
-        byo_bfs_iter* r = a.trace + L;
-        r->level = L;
-        r->direction = (uint32_t)S.dir;
-        r->action = (uint32_t)action;
-        r->frontier = S.nf;
-        r->frontier_edges = S.mf;
-        r->unvisited = (uint32_t)f.nu;
-        r->unvisited_edges = f.mu;
-        for (int k = 0; k < 4; ++k) r->hist[k] = f.h[k];
-        r->reserved = 0;
-        r->edges_examined = 0;
-        r->t_ns = 0;
-      }
-      // CTA-bin work items: vertices * chunks per vertex
-      S.preC[0] = 0;
-      for (int b = 0; b < kBuckets; ++b) {
-        uint64_t K = (b >= 12) ? (1ull << (b - 11)) : 1ull;
-        S.preC[b + 1] = S.preC[b] + (b > S.bw ? (uint64_t)S.cnt[b] * K : 0ull);
-      }
-    }
   }
   __syncthreads();
   return S.nf;
@@ -951,11 +1012,13 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
   uint32_t L = 0;
   while (true) {
     // a BFS has at most n levels; the whole traversal is also time-bounded
-    if (L > n || ld_cg(&ctl->err) != 0 || globaltimer() - t_begin > a.limit_ns) {
+    if (L > n || globaltimer() - t_begin > a.limit_ns) {
       if (tid == 0) atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_TIMEOUT);
       return;
     }
-    if (level_top(a, S, L, owner) == 0) {
+    const uint32_t nf_top = level_top(a, S, L, owner);
+    if (S.err_seen != 0) return;  // the error another CTA set stands
+    if (nf_top == 0) {
       if (owner && tid == 0) ctl->levels = L;
       break;
     }
@@ -1067,6 +1130,7 @@ byo_status launch_bfs(BfsArgs<G>& args, cudaStream_t s) {
   }
   int grid = per_sm * sm_count();
   void* kargs[] = {&args};
+  BYO_CUDA(reset_barrier(&args.ctl->bar, s));
   ProfScope ps("bfs_persistent", s);
   BYO_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kBfsThreads), kargs, 0, s));
   note_launch();

@@ -175,47 +175,43 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
 
 __device__ __forceinline__ int degree_bucket(uint32_t d) { return d == 0 ? 0 : 32 - __clz(d); }
 
-// Grid-wide barrier for a cooperative launch, two levels deep: CTAs arrive
-// in groups of kBarGroup on their own counters (32 bytes apart), the last of
-// each group arrives at the root, and the last group releases everyone by
-// bumping the generation.  Every wait is bounded by `limit_ns`; on timeout the
-// error word is set and false is returned (the caller leaves its loop and exits).
-constexpr uint32_t kBarGroup = 16;
-constexpr uint32_t kBarMaxGroups = 512;  // up to 8192 CTAs
-
+// Grid-wide barrier for a cooperative launch.  One 64-bit arrival counter
+// that only grows within a launch: the k-th barrier of a launch of B CTAs
+// takes the arrivals numbered [kB, (k+1)B), because no CTA can arrive at a
+// barrier before all B have arrived at the one before it.  So each CTA's
+// thread 0 adds one (acquire-release, which also publishes what the CTA wrote
+// before the barrier) and waits until the counter reaches the next multiple of
+// B above the number its add returned; the last to arrive does not wait.
+// The counter must be zero when a launch starts (reset_barrier).  A wait
+// is bounded by `limit_ns`; on timeout the error word is set and false is
+// returned (the caller leaves its loop and exits).
 struct GridBar {
-  uint32_t count;  // groups arrived
-  uint32_t gen;
+  unsigned long long arrive;
   uint32_t pad[30];
-  uint32_t sub[kBarMaxGroups * 8];  // group counters, one per 32 bytes
 };
+
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long* p, unsigned long long v) {
+  unsigned long long r;
+  asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ bool grid_barrier(GridBar* bar, uint32_t nblocks, uint32_t* err, uint64_t limit_ns) {
   __shared__ uint32_t ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t ok = 1;
-    uint32_t g = ld_acquire(&bar->gen);
-    __threadfence();
-    const uint32_t grp = blockIdx.x / kBarGroup;
-    const uint32_t gsize = min(kBarGroup, nblocks - grp * kBarGroup);
-    const uint32_t ngroups = (nblocks + kBarGroup - 1) / kBarGroup;
-    uint32_t* sc = &bar->sub[grp * 8];
-    bool release = false;
-    if (atomicAdd(sc, 1u) == gsize - 1) {
-      *sc = 0;  // every member of the group has arrived and now waits on gen
-      __threadfence();
-      if (atomicAdd(&bar->count, 1u) == ngroups - 1) {
-        bar->count = 0;
-        __threadfence();
-        st_release(&bar->gen, g + 1);
-        release = true;
-      }
-    }
-    if (!release) {
+    const unsigned long long old = atom_add_acq_rel(&bar->arrive, 1ull);
+    const unsigned long long target = (old / nblocks + 1) * nblocks;
+    if (old + 1 != target) {
       uint64_t t0 = globaltimer();
       uint32_t spins = 0;
-      while (ld_acquire(&bar->gen) == g) {
+      while (ld_acquire(&bar->arrive) < target) {
         if (++spins > 64) {
           spins = 0;
           if (ld_cg(err) != 0 || globaltimer() - t0 > limit_ns) {
@@ -223,7 +219,6 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, uint32_t nblocks, uin
             ok = 0;
             break;
           }
-          __nanosleep(32);
         }
       }
     }
@@ -231,6 +226,12 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, uint32_t nblocks, uin
   }
   __syncthreads();
   return ok_s != 0;
+}
+
+// Clears the arrival counter of `bar` on stream `s`; called before each
+// cooperative launch that synchronises through it.
+inline cudaError_t reset_barrier(GridBar* bar, cudaStream_t s) {
+  return cudaMemsetAsync(&bar->arrive, 0, sizeof(bar->arrive), s);
 }
 
 }  // namespace byo

@@ -479,6 +479,7 @@ byo_status comp_bfs_launch(CompBfsArgs<OffT>& args, cudaStream_t s) {
     return BYO_ERR_CUDA;
   }
   void* kargs[] = {&args};
+  BYO_CUDA(reset_barrier(&args.ctl->bar, s));
   ProfScope ps("comp_bfs", s);
   BYO_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(per_sm * sm_count()), dim3(kCompThreads), kargs, 0, s));
   note_launch();

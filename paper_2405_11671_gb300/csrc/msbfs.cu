@@ -363,6 +363,7 @@ extern "C" byo_status byo_msbfs(const byo_graph* gc, const uint32_t* host_source
       return BYO_ERR_CUDA;
     }
     void* kargs[] = {&a};
+    BYO_CUDA(reset_barrier(&a.ctl->bar, s));
     ProfScope ps("msbfs_persistent", s);
     BYO_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(per_sm * sm_count()), dim3(kMsThreads), kargs, 0, s));
     note_launch();

@@ -106,7 +106,7 @@ __device__ __forceinline__ void sched_bins(const SchedParams& sp, int action, in
 
 // Whether the learned schedule may pull: where either Beamer test would.
 __device__ __forceinline__ bool sched_pull_allowed(const SchedParams& sp, const SchedFeatures& f) {
-  return (double)f.mf > (double)f.mu / (double)sp.alpha || (double)f.nf >= (double)f.n / (double)sp.beta;
+  return (double)f.mf * (double)sp.alpha > (double)f.mu || (double)f.nf * (double)sp.beta >= (double)f.n;
 }
 
 // Warp-collective (all 32 lanes of one warp); returns the action on every lane.
@@ -114,8 +114,10 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
   if (sp.mode == BYO_SCHED_FIXED) return sp.fixed_action;
   if (sp.mode == BYO_SCHED_PUSH) return 1;
   if (sp.mode == BYO_SCHED_PULL) return 0;
-  const int beamer = prev_dir == 1 ? ((double)f.mf > (double)f.mu / (double)sp.alpha ? 0 : 1)
-                                    : ((double)f.nf < (double)f.n / (double)sp.beta ? 1 : 0);
+  // the two tests as products (alpha, beta > 0): a division would cost more
+  // than the rest of the decision on this part's FP64 pipe
+  const int beamer = prev_dir == 1 ? ((double)f.mf * (double)sp.alpha > (double)f.mu ? 0 : 1)
+                                    : ((double)f.nf * (double)sp.beta < (double)f.n ? 1 : 0);
   if (sp.mode == BYO_SCHED_HEURISTIC || sp.w == nullptr) return beamer;
   // LEARNED: lane j owns hidden unit j of both layers
   const uint32_t lane = lane_id();

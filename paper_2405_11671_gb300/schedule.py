@@ -114,7 +114,7 @@ def allowed(t_row, stats_row, alpha: float = ALPHA, beta: float = BETA):
     t = np.array(t_row, np.float64)
     if mf > SOLO_MAX_EDGES or nf > SOLO_MAX_VERTICES:
         t[4] = np.inf
-    if not (mf > mu / alpha or nf >= n / beta):
+    if not (mf * alpha > mu or nf * beta >= n):  # the device's form of the two tests
         t[0] = np.inf
     return t
 
