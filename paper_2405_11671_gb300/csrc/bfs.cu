@@ -43,13 +43,22 @@ constexpr int kPullThreadMax = 32;  // pull: each lane scans this many ids of it
 constexpr uint32_t kChunk = 2048;   // push: edges per CTA work item in the CTA bin
 static_assert(kChunk == 1u << 11, "bucket b >= 12 splits into 2^(b - 11) CTA work items");
 constexpr uint32_t kTraceCap = 1u << 16;
+constexpr int kPushK = 4;  // push: candidates per lane in flight at once
 constexpr uint64_t kPrecheckMinEdges = 1u << 15;  // push levels with fewer frontier edges claim directly
+
+// A counter alone in its 128-byte line: the queue counters take one atomic
+// per warp and bucket from every CTA, and counters that share lines (and so
+// L2 slices) serialise each other.
+struct LineCounter {
+  unsigned long long v;
+  unsigned long long pad[15];
+};
 
 struct BfsCtl {
   GridBar bar;
   uint32_t err;
   uint32_t levels;
-  unsigned long long cnt[3][kBuckets];  // appends per bucket, by level mod 3
+  LineCounter cnt[3][kBuckets];  // appends per bucket, by level mod 3
   unsigned long long sdeg[3];           // sum of degrees of the frontier being built
   unsigned long long scanned[3];        // neighbour ids read while building it
   // hand-over from a solo run of block 0 to the grid
@@ -101,6 +110,20 @@ struct BfsArgs {
 
 namespace {
 
+// Winners of a warp waiting for their queue slots.  Reserving slots costs
+// one global atomicAdd per degree bucket, and the counter of a popular
+// bucket takes every warp's atomics (a single address sustains about 1.5 G
+// atomics/s), so a warp stages its winners and reserves for at least
+// kStage - 31 of them at a time.
+constexpr uint32_t kStage = 128;
+struct WarpStage {
+  uint32_t v[kStage];
+  uint32_t cur[kBuckets];             // per-bucket counts, then cursors
+  unsigned long long base[kBuckets];  // reserved start of each bucket's run
+  uint8_t b[kStage];
+  uint32_t n;  // entries staged
+};
+
 struct BfsShared {
   uint64_t bstart[kBuckets + 1];
   uint64_t base[kBuckets];   // start of the current level's run inside each bucket region
@@ -118,6 +141,7 @@ struct BfsShared {
   int precheck;        // push reads the visited bit before claiming
   uint32_t tg_min;     // smallest thread-bin group: 32 / (lower bound of the bin's mean degree)
   uint32_t err_seen;   // the control block's error word at the start of the level
+  WarpStage* stage;    // per-warp stages (shared memory, overlaid on the solo lists)
   unsigned long long red[2];  // this CTA's share of the next frontier's degree sum and ids read
 };
 
@@ -131,33 +155,62 @@ __device__ __forceinline__ int find_bucket(const uint64_t* pre, int lo, int hi, 
   return lo;
 }
 
-// Appends the calling warp's winners (lanes with `won`, vertex v, degree
-// bucket b; wm = the ballot of `won`) to the next level's queue.  Lanes are
-// grouped by bucket with one ballot per distinct bucket (a few ALU steps; a
-// warp match instruction costs far more on the critical path of a small
-// level), then the lowest lane of every group reserves the group's slots with
-// one atomicAdd, all groups at once.  Warp-collective.
+// Writes the calling warp's staged winners to the next level's queue: a
+// per-bucket count in shared memory, one global atomicAdd per bucket present
+// (issued by different lanes at once), then every entry takes its slot from
+// the bucket's shared cursor.  Warp-collective.
 template <typename G>
-__device__ __forceinline__ void queue_append(const BfsArgs<G>& a, const BfsShared& S, bool won, uint32_t v,
-                                             uint32_t b, int nxt, uint32_t wm) {
+__device__ __noinline__ void stage_flush(const BfsArgs<G>& a, BfsShared& S, int nxt) {
+  WarpStage& W = S.stage[threadIdx.x >> 5];
   const uint32_t lane = lane_id();
-  uint32_t todo = wm, grp = 0;
-  while (todo) {
-    const uint32_t l = __ffs(todo) - 1;
-    const uint32_t bl = __shfl_sync(0xFFFFFFFFu, b, l);
-    const uint32_t g = __ballot_sync(0xFFFFFFFFu, won && b == bl);
-    if (won && b == bl) grp = g;
-    todo &= ~g;
+  const uint32_t ns = W.n;
+  for (uint32_t i = lane; i < (uint32_t)kBuckets; i += 32) W.cur[i] = 0;
+  __syncwarp();
+  for (uint32_t i = lane; i < ns; i += 32) atomicAdd(&W.cur[W.b[i]], 1u);
+  __syncwarp();
+  for (uint32_t i = lane; i < (uint32_t)kBuckets; i += 32) {
+    const uint32_t c = W.cur[i];
+    W.base[i] = c ? atomicAdd(&a.ctl->cnt[nxt][i].v, (unsigned long long)c) : 0ull;
+    W.cur[i] = 0;
   }
-  const uint32_t leader = won ? __ffs(grp) - 1 : 0;
-  unsigned long long pos = 0;
-  if (won && lane == leader) pos = atomicAdd(&a.ctl->cnt[nxt][b], (unsigned long long)__popc(grp));
-  pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-  if (won) {
-    const uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + pos + __popc(grp & lanemask_lt());
-    if (at < S.bstart[b + 1]) a.queue[at] = v;
+  __syncwarp();
+  for (uint32_t i = lane; i < ns; i += 32) {
+    const uint32_t b = W.b[i];
+    const uint32_t r = atomicAdd(&W.cur[b], 1u);
+    const uint64_t at = S.bstart[b] + S.base[b] + S.cnt[b] + W.base[b] + r;
+    if (at < S.bstart[b + 1]) a.queue[at] = W.v[i];
     else atomicCAS(&a.ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is claimed once
   }
+  __syncwarp();
+  if (lane == 0) W.n = 0;
+  __syncwarp();
+}
+
+// Stages the calling warp's winners (lanes with `won`: vertex v of degree
+// bucket b) and flushes once fewer than 32 free entries remain.  Warp-collective.
+template <typename G>
+__device__ __forceinline__ void stage_add(const BfsArgs<G>& a, BfsShared& S, bool won, uint32_t v, uint32_t b,
+                                          int nxt) {
+  const uint32_t m = __ballot_sync(0xFFFFFFFFu, won);
+  if (m == 0) return;
+  WarpStage& W = S.stage[threadIdx.x >> 5];
+  const uint32_t n0 = W.n;
+  if (won) {
+    const uint32_t slot = n0 + __popc(m & lanemask_lt());
+    W.v[slot] = v;
+    W.b[slot] = (uint8_t)b;
+  }
+  __syncwarp();
+  const uint32_t n1 = n0 + __popc(m);
+  if (lane_id() == 0) W.n = n1;
+  __syncwarp();
+  if (n1 > kStage - 32) stage_flush(a, S, nxt);
+}
+
+// The rest of the calling warp's stage, at the end of a phase.  Warp-collective.
+template <typename G>
+__device__ __forceinline__ void stage_drain(const BfsArgs<G>& a, BfsShared& S, int nxt) {
+  if (S.stage[threadIdx.x >> 5].n) stage_flush(a, S, nxt);
 }
 
 // Warp-collective: claim v for every lane with `cand`, then record the
@@ -175,8 +228,7 @@ __device__ __forceinline__ void claim_emit(const BfsArgs<G>& a, BfsShared& S, bo
   const uint32_t bit = 1u << (v & 31);
   const uint32_t d = cand ? a.g.degree(v) : 0u;  // read while the claim is in flight
   const bool won = cand && !(atomicOr(a.vis + (v >> 5), bit) & bit);
-  const uint32_t wm = __ballot_sync(0xFFFFFFFFu, won);
-  if (wm == 0) return;
+  if (!__any_sync(0xFFFFFFFFu, won)) return;
   uint32_t b = 0xFFFFFFFFu;
   if (won) {
     a.level[v] = next_level;
@@ -184,7 +236,53 @@ __device__ __forceinline__ void claim_emit(const BfsArgs<G>& a, BfsShared& S, bo
     acc_deg += d;
     b = (uint32_t)degree_bucket(d);
   }
-  queue_append(a, S, won, v, b, nxt, wm);
+  stage_add(a, S, won, v, b, nxt);
+}
+
+// claim_emit for K candidates per lane (v[k], parent u[k]), with the K
+// visited reads, the K degree reads, the K claims and the K queue
+// reservations each issued together, so that one warp keeps K chains of
+// memory operations in flight instead of one.  Warp-collective.
+template <typename G, bool kParents, int K>
+__device__ __forceinline__ void claim_emit_k(const BfsArgs<G>& a, BfsShared& S, const bool (&cand_in)[K],
+                                             const uint32_t (&v)[K], const uint32_t (&u)[K], uint32_t next_level,
+                                             int nxt, uint64_t& acc_deg) {
+  bool cand[K];
+  bool any = false;
+  if (S.precheck) {
+    uint32_t w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = cand_in[k] ? ld_cg(a.vis + (v[k] >> 5)) : 0u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      cand[k] = cand_in[k] && !((w[k] >> (v[k] & 31)) & 1u);
+      any |= cand[k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      cand[k] = cand_in[k];
+      any |= cand[k];
+    }
+  }
+  if (!__any_sync(0xFFFFFFFFu, any)) return;
+  uint32_t d[K], old[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) d[k] = cand[k] ? a.g.degree(v[k]) : 0u;
+#pragma unroll
+  for (int k = 0; k < K; ++k) old[k] = cand[k] ? atomicOr(a.vis + (v[k] >> 5), 1u << (v[k] & 31)) : ~0u;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const bool won = cand[k] && !(old[k] & (1u << (v[k] & 31)));
+    uint32_t b = 0xFFFFFFFFu;
+    if (won) {
+      a.level[v[k]] = next_level;
+      if (kParents) a.parent[v[k]] = u[k];
+      acc_deg += d[k];
+      b = (uint32_t)degree_bucket(d[k]);
+    }
+    stage_add(a, S, won, v[k], b, nxt);
+  }
 }
 
 template <typename G>
@@ -219,12 +317,18 @@ __device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, const Workers& wk,
     Seg s = a.g.seg(u);
     uint32_t per = (uint32_t)((s.len + K - 1) / K);
     uint32_t lo = chunk * per, hi = min(s.len, lo + per);
-    for (uint32_t base = lo; base < hi; base += blockDim.x) {
-      uint32_t e = base + threadIdx.x;
-      bool ok = e < hi;
-      uint32_t v = ok ? __ldg(s.p + e) : 0;
-      if (ok) ++acc_scan;
-      claim_emit<G, kParents>(a, S, ok, v, u, L + 1, nxt, acc_deg);
+    for (uint32_t base = lo; base < hi; base += blockDim.x * kPushK) {
+      bool ok[kPushK];
+      uint32_t v[kPushK], uu[kPushK];
+#pragma unroll
+      for (int k = 0; k < kPushK; ++k) {
+        const uint32_t e = base + k * blockDim.x + threadIdx.x;
+        ok[k] = e < hi;
+        v[k] = ok[k] ? __ldg(s.p + e) : 0u;
+        uu[k] = u;
+        acc_scan += ok[k];
+      }
+      claim_emit_k<G, kParents, kPushK>(a, S, ok, v, uu, L + 1, nxt, acc_deg);
     }
   }
   // warp bin: one warp per vertex
@@ -233,12 +337,18 @@ __device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, const Workers& wk,
     int b = find_bucket(S.pre, bt + 1, bw, j);
     uint32_t u = frontier_vertex(a, S, b, j - S.pre[b]);
     Seg s = a.g.seg(u);
-    for (uint32_t base = 0; base < s.len; base += 32) {
-      uint32_t e = base + lane;
-      bool ok = e < s.len;
-      uint32_t v = ok ? __ldg(s.p + e) : 0;
-      if (ok) ++acc_scan;
-      claim_emit<G, kParents>(a, S, ok, v, u, L + 1, nxt, acc_deg);
+    for (uint32_t base = 0; base < s.len; base += 32 * kPushK) {
+      bool ok[kPushK];
+      uint32_t v[kPushK], uu[kPushK];
+#pragma unroll
+      for (int k = 0; k < kPushK; ++k) {
+        const uint32_t e = base + k * 32 + lane;
+        ok[k] = e < s.len;
+        v[k] = ok[k] ? __ldg(s.p + e) : 0u;
+        uu[k] = u;
+        acc_scan += ok[k];
+      }
+      claim_emit_k<G, kParents, kPushK>(a, S, ok, v, uu, L + 1, nxt, acc_deg);
     }
   }
   // thread bin: 32 vertices per warp, their edges walked 32 at a time
@@ -262,6 +372,7 @@ __device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, const Workers& wk,
         claim_emit<G, kParents>(a, S, ok, v, u, L + 1, nxt, acc_deg);
       }
     }
+    stage_drain(a, S, nxt);
     return;
   }
   // Vertices per warp: 32 once every warp has a group of its own, fewer on
@@ -308,6 +419,7 @@ __device__ void push_phase(const BfsArgs<G>& a, BfsShared& S, const Workers& wk,
       claim_emit<G, kParents>(a, S, ok, v, ou, L + 1, nxt, acc_deg);
     }
   }
+  stage_drain(a, S, nxt);
 }
 
 // ---------------------------------------------------------------- pull
@@ -321,11 +433,10 @@ __device__ __forceinline__ bool in_frontier(const uint32_t* fb, uint32_t u) {
 // the words being the calling warp's own) and their queue slots (one atomic
 // per degree bucket).  Warp-collective.
 template <typename G, bool kParents>
-__device__ __forceinline__ void pull_emit(const BfsArgs<G>& a, const BfsShared& S, uint32_t* fbn, bool found,
+__device__ __forceinline__ void pull_emit(const BfsArgs<G>& a, BfsShared& S, uint32_t* fbn, bool found,
                                           uint32_t v, uint32_t par, uint32_t len, uint32_t L, int nxt,
                                           uint64_t& acc_deg) {
-  const uint32_t wm = __ballot_sync(0xFFFFFFFFu, found);
-  if (wm == 0) return;
+  if (!__any_sync(0xFFFFFFFFu, found)) return;
   uint32_t b = 0xFFFFFFFFu;
   if (found) {
     a.level[v] = L + 1;
@@ -337,7 +448,7 @@ __device__ __forceinline__ void pull_emit(const BfsArgs<G>& a, const BfsShared& 
     atomicOr(a.vis + (v >> 5), 1u << (v & 31));
     atomicOr(fbn + (v >> 5), 1u << (v & 31));
   }
-  queue_append(a, S, found, v, b, nxt, wm);
+  stage_add(a, S, found, v, b, nxt);
   __syncwarp();  // the word updates are seen by the warp's later readers
 }
 
@@ -363,7 +474,7 @@ struct PullDefer {
 };
 
 template <typename G, bool kParents>
-__device__ void pull_long(const BfsArgs<G>& a, const BfsShared& S, uint32_t* fbn, const uint32_t* fb,
+__device__ void pull_long(const BfsArgs<G>& a, BfsShared& S, uint32_t* fbn, const uint32_t* fb,
                           PullDefer& D, uint32_t cnt, uint32_t L, int nxt, bool no_exit, uint64_t& acc_deg,
                           uint64_t& acc_scan) {
   const uint32_t lane = lane_id();
@@ -555,6 +666,7 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
     }
   }
   if (ndef) pull_long<G, kParents>(a, S, fbn, fb, D, ndef, L, nxt, no_exit, acc_deg, acc_scan);
+  stage_drain(a, S, nxt);
   asm volatile("" ::"r"(sink));  // the ablation's reads are kept
 }
 
@@ -581,7 +693,7 @@ __device__ uint32_t level_top(const BfsArgs<G>& a, BfsShared& S, uint32_t L, boo
   const uint64_t m = a.g.num_edges();
   BfsCtl* ctl = a.ctl;
   const int cur = L % 3, old = (L + 2) % 3;
-  if (tid < (uint32_t)kBuckets) S.cnt[tid] = (uint32_t)ld_cg(&ctl->cnt[cur][tid]);
+  if (tid < (uint32_t)kBuckets) S.cnt[tid] = (uint32_t)ld_cg(&ctl->cnt[cur][tid].v);
   else if (tid == kBuckets) S.mf = ld_cg(&ctl->sdeg[cur]);
   else if (tid == kBuckets + 1 && owner) S.scan_prev = ld_cg(&ctl->scanned[cur]);
   else if (tid == kBuckets + 2) S.err_seen = ld_cg(&ctl->err);
@@ -678,7 +790,7 @@ __device__ uint32_t level_top(const BfsArgs<G>& a, BfsShared& S, uint32_t L, boo
       }
     }
   } else if (owner && tid >= 64 && tid < 64 + (uint32_t)kBuckets) {
-    ctl->cnt[old][tid - 64] = 0;
+    ctl->cnt[old][tid - 64].v = 0;
   } else if (owner && tid == 64 + (uint32_t)kBuckets) {
     ctl->sdeg[old] = 0;
     ctl->scanned[old] = 0;
@@ -810,7 +922,7 @@ __device__ void fast_solo(const BfsArgs<G>& a, BfsShared& S, SoloShared& Q, uint
     SoloEntry* B = Q.list[cur ^ 1];
     solo_prefix(Q, A, nA);
     const uint32_t TE = Q.pre[nA];
-    if (tid < (uint32_t)kBuckets) ctl->cnt[nx][tid] = 0;
+    if (tid < (uint32_t)kBuckets) ctl->cnt[nx][tid].v = 0;
     if (tid == 0) {
       Q.n_next = 0;
       Q.spilled = 0;
@@ -857,7 +969,7 @@ __device__ void fast_solo(const BfsArgs<G>& a, BfsShared& S, SoloShared& Q, uint
           B[slot] = SoloEntry{sg.p, w, sg.len};
         } else {
           const int b = degree_bucket(sg.len);
-          const unsigned long long pos = atomicAdd(&ctl->cnt[nx][b], 1ull);
+          const unsigned long long pos = atomicAdd(&ctl->cnt[nx][b].v, 1ull);
           const uint64_t at = S.bstart[b] + S.base[b] + pos;
           if (at < S.bstart[b + 1]) a.queue[at] = w;
           else atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);  // cannot happen: each vertex is claimed once
@@ -925,7 +1037,7 @@ __device__ void fast_solo(const BfsArgs<G>& a, BfsShared& S, SoloShared& Q, uint
     for (uint32_t i = tid; i < kept; i += blockDim.x) {
       const SoloEntry e = B[i];
       const int b = degree_bucket(e.len);
-      const unsigned long long pos = atomicAdd(&ctl->cnt[L % 3][b], 1ull);
+      const unsigned long long pos = atomicAdd(&ctl->cnt[L % 3][b].v, 1ull);
       const uint64_t at = S.bstart[b] + S.base[b] + pos;
       if (at < S.bstart[b + 1]) a.queue[at] = e.v;
       else atomicCAS(&ctl->err, 0u, (uint32_t)BYO_ERR_CUDA);
@@ -936,8 +1048,8 @@ __device__ void fast_solo(const BfsArgs<G>& a, BfsShared& S, SoloShared& Q, uint
     }
     // the counters of the next two levels start from zero
     if (tid < (uint32_t)kBuckets) {
-      ctl->cnt[(L + 1) % 3][tid] = 0;
-      ctl->cnt[(L + 2) % 3][tid] = 0;
+      ctl->cnt[(L + 1) % 3][tid].v = 0;
+      ctl->cnt[(L + 2) % 3][tid].v = 0;
     }
     if (tid == 0) {
       ctl->sdeg[(L + 1) % 3] = 0;
@@ -953,7 +1065,13 @@ __device__ void fast_solo(const BfsArgs<G>& a, BfsShared& S, SoloShared& Q, uint
 template <typename G, bool kParents>
 __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
   __shared__ BfsShared S;
-  __shared__ SoloShared Q;
+  // the solo lists and the warp stages are never in use at the same time
+  // (every phase drains its stage before the level ends)
+  __shared__ union SoloOrStage {
+    SoloShared solo;
+    WarpStage stage[kBfsThreads / 32];
+  } U;
+  SoloShared& Q = U.solo;
   __shared__ PullDefer defer[kBfsThreads / 32];
   __shared__ float wsm[kMlpParams];
   sched_stage_weights(a.sp, wsm);
@@ -977,12 +1095,14 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
   // has nothing to scan: it starts as visited, so that pulls skip it
   for (uint64_t w = gtid; w < a.nw; w += gthreads) a.vis[w] = a.zmask ? __ldg(a.zmask + w) : 0u;
   if (owner) {
-    for (int i = tid; i < 3 * kBuckets; i += blockDim.x) (&ctl->cnt[0][0])[i] = 0;
+    for (int i = tid; i < 3 * kBuckets; i += blockDim.x) ctl->cnt[i / kBuckets][i % kBuckets].v = 0;
     if (tid < 3) {
       ctl->sdeg[tid] = 0;
       ctl->scanned[tid] = 0;
     }
   }
+  if (tid < kBfsThreads / 32) U.stage[tid].n = 0;
+  if (tid == 0) S.stage = U.stage;
   if (tid <= (uint32_t)kBuckets) S.bstart[tid] = a.bstart[tid];
   if (tid < (uint32_t)kBuckets) S.base[tid] = 0;
   if (tid == 0) {
@@ -1003,7 +1123,7 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
     if (kParents) a.parent[s] = s;
     a.vis[s >> 5] = ld_cg(a.vis + (s >> 5)) | (1u << (s & 31));
     a.queue[S.bstart[b]] = s;
-    ctl->cnt[0][b] = 1;
+    ctl->cnt[0][b].v = 1;
     ctl->sdeg[0] = d;
   }
   if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
@@ -1033,6 +1153,8 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
         uint32_t Ls = L;
         bool done = false;
         fast_solo<G, kParents>(a, S, Q, Ls, done, t_begin);
+        __syncthreads();
+        if (tid < kBfsThreads / 32) U.stage[tid].n = 0;  // the solo lists overlaid the stages
         if (tid == 0) {
           ctl->solo_L = Ls;
           ctl->solo_done = done ? 1u : 0u;
