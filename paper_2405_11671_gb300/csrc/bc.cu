@@ -40,31 +40,85 @@ __global__ void bc_init_kernel(uint32_t n, uint32_t src, const uint32_t* __restr
   if (lane_id() == 0 && mx) atomicMax(maxl, mx);
 }
 
+// Levels below kBcSmemLevels are counted in shared memory and reach the
+// global counters once per CTA (a few popular levels hold most vertices, and
+// one address takes about 1.5 G atomics/s); deeper levels, which a deep
+// graph spreads thinly, count directly.
+constexpr uint32_t kBcSmemLevels = 64;
+constexpr int kBcItems = 8;  // vertices per thread per scatter tile
+
 // per level: how many vertices (cnt) and how many of them are light (lcnt)
 template <typename G>
 __global__ void bc_hist_kernel(G g, const uint32_t* __restrict__ level, uint32_t* cnt, uint32_t* lcnt) {
+  __shared__ uint32_t sc[kBcSmemLevels], sl[kBcSmemLevels];
+  for (uint32_t i = threadIdx.x; i < kBcSmemLevels; i += blockDim.x) sc[i] = sl[i] = 0;
+  __syncthreads();
   const uint32_t n = g.num_vertices();
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t l = level[v];
     if (l == kInf) continue;
-    atomicAdd(cnt + l, 1u);
-    if (g.degree((uint32_t)v) < kHeavy) atomicAdd(lcnt + l, 1u);
+    const bool light = g.degree((uint32_t)v) < kHeavy;
+    if (l < kBcSmemLevels) {
+      atomicAdd(&sc[l], 1u);
+      if (light) atomicAdd(&sl[l], 1u);
+    } else {
+      atomicAdd(cnt + l, 1u);
+      if (light) atomicAdd(lcnt + l, 1u);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kBcSmemLevels; i += blockDim.x) {
+    if (sc[i]) atomicAdd(cnt + i, sc[i]);
+    if (sl[i]) atomicAdd(lcnt + i, sl[i]);
   }
 }
 
 // vertices grouped by level: light ones from the start of their level's range,
-// heavy ones from its end
+// heavy ones from its end.  Per tile of blockDim * kBcItems vertices a CTA
+// counts its vertices per level, reserves each level's run with one atomic,
+// and places them from shared cursors.
 template <typename G>
 __global__ void bc_scatter_kernel(G g, const uint32_t* __restrict__ level, const uint64_t* __restrict__ lstart,
                                   uint32_t* lcur, uint32_t* hcur, uint32_t* order) {
+  __shared__ uint32_t cl[kBcSmemLevels], ch[kBcSmemLevels], bl[kBcSmemLevels], bh[kBcSmemLevels];
   const uint32_t n = g.num_vertices();
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t l = level[v];
-    if (l == kInf) continue;
-    uint64_t at;
-    if (g.degree((uint32_t)v) < kHeavy) at = lstart[l] + atomicAdd(lcur + l, 1u);
-    else at = lstart[l + 1] - 1 - atomicAdd(hcur + l, 1u);
-    order[at] = (uint32_t)v;
+  const uint64_t tile = (uint64_t)blockDim.x * kBcItems;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < n; t0 += (uint64_t)gridDim.x * tile) {
+    for (uint32_t i = threadIdx.x; i < kBcSmemLevels; i += blockDim.x) cl[i] = ch[i] = 0;
+    __syncthreads();
+    uint32_t lv[kBcItems];
+    bool light[kBcItems];
+#pragma unroll
+    for (int k = 0; k < kBcItems; ++k) {
+      const uint64_t v = t0 + (uint64_t)k * blockDim.x + threadIdx.x;
+      lv[k] = v < n ? level[v] : kInf;
+      light[k] = lv[k] != kInf && g.degree((uint32_t)v) < kHeavy;
+      if (lv[k] < kBcSmemLevels) atomicAdd(light[k] ? &cl[lv[k]] : &ch[lv[k]], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kBcSmemLevels; i += blockDim.x) {
+      bl[i] = cl[i] ? atomicAdd(lcur + i, cl[i]) : 0u;
+      bh[i] = ch[i] ? atomicAdd(hcur + i, ch[i]) : 0u;
+      cl[i] = 0;
+      ch[i] = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kBcItems; ++k) {
+      const uint32_t l = lv[k];
+      if (l == kInf) continue;
+      const uint64_t v = t0 + (uint64_t)k * blockDim.x + threadIdx.x;
+      uint64_t at;
+      if (l < kBcSmemLevels) {
+        if (light[k]) at = lstart[l] + bl[l] + atomicAdd(&cl[l], 1u);
+        else at = lstart[l + 1] - 1 - (bh[l] + atomicAdd(&ch[l], 1u));
+      } else {
+        if (light[k]) at = lstart[l] + atomicAdd(lcur + l, 1u);
+        else at = lstart[l + 1] - 1 - atomicAdd(hcur + l, 1u);
+      }
+      order[at] = (uint32_t)v;
+    }
+    __syncthreads();
   }
 }
 
@@ -207,11 +261,12 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
     cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (L + 1), s);
     cudaMemsetAsync(lcnt, 0, sizeof(uint32_t) * L, s);
     cudaMemsetAsync(cur, 0, sizeof(uint32_t) * 2 * L, s);
-    bc_hist_kernel<G><<<grid_for(n, kBcThreads), kBcThreads, 0, s>>>(view, level, cnt, lcnt);
+    const uint32_t gb = (uint32_t)sm_count() * 4;  // CTAs for the two grouping passes
+    bc_hist_kernel<G><<<gb, kBcThreads, 0, s>>>(view, level, cnt, lcnt);
     note_launch();
     st = scan_u32_to_u64(cnt, lstart, L + 1, nullptr, s);
     if (st == BYO_OK) {
-      bc_scatter_kernel<G><<<grid_for(n, kBcThreads), kBcThreads, 0, s>>>(view, level, lstart, cur, cur + L, order);
+      bc_scatter_kernel<G><<<gb, kBcThreads, 0, s>>>(view, level, lstart, cur, cur + L, order);
       note_launch();
       hstart.resize(L + 1);
       cudaError_t e = cudaGetLastError();

@@ -254,25 +254,57 @@ struct CompBfsArgs {
 // Warp-collective: the `cand` lanes claim vertex x (parent u) for level
 // next_level; winners get level/parent, go to the next queue and add their
 // degree to the next level's edge count (one atomic per warp each).
+// Winners of a warp waiting for their queue slots: the queue counter takes
+// every warp's reservations, so a warp reserves for at least
+// kCompStage - 31 winners at a time.
+constexpr uint32_t kCompStage = 128;
+struct CompStage {
+  uint32_t x[kCompStage];
+  uint32_t n;
+};
+
+template <typename OffT>
+__device__ __noinline__ void comp_stage_flush(const CompBfsArgs<OffT>& a, CompStage& W, int nxt) {
+  const uint32_t lane = lane_id();
+  const uint32_t ns = W.n;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&a.ctl->nq[nxt], (unsigned long long)ns);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  for (uint32_t i = lane; i < ns; i += 32) a.queue[(size_t)nxt * a.n + base + i] = W.x[i];
+  __syncwarp();
+  if (lane == 0) W.n = 0;
+  __syncwarp();
+}
+
+// Stages the lanes with `won` (vertex x); warp-collective.
+template <typename OffT>
+__device__ __forceinline__ void comp_stage_add(const CompBfsArgs<OffT>& a, CompStage& W, bool won, uint32_t x,
+                                               int nxt) {
+  const uint32_t m = __ballot_sync(0xFFFFFFFFu, won);
+  if (m == 0) return;
+  const uint32_t n0 = W.n;
+  if (won) W.x[n0 + __popc(m & lanemask_lt())] = x;
+  __syncwarp();
+  const uint32_t n1 = n0 + __popc(m);
+  if (lane_id() == 0) W.n = n1;
+  __syncwarp();
+  if (n1 > kCompStage - 32) comp_stage_flush(a, W, nxt);
+}
+
 template <typename OffT, bool kParents>
-__device__ __forceinline__ void comp_claim(const CompBfsArgs<OffT>& a, bool cand, uint32_t x, uint32_t u,
-                                           uint32_t next_level, int nxt, uint64_t& acc_deg) {
+__device__ __forceinline__ void comp_claim(const CompBfsArgs<OffT>& a, CompStage& W, bool cand, uint32_t x,
+                                           uint32_t u, uint32_t next_level, int nxt, uint64_t& acc_deg) {
   if (cand) cand = !((ld_cg(a.vis + (x >> 5)) >> (x & 31)) & 1u);
   if (__ballot_sync(0xFFFFFFFFu, cand) == 0) return;
   bool won = false;
   if (cand) won = !(atomicOr(a.vis + (x >> 5), 1u << (x & 31)) & (1u << (x & 31)));
-  const uint32_t wm = __ballot_sync(0xFFFFFFFFu, won);
-  if (wm == 0) return;
-  unsigned long long base = 0;
-  const uint32_t lane = lane_id();
-  if (lane == 0) base = atomicAdd(&a.ctl->nq[nxt], (unsigned long long)__popc(wm));
-  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  if (!__any_sync(0xFFFFFFFFu, won)) return;
   if (won) {
     a.level[x] = next_level;
     if (kParents) a.parent[x] = u;
-    a.queue[(size_t)nxt * a.n + base + __popc(wm & lanemask_lt())] = x;
     acc_deg += (uint64_t)(__ldg(a.off + x + 1) - __ldg(a.off + x));
   }
+  comp_stage_add(a, W, won, x, nxt);
 }
 
 __device__ __forceinline__ bool comp_in_frontier(const uint32_t* fb, uint32_t u) {
@@ -282,7 +314,10 @@ __device__ __forceinline__ bool comp_in_frontier(const uint32_t* fb, uint32_t u)
 template <typename OffT, bool kParents>
 __global__ void __launch_bounds__(kCompThreads, 4) comp_bfs_kernel(CompBfsArgs<OffT> a) {
   __shared__ unsigned long long red;
+  __shared__ CompStage stage[kCompThreads / 32];
   const uint32_t tid = threadIdx.x, lane = lane_id();
+  CompStage& W = stage[tid >> 5];
+  if (lane == 0) W.n = 0;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
   const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint32_t gwarp = (uint32_t)(gtid >> 5), nwarps = (uint32_t)(gthreads >> 5);
@@ -344,9 +379,10 @@ __global__ void __launch_bounds__(kCompThreads, 4) comp_bfs_kernel(CompBfsArgs<O
         while (ci < d) {
           const uint32_t T = warp_decode_window(a.bytes, &p, end, u, &ci, &prev, &x);
           if (T == 0) break;
-          comp_claim<OffT, kParents>(a, (T >> lane) & 1u, x, u, L + 1, nxt, acc);
+          comp_claim<OffT, kParents>(a, W, (T >> lane) & 1u, x, u, L + 1, nxt, acc);
         }
       }
+      if (W.n) comp_stage_flush(a, W, nxt);
       fb_valid = false;
     } else {
       uint32_t* fbc = a.fb + (size_t)cur * a.nw;
@@ -419,16 +455,14 @@ __global__ void __launch_bounds__(kCompThreads, 4) comp_bfs_kernel(CompBfsArgs<O
           a.vis[w] = vw | fm;
           fbn[w] = fm;
         }
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&ctl->nq[nxt], (unsigned long long)__popc(fm));
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (found) {
           a.level[x] = L + 1;
           if (kParents) a.parent[x] = par;
-          a.queue[(size_t)nxt * a.n + base + __popc(fm & lanemask_lt())] = x;
           acc += d;
         }
+        comp_stage_add(a, W, found, x, nxt);
       }
+      if (W.n) comp_stage_flush(a, W, nxt);
       fb_valid = true;
     }
     // the next level's edge count: one atomic per CTA
