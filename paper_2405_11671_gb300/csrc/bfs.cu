@@ -59,6 +59,7 @@ struct BfsCtl {
   uint32_t err;
   uint32_t levels;
   LineCounter cnt[3][kBuckets];  // appends per bucket, by level mod 3
+  LineCounter pull_next[3];      // pull: next batch of 32 words to hand out, by level mod 3
   unsigned long long sdeg[3];           // sum of degrees of the frontier being built
   unsigned long long scanned[3];        // neighbour ids read while building it
   // hand-over from a solo run of block 0 to the grid
@@ -511,11 +512,14 @@ __device__ void pull_long(const BfsArgs<G>& a, BfsShared& S, uint32_t* fbn, cons
 }
 
 template <typename G, bool kParents>
-__device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, uint32_t L, int nxt,
+__device__ bool pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, uint32_t L, int nxt,
                            uint64_t& acc_deg, uint64_t& acc_scan) {
-  // Each warp owns a contiguous range of 32-vertex words of the bit arrays, so
-  // it is the only writer of those words of `vis` and of the next frontier.
-  // Its lanes work as a pool: a lane scans one unvisited vertex at a time,
+  // Warps take batches of 32 words (1,024 vertices) from a per-level counter
+  // as they finish the previous batch, so a warp that meets long lists does
+  // not hold up the level; the visited and next-frontier bits are set with
+  // atomic ORs.  The next frontier's words are cleared first, each warp a
+  // fixed range, and a grid barrier separates that from the first emits.
+  // A warp's lanes work as a pool: a lane scans one unvisited vertex at a time,
   // eight ids per step, and takes the next pending vertex of the warp's range
   // as soon as it is done, so a long scan in one lane does not hold the
   // others (no warp-wide wait on the slowest vertex of a word).  A vertex
@@ -530,10 +534,12 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
   const uint32_t n = a.g.num_vertices();
   const uint32_t per = (a.nw + nwarps - 1) / nwarps;
   const uint32_t w_lo = min(a.nw, gwarp * per), w_hi = min(a.nw, w_lo + per);
-  for (uint32_t w = w_lo + lane; w < w_hi; w += 32) fbn[w] = 0;  // this warp's words only
-  __syncwarp();
+  for (uint32_t w = w_lo + lane; w < w_hi; w += 32) fbn[w] = 0;
+  if (!grid_barrier(&a.ctl->bar, gridDim.x, &a.ctl->err, a.limit_ns)) return false;
+  unsigned long long* next_batch = &a.ctl->pull_next[L % 3].v;
   // 32 words of pending (unvisited) bits are loaded at a time, one per lane
-  uint32_t batch = w_lo;        // first word of the loaded batch
+  uint32_t batch = 0;           // first word of the loaded batch
+  bool drained = false;         // the level's words are all handed out
   uint32_t pend_lane = 0;       // pending bits of word batch + lane
   uint32_t k = 32;              // next word of the batch to open (32 = load a new batch)
   uint32_t P = 0, Pw = 0;       // pending vertices of the open word, and its index
@@ -552,16 +558,23 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
     while (freeL) {
       if (P == 0) {
         if (k == 32) {
-          if (batch >= w_hi) break;
+          if (drained) break;
+          unsigned long long nb = 0;
+          if (lane == 0) nb = atomicAdd(next_batch, 32ull);
+          nb = __shfl_sync(0xFFFFFFFFu, nb, 0);
+          if (nb >= a.nw) {
+            drained = true;
+            break;
+          }
+          batch = (uint32_t)nb;
           const uint32_t w = batch + lane;
-          uint32_t vw = w < w_hi ? ld_cg(a.vis + w) : ~0u;
-          if (w < w_hi && w == a.nw - 1 && (n & 31)) vw |= ~0u << (n & 31);  // past n: not a vertex
+          uint32_t vw = w < a.nw ? ld_cg(a.vis + w) : ~0u;
+          if (w == a.nw - 1 && (n & 31)) vw |= ~0u << (n & 31);  // past n: not a vertex
           pend_lane = ~vw;
           k = 0;
         }
         const uint32_t any = __ballot_sync(0xFFFFFFFFu, pend_lane != 0 && lane >= k);
         if (any == 0) {
-          batch += 32;
           k = 32;
           continue;
         }
@@ -569,7 +582,6 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
         P = __shfl_sync(0xFFFFFFFFu, pend_lane, k);
         Pw = batch + k;
         ++k;
-        if (k == 32) batch += 32;
       }
       // the free lane of rank r takes the r-th pending vertex (lowest first)
       const uint32_t r = __popc(freeL & lanemask_lt());
@@ -668,6 +680,7 @@ __device__ void pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
   if (ndef) pull_long<G, kParents>(a, S, fbn, fb, D, ndef, L, nxt, no_exit, acc_deg, acc_scan);
   stage_drain(a, S, nxt);
   asm volatile("" ::"r"(sink));  // the ablation's reads are kept
+  return true;
 }
 
 // warp sum of v into a shared-memory accumulator of the CTA
@@ -794,6 +807,7 @@ __device__ uint32_t level_top(const BfsArgs<G>& a, BfsShared& S, uint32_t L, boo
   } else if (owner && tid == 64 + (uint32_t)kBuckets) {
     ctl->sdeg[old] = 0;
     ctl->scanned[old] = 0;
+    ctl->pull_next[old].v = 0;
   }
   __syncthreads();
   return S.nf;
@@ -1073,8 +1087,7 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
   } U;
   SoloShared& Q = U.solo;
   __shared__ PullDefer defer[kBfsThreads / 32];
-  __shared__ float wsm[kMlpParams];
-  sched_stage_weights(a.sp, wsm);
+  sched_stage_weights(a.sp);
   const uint32_t tid = threadIdx.x;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
   const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
@@ -1099,6 +1112,7 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
     if (tid < 3) {
       ctl->sdeg[tid] = 0;
       ctl->scanned[tid] = 0;
+      ctl->pull_next[tid].v = 0;
     }
   }
   if (tid < kBfsThreads / 32) U.stage[tid].n = 0;
@@ -1219,7 +1233,7 @@ __global__ void __launch_bounds__(kBfsThreads, 4) bfs_kernel(BfsArgs<G> a) {
         }
         if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
       }
-      pull_phase<G, kParents>(a, S, defer, L, nxt, acc_deg, acc_scan);
+      if (!pull_phase<G, kParents>(a, S, defer, L, nxt, acc_deg, acc_scan)) return;
     } else {
       push_phase<G, kParents>(a, S, grid_wk, L, nxt, acc_deg, acc_scan);
     }

@@ -267,6 +267,10 @@ byo_status sched_params(const byo_sched* s, SchedParams* out) {
   out->bw = bw;
   out->alpha = d.alpha;
   out->beta = d.beta;
+  // whole-number constants (the usual case) let the device test in integers
+  auto whole = [](float x) -> uint32_t { return (x >= 1.0f && x <= 1048576.0f && x == floorf(x)) ? (uint32_t)x : 0u; };
+  out->alpha_i = whole(d.alpha);
+  out->beta_i = whole(d.beta);
   out->w = d.mode == BYO_SCHED_LEARNED ? mlp_device_params(d.mlp) : nullptr;
   out->flags = d.flags;
   return BYO_OK;

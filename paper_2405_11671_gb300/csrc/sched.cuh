@@ -37,6 +37,7 @@ struct SchedParams {
   int fixed_action;
   int bt, bw;  // log2 of thr_thread / thr_warp
   float alpha, beta;
+  uint32_t alpha_i, beta_i;  // alpha and beta when they are whole numbers (<= 2^20), else 0
   const float* w;  // MLP parameters (LEARNED): global on the host side, the CTA's staged copy in kernels
   uint32_t flags;  // BYO_SCHED_NO_EARLY_EXIT | BYO_SCHED_SEQUENTIAL_MAPS
 };
@@ -47,17 +48,19 @@ struct SchedParams {
 // so that the 32 lanes, one per hidden unit, read 32 consecutive words
 // (no bank conflicts).  Every caller of sched_decide in LEARNED mode stages
 // the network first.
-__device__ __forceinline__ void sched_stage_weights(SchedParams& sp, float* smem_w) {
+__shared__ float g_sched_w[kMlpParams];
+
+__device__ __forceinline__ void sched_stage_weights(SchedParams& sp) {
   if (sp.mode != BYO_SCHED_LEARNED || sp.w == nullptr) return;
   constexpr int o1 = kHidden * kFeatures, o2 = o1 + kHidden, o3 = o2 + kHidden * kHidden;
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
     int d = i;
     if (i < o1) d = (i % kFeatures) * kHidden + i / kFeatures;                  // W1 [32 x 12]
     else if (i >= o2 && i < o3) d = o2 + ((i - o2) % kHidden) * kHidden + (i - o2) / kHidden;  // W2 [32 x 32]
-    smem_w[d] = __ldg(sp.w + i);
+    g_sched_w[d] = __ldg(sp.w + i);
   }
   __syncthreads();
-  sp.w = smem_w;
+  sp.w = g_sched_w;
 }
 
 struct SchedFeatures {
@@ -75,19 +78,26 @@ byo_status sched_params(const byo_sched* s, SchedParams* out);
 // Host: device pointer of a network's FP32 parameters (packed as in the oracle).
 const float* mlp_device_params(const byo_mlp* m);
 
+__device__ __forceinline__ float u64_to_float(uint64_t v) {
+  return fmaf((float)(uint32_t)(v >> 32), 4294967296.0f, (float)(uint32_t)v);
+}
+
 // The 12 network inputs, all in [0, ~1]: log-scaled sizes, ratios and the
 // degree histogram of the frontier.  Host code that builds training samples
-// from byo_bfs_iter records computes the same numbers.
-__host__ __device__ inline void sched_feature_vector(const SchedFeatures& f, float* x) {
-  x[0] = log2f(1.0f + (float)f.nf) / 32.0f;
-  x[1] = log2f(1.0f + (float)f.mf) / 40.0f;
-  x[2] = log2f(1.0f + (float)f.nu) / 32.0f;
-  x[3] = log2f(1.0f + (float)f.mu) / 40.0f;
-  x[4] = log2f(1.0f + (float)f.n) / 32.0f;
-  x[5] = log2f(1.0f + (float)f.m) / 40.0f;
-  x[6] = (float)f.nf / (float)(f.n ? f.n : 1);
-  x[7] = (float)((double)f.mf / (double)(f.mf + f.mu + 1));
-  float inv = 1.0f / (float)(f.nf ? f.nf : 1);
+// from byo_bfs_iter records computes the same quantities (in double
+// precision; the network does not depend on the last bits).  On the device
+// they are on the critical path of every level, so they use the hardware's
+// approximate base-2 logarithm and division (each accurate to a few ulp).
+__device__ __forceinline__ void sched_feature_vector(const SchedFeatures& f, float* x) {
+  x[0] = __log2f(1.0f + (float)f.nf) * (1.0f / 32.0f);
+  x[1] = __log2f(1.0f + u64_to_float(f.mf)) * (1.0f / 40.0f);
+  x[2] = __log2f(1.0f + u64_to_float(f.nu)) * (1.0f / 32.0f);
+  x[3] = __log2f(1.0f + u64_to_float(f.mu)) * (1.0f / 40.0f);
+  x[4] = __log2f(1.0f + u64_to_float(f.n)) * (1.0f / 32.0f);
+  x[5] = __log2f(1.0f + u64_to_float(f.m)) * (1.0f / 40.0f);
+  x[6] = __fdividef((float)f.nf, u64_to_float(f.n ? f.n : 1));
+  x[7] = __fdividef(u64_to_float(f.mf), u64_to_float(f.mf + f.mu + 1));
+  const float inv = __fdividef(1.0f, (float)(f.nf ? f.nf : 1));
   for (int k = 0; k < 4; ++k) x[8 + k] = (float)f.h[k] * inv;
 }
 
@@ -104,26 +114,32 @@ __device__ __forceinline__ void sched_bins(const SchedParams& sp, int action, in
   }
 }
 
-// Whether the learned schedule may pull: where either Beamer test would.
-__device__ __forceinline__ bool sched_pull_allowed(const SchedParams& sp, const SchedFeatures& f) {
-  return (double)f.mf * (double)sp.alpha > (double)f.mu || (double)f.nf * (double)sp.beta >= (double)f.n;
-}
-
 // Warp-collective (all 32 lanes of one warp); returns the action on every lane.
 __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFeatures& f, int prev_dir) {
   if (sp.mode == BYO_SCHED_FIXED) return sp.fixed_action;
   if (sp.mode == BYO_SCHED_PUSH) return 1;
   if (sp.mode == BYO_SCHED_PULL) return 0;
-  // the two tests as products (alpha, beta > 0): a division would cost more
-  // than the rest of the decision on this part's FP64 pipe
-  const int beamer = prev_dir == 1 ? ((double)f.mf * (double)sp.alpha > (double)f.mu ? 0 : 1)
-                                    : ((double)f.nf * (double)sp.beta < (double)f.n ? 1 : 0);
+  // The decision sits on the critical path of every level, and this part's
+  // FP64 pipe is narrow: the two Beamer tests (as products, alpha and beta >
+  // 0) run on lane 0 alone and reach the other lanes by a shuffle.
+  const uint32_t lane = lane_id();
+  uint32_t tests = 0;
+  if (lane == 0) {
+    // push -> pull: mf * alpha > mu; pull -> push: nf * beta < n (exact in
+    // 128-bit integers for whole-number constants)
+    const bool p2p = sp.alpha_i ? (unsigned __int128)f.mf * sp.alpha_i > (unsigned __int128)f.mu
+                                : (double)f.mf * (double)sp.alpha > (double)f.mu;
+    const bool small = sp.beta_i ? (uint64_t)f.nf * sp.beta_i < f.n : (double)f.nf * (double)sp.beta < (double)f.n;
+    tests = (p2p ? 1u : 0u) | (small ? 2u : 0u);
+  }
+  tests = __shfl_sync(0xFFFFFFFFu, tests, 0);
+  const int beamer = prev_dir == 1 ? ((tests & 1u) ? 0 : 1) : ((tests & 2u) ? 1 : 0);
   if (sp.mode == BYO_SCHED_HEURISTIC || sp.w == nullptr) return beamer;
   // LEARNED: lane j owns hidden unit j of both layers
-  const uint32_t lane = lane_id();
   float x[kFeatures];
   sched_feature_vector(f, x);
-  const float* W1 = sp.w;
+  // the staged copy, named directly so that its reads are shared-memory loads
+  const float* W1 = g_sched_w;
   const float* b1 = W1 + kHidden * kFeatures;
   const float* W2 = b1 + kHidden;
   const float* b2 = W2 + kHidden * kHidden;
@@ -141,7 +157,8 @@ __device__ __forceinline__ int sched_decide(const SchedParams& sp, const SchedFe
     a2[k & 3] = fmaf(W2[k * kHidden + lane], __shfl_sync(0xFFFFFFFFu, h1, k), a2[k & 3]);
   const float h2 = fmaxf((a2[0] + a2[1]) + (a2[2] + a2[3]), 0.0f);
   const bool solo_ok = f.mf <= kSoloMaxEdges && f.nf <= kSoloMaxVertices && !(sp.flags & BYO_SCHED_SEQUENTIAL_MAPS);
-  const bool pull_ok = sched_pull_allowed(sp, f);
+  // pull only where either Beamer test would pull
+  const bool pull_ok = (tests & 1u) || !(tests & 2u);
   int best = -1;  // action 1 is always allowed
   float bestz = 0.0f;
 #pragma unroll

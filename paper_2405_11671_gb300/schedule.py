@@ -46,7 +46,8 @@ DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "sched_m
 
 def feature_vector(nf, mf, nu, mu, n, m, hist) -> np.ndarray:
     """The 12 network inputs of one iteration; the same formula as the device
-    function that feeds the network inside the BFS loop."""
+    function that feeds the network inside the BFS loop (which evaluates it
+    with the hardware's approximate logarithm and division, a few ulp apart)."""
     x = np.zeros(NUM_FEATURES, np.float32)
     f = np.float32
     x[0] = math.log2(1.0 + nf) / 32.0
