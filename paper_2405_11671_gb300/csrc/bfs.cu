@@ -540,9 +540,7 @@ __device__ bool pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
   // 32 words of pending (unvisited) bits are loaded at a time, one per lane
   uint32_t batch = 0;           // first word of the loaded batch
   bool drained = false;         // the level's words are all handed out
-  uint32_t pend_lane = 0;       // pending bits of word batch + lane
-  uint32_t k = 32;              // next word of the batch to open (32 = load a new batch)
-  uint32_t P = 0, Pw = 0;       // pending vertices of the open word, and its index
+  uint32_t pend_lane = 0;       // pending bits of word batch + lane not taken yet
   uint32_t ndef = 0;            // deferred vertices
   uint32_t v = kInf;            // this lane's vertex
   const uint32_t* al = nullptr;
@@ -554,44 +552,52 @@ __device__ bool pull_phase(const BfsArgs<G>& a, BfsShared& S, PullDefer* defer, 
   uint32_t sink = 0;
   while (true) {
     // free lanes take pending vertices, opening words as needed
+    // free lanes take the batch's first pending vertices, in word order, all
+    // at once: a warp scan of the words' pending counts (one word per lane),
+    // then each taking lane finds its word by a 5-step search over the scan
     uint32_t freeL = __ballot_sync(0xFFFFFFFFu, v == kInf);
     while (freeL) {
-      if (P == 0) {
-        if (k == 32) {
-          if (drained) break;
-          unsigned long long nb = 0;
-          if (lane == 0) nb = atomicAdd(next_batch, 32ull);
-          nb = __shfl_sync(0xFFFFFFFFu, nb, 0);
-          if (nb >= a.nw) {
-            drained = true;
-            break;
-          }
-          batch = (uint32_t)nb;
-          const uint32_t w = batch + lane;
-          uint32_t vw = w < a.nw ? ld_cg(a.vis + w) : ~0u;
-          if (w == a.nw - 1 && (n & 31)) vw |= ~0u << (n & 31);  // past n: not a vertex
-          pend_lane = ~vw;
-          k = 0;
+      if (__ballot_sync(0xFFFFFFFFu, pend_lane != 0) == 0) {  // the batch is used up
+        if (drained) break;
+        unsigned long long nb = 0;
+        if (lane == 0) nb = atomicAdd(next_batch, 32ull);
+        nb = __shfl_sync(0xFFFFFFFFu, nb, 0);
+        if (nb >= a.nw) {
+          drained = true;
+          break;
         }
-        const uint32_t any = __ballot_sync(0xFFFFFFFFu, pend_lane != 0 && lane >= k);
-        if (any == 0) {
-          k = 32;
-          continue;
-        }
-        k = __ffs(any) - 1;
-        P = __shfl_sync(0xFFFFFFFFu, pend_lane, k);
-        Pw = batch + k;
-        ++k;
+        batch = (uint32_t)nb;
+        const uint32_t w = batch + lane;
+        uint32_t vw = w < a.nw ? ld_cg(a.vis + w) : ~0u;
+        if (w == a.nw - 1 && (n & 31)) vw |= ~0u << (n & 31);  // past n: not a vertex
+        pend_lane = ~vw;
+        continue;
       }
-      // the free lane of rank r takes the r-th pending vertex (lowest first)
+      const uint32_t c = __popc(pend_lane);
+      uint32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      const uint32_t take = min((uint32_t)__popc(freeL), total);
       const uint32_t r = __popc(freeL & lanemask_lt());
-      const uint32_t np = __popc(P);
-      if (v == kInf && r < np) {
-        v = Pw * 32 + nth_set_bit(P, r);
+      const uint32_t rr = min(r, total - 1);
+      uint32_t j = 0;  // the first word whose inclusive count exceeds rr
+#pragma unroll
+      for (uint32_t step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(0xFFFFFFFFu, incl, j + step - 1) <= rr) j += step;
+      const uint32_t wbits = __shfl_sync(0xFFFFFFFFu, pend_lane, j);
+      const uint32_t wex = __shfl_sync(0xFFFFFFFFu, incl - c, j);
+      if (v == kInf && r < take) {
+        v = (batch + j) * 32 + nth_set_bit(wbits, rr - wex);
         fresh = true;
       }
-      const uint32_t taken = min((uint32_t)__popc(freeL), np);
-      P = taken >= np ? 0u : P & ~((1u << nth_set_bit(P, taken)) - 1u);  // drop the lowest `taken`
+      // the first `take` pending vertices of the batch are gone
+      const uint32_t excl = incl - c;
+      if (incl <= take) pend_lane = 0u;
+      else if (excl < take) pend_lane &= ~((1u << nth_set_bit(pend_lane, take - excl)) - 1u);
       freeL = __ballot_sync(0xFFFFFFFFu, v == kInf);
     }
     const bool active = v != kInf;
