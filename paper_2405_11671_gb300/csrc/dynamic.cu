@@ -144,15 +144,40 @@ __global__ void newdeg_kernel(DynView g, const uint64_t* __restrict__ seg_start,
   if (lane_id() == 0 && dsum) atomicAdd((unsigned long long*)delta, (unsigned long long)dsum);
 }
 
-// One warp per affected vertex writes its merged list into buf[toff[a] ...].
+// Long lists are split into chunks of kChunkIds ids, one warp task each, so
+// that a high-degree vertex (which a batch of uniformly chosen edges touches
+// every time) does not leave one warp working on it long after the others.
+constexpr uint32_t kChunkIds = 4096;
+
+// chunks per affected vertex: cm by the old list (merge), cc by the new one (copy-back)
+__global__ void chunk_count_kernel(DynView g, const uint32_t* __restrict__ seg_v, const uint32_t* __restrict__ newdeg,
+                                   uint64_t A, uint32_t* cm, uint32_t* cc) {
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t d = g.degree(seg_v[a]), nd = newdeg[a];
+    cm[a] = d > kChunkIds ? (d + kChunkIds - 1) / kChunkIds : 1u;
+    cc[a] = nd > kChunkIds ? (nd + kChunkIds - 1) / kChunkIds : 1u;
+  }
+}
+
+// item[j] = the affected vertex of chunk task j (starts = scan of the counts)
+__global__ void chunk_expand_kernel(const uint64_t* __restrict__ start, uint64_t A, uint32_t* item) {
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x)
+    for (uint64_t j = start[a]; j < start[a + 1]; ++j) item[j] = (uint32_t)a;
+}
+
+// One warp per chunk task writes its part of a merged list into buf[toff[a] ...]:
+// the old ids of the chunk, and (chunk 0 of an insert) the effective batch ids.
 __global__ void merge_kernel(DynView g, const uint32_t* __restrict__ cols, const uint64_t* __restrict__ seg_start,
                              const uint32_t* __restrict__ seg_v, const uint32_t* __restrict__ mark,
-                             const uint64_t* __restrict__ mrank, const uint64_t* __restrict__ toff, uint64_t A,
+                             const uint64_t* __restrict__ mrank, const uint64_t* __restrict__ toff,
+                             const uint32_t* __restrict__ item, const uint64_t* __restrict__ cstart, uint64_t NC,
                              bool insert, uint32_t* __restrict__ buf) {
   const uint32_t lane = lane_id();
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t a = w0; a < A; a += nw) {
+  for (uint64_t t = w0; t < NC; t += nw) {
+    const uint32_t a = item[t];
+    const uint32_t c = (uint32_t)(t - cstart[a]);
     const uint32_t v = seg_v[a];
     const Seg s = g.seg(v);
     const uint64_t b0 = seg_start[a], b1 = seg_start[a + 1];
@@ -160,8 +185,9 @@ __global__ void merge_kernel(DynView g, const uint32_t* __restrict__ cols, const
     const uint32_t* bcol = cols + b0;
     const uint64_t r0 = mrank[b0];
     uint32_t* out = buf + toff[a];
+    const uint32_t i1 = min(s.len, (c + 1) * kChunkIds);
     // old ids
-    for (uint32_t i = lane; i < s.len; i += 32) {
+    for (uint32_t i = c * kChunkIds + lane; i < i1; i += 32) {
       uint32_t x = __ldg(s.p + i);
       uint32_t j = lower_bound(bcol, blen, x);  // batch ids < x
       uint32_t marked_before = (uint32_t)(mrank[b0 + j] - r0);
@@ -173,7 +199,7 @@ __global__ void merge_kernel(DynView g, const uint32_t* __restrict__ cols, const
       }
     }
     // effective batch ids (insert only)
-    if (insert) {
+    if (insert && c == 0) {
       for (uint32_t q = lane; q < blen; q += 32) {
         if (mark[b0 + q]) {
           uint32_t y = __ldg(bcol + q);
@@ -231,14 +257,19 @@ __global__ void clamp_tops_kernel(long long* tops) {
   if (threadIdx.x < kClasses && tops[threadIdx.x] < 0) tops[threadIdx.x] = 0;
 }
 
+// One warp per chunk task copies its part of a merged list to the new
+// storage; chunk 0 also writes the inline ids and the vertex record.
 __global__ void copyback_kernel(DynVertex* vtx, uint32_t* pool, const uint32_t* __restrict__ seg_v,
                                 const uint32_t* __restrict__ newdeg, const uint64_t* __restrict__ new_run,
                                 const uint32_t* __restrict__ new_cls, const uint64_t* __restrict__ toff,
-                                const uint32_t* __restrict__ buf, uint64_t A, uint32_t icap) {
+                                const uint32_t* __restrict__ buf, const uint32_t* __restrict__ item,
+                                const uint64_t* __restrict__ cstart, uint64_t NC, uint32_t icap) {
   const uint32_t lane = lane_id();
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t a = w0; a < A; a += nw) {
+  for (uint64_t t = w0; t < NC; t += nw) {
+    const uint32_t a = item[t];
+    const uint32_t c = (uint32_t)(t - cstart[a]);
     DynVertex* r = vtx + seg_v[a];
     const uint32_t nd = newdeg[a];
     const uint32_t* src = buf + toff[a];
@@ -246,10 +277,11 @@ __global__ void copyback_kernel(DynVertex* vtx, uint32_t* pool, const uint32_t* 
       if (lane < kInline) r->inl[lane] = lane < nd ? src[lane] : kInf;
     } else {
       uint32_t* dst = pool + new_run[a] * kBlockIds;
-      for (uint32_t i = lane; i < nd; i += 32) dst[i] = src[i];
+      const uint32_t i1 = min(nd, (c + 1) * kChunkIds);
+      for (uint32_t i = c * kChunkIds + lane; i < i1; i += 32) dst[i] = src[i];
     }
     __syncwarp();
-    if (lane == 0) {
+    if (lane == 0 && c == 0) {
       r->deg = nd;
       r->cls = new_cls[a];
       r->run = nd <= icap ? 0 : new_run[a];
@@ -351,6 +383,9 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
   const DynView view = dyn_view(g);
   uint32_t *flags = nullptr, *seg_v = nullptr, *mark = nullptr, *newdeg = nullptr, *buf = nullptr;
   uint32_t *new_cls = nullptr, *free_cls = nullptr;
+  uint32_t *cm = nullptr, *cc = nullptr, *item_m = nullptr, *item_c = nullptr;
+  uint64_t *mstart = nullptr, *cstart = nullptr;
+  uint64_t NM = 0, NCC = 0;
   uint64_t *idx = nullptr, *seg_start = nullptr, *mrank = nullptr, *toff = nullptr;
   uint64_t *new_run = nullptr, *free_run = nullptr;
   long long* delta = nullptr;
@@ -389,9 +424,27 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
     st = scan_u32_to_u64(newdeg, toff, A, &T, s);
   }
   if (st == BYO_OK) st = tmp_alloc_t(&buf, T + 1, s, "merge buffer");
+  // chunk tasks of the merge (old lists) and of the copy-back (new lists)
+  if (st == BYO_OK) st = tmp_alloc_t(&cm, A + 1, s, "merge chunk counts");
+  if (st == BYO_OK) st = tmp_alloc_t(&cc, A + 1, s, "copy chunk counts");
+  if (st == BYO_OK) st = tmp_alloc_t(&mstart, A + 1, s, "merge chunk starts");
+  if (st == BYO_OK) st = tmp_alloc_t(&cstart, A + 1, s, "copy chunk starts");
   if (st == BYO_OK) {
-    merge_kernel<<<grid_for(A * 32, 256), 256, 0, s>>>(view, cols, seg_start, seg_v, mark, mrank, toff, A, insert,
-                                                        buf);
+    chunk_count_kernel<<<grid_for(A, 256), 256, 0, s>>>(view, seg_v, newdeg, A, cm, cc);
+    note_launch();
+    cudaMemsetAsync(cm + A, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(cc + A, 0, sizeof(uint32_t), s);
+    st = scan_u32_to_u64(cm, mstart, A + 1, &NM, s);  // mstart[A] = all merge tasks
+  }
+  if (st == BYO_OK) st = scan_u32_to_u64(cc, cstart, A + 1, &NCC, s);
+  if (st == BYO_OK) st = tmp_alloc_t(&item_m, NM + 1, s, "merge chunk tasks");
+  if (st == BYO_OK) st = tmp_alloc_t(&item_c, NCC + 1, s, "copy chunk tasks");
+  if (st == BYO_OK) {
+    chunk_expand_kernel<<<grid_for(A, 256), 256, 0, s>>>(mstart, A, item_m);
+    chunk_expand_kernel<<<grid_for(A, 256), 256, 0, s>>>(cstart, A, item_c);
+    note_launch(2);
+    merge_kernel<<<grid_for(NM * 32, 256), 256, 0, s>>>(view, cols, seg_start, seg_v, mark, mrank, toff, item_m,
+                                                         mstart, NM, insert, buf);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_status(e, "merge_kernel");
@@ -421,8 +474,8 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
     alloc_kernel<<<grid_for(A, 256), 256, 0, s>>>(d->vtx, seg_v, newdeg, A, d->icap, d_stacks, d->tops, d->bump,
                                                    new_run, new_cls, free_run, free_cls);
     clamp_tops_kernel<<<1, 32, 0, s>>>(d->tops);
-    copyback_kernel<<<grid_for(A * 32, 256), 256, 0, s>>>(d->vtx, d->pool, seg_v, newdeg, new_run, new_cls, toff, buf,
-                                                           A, d->icap);
+    copyback_kernel<<<grid_for(NCC * 32, 256), 256, 0, s>>>(d->vtx, d->pool, seg_v, newdeg, new_run, new_cls, toff,
+                                                             buf, item_c, cstart, NCC, d->icap);
     free_kernel<<<grid_for(A, 256), 256, 0, s>>>(free_run, free_cls, A, d_stacks, d->tops, d_cap);
     note_launch(4);
     long long hdelta = 0;
@@ -451,6 +504,12 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
   tmp_free(free_cls, s);
   tmp_free(d_stacks, s);
   tmp_free(d_cap, s);
+  tmp_free(cm, s);
+  tmp_free(cc, s);
+  tmp_free(mstart, s);
+  tmp_free(cstart, s);
+  tmp_free(item_m, s);
+  tmp_free(item_c, s);
   // the batch is applied; if the buckets cannot be re-derived now (no memory
   // for the sort), the next call that reads them does it
   if (st == BYO_OK) {
