@@ -256,6 +256,7 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
   if (st == BYO_OK) st = tmp_alloc_t(&lstart, L + 1, s, "BC level starts");
   if (st == BYO_OK) st = tmp_alloc_t(&order, n, s, "BC level order");
   std::vector<uint64_t> hstart;
+  std::vector<uint32_t> hlight;  // light vertices per level
   if (st == BYO_OK) {
     ProfScope ps("bc_group", s);
     cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (L + 1), s);
@@ -269,9 +270,11 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
       bc_scatter_kernel<G><<<gb, kBcThreads, 0, s>>>(view, level, lstart, cur, cur + L, order);
       note_launch();
       hstart.resize(L + 1);
+      hlight.resize(L);
       cudaError_t e = cudaGetLastError();
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(hstart.data(), lstart, sizeof(uint64_t) * (L + 1), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hlight.data(), lcnt, sizeof(uint32_t) * L, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) st = cuda_status(e, "bc grouping");
     }
@@ -282,12 +285,17 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
       uint64_t want = (c * kGroup + kBcThreads - 1) / kBcThreads;
       return (uint32_t)(want < cap ? (want ? want : 1) : cap);
     };
+    // heavy vertices (degree >= kHeavy, most of the edges on skewed graphs):
+    // a CTA each, as many CTAs as the level has of them, up to 8 per SM
+    auto heavy_blocks = [&](uint32_t l) {
+      const uint64_t h = hstart[l + 1] - hstart[l] - hlight[l];
+      return (uint32_t)(h < cap ? (h ? h : 1) : cap);
+    };
     {
       ProfScope ps("bc_forward", s);
       for (uint32_t l = 1; l < L; ++l) {
-        const uint64_t c = hstart[l + 1] - hstart[l];
-        const uint32_t lb = blocks(c);
-        bc_level_kernel<G, true><<<lb + (uint32_t)sm_count(), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
+        const uint32_t lb = blocks(hlight[l]);
+        bc_level_kernel<G, true><<<lb + heavy_blocks(l), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
                                                                                    level, sigma, delta, ratio);
         note_launch();
       }
@@ -295,9 +303,8 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
     {
       ProfScope ps("bc_backward", s);
       for (uint32_t l = depth; l-- > 1;) {  // the deepest level has no deeper neighbour; delta(s) stays 0
-        const uint64_t c = hstart[l + 1] - hstart[l];
-        const uint32_t lb = blocks(c);
-        bc_level_kernel<G, false><<<lb + (uint32_t)sm_count(), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
+        const uint32_t lb = blocks(hlight[l]);
+        bc_level_kernel<G, false><<<lb + heavy_blocks(l), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
                                                                                     level, sigma, delta, ratio);
         note_launch();
       }
