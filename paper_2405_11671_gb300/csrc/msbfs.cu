@@ -32,6 +32,7 @@ struct MsCtl {
 namespace {
 
 constexpr int kMsThreads = 256;
+constexpr uint32_t kMsWarpDeg = 128;  // bottom-up: vertices of at least this degree get a warp
 
 template <typename G>
 struct MsArgs {
@@ -116,30 +117,78 @@ __global__ void __launch_bounds__(kMsThreads) msbfs_kernel(MsArgs<G> a) {
     mseen += mf;
     const bool top_down = (double)mf * (double)a.alpha < (double)(m > mseen ? m - mseen : 0) || L == 0;
     if (top_down) {
-      // one warp per frontier vertex, lanes over its neighbours
-      for (uint64_t v = gwarp; v < n; v += nwarps) {
-        unsigned long long f = ld_cg(a.visit + v);
-        if (!f) continue;
-        Seg s = a.g.seg((uint32_t)v);
-        for (uint32_t k = lane; k < s.len; k += 32) {
-          uint32_t u = __ldg(s.p + k);
-          unsigned long long d = f & ~ld_cg(a.seen + u);
-          if (d) atomicOr(a.next + u, d);
+      // warps look at 32 vertices at a time for non-empty frontier words; each
+      // frontier vertex then gets the whole warp, lanes over its neighbours
+      for (uint64_t v0 = gwarp * 32; v0 < n; v0 += nwarps * 32) {
+        const uint64_t v = v0 + lane;
+        const unsigned long long f = v < n ? ld_cg(a.visit + v) : 0ull;
+        uint32_t fm = __ballot_sync(0xFFFFFFFFu, f != 0);
+        while (fm) {
+          const int l = __ffs(fm) - 1;
+          fm &= fm - 1;
+          const unsigned long long fu = __shfl_sync(0xFFFFFFFFu, f, l);
+          const Seg s = a.g.seg((uint32_t)(v0 + l));
+          for (uint32_t k = lane; k < s.len; k += 32) {
+            const uint32_t u = __ldg(s.p + k);
+            const unsigned long long d = fu & ~ld_cg(a.seen + u);
+            if (d) atomicOr(a.next + u, d);
+          }
         }
       }
     } else {
-      // one thread per vertex with unseen bits; early exit once all are found
+      // a thread per vertex of degree < kMsWarpDeg with unseen bits, eight
+      // neighbours' frontier words in flight per step; early exit once every
+      // source has reached it
       for (uint64_t v = gtid; v < n; v += gthreads) {
-        unsigned long long sv = ld_cg(a.seen + v);
+        const unsigned long long sv = ld_cg(a.seen + v);
         if (sv == full) continue;
-        Seg s = a.g.seg((uint32_t)v);
+        const Seg s = a.g.seg((uint32_t)v);
+        if (s.len >= kMsWarpDeg) continue;  // a warp takes it below
         unsigned long long acc = 0;
-        for (uint32_t k = 0; k < s.len; ++k) {
-          acc |= ld_cg(a.visit + __ldg(s.p + k));
-          if ((acc | sv) == full) break;
+        for (uint32_t k = 0; k < s.len && (acc | sv) != full; k += 8) {
+          unsigned long long w[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) w[j] = k + j < s.len ? ld_cg(a.visit + __ldg(s.p + k + j)) : 0ull;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc |= w[j];
         }
         acc &= ~sv;
         if (acc) a.next[v] = acc;
+      }
+      // a warp per vertex of degree >= kMsWarpDeg (found 32 at a time): 128
+      // neighbours per step, the words OR-ed across the warp
+      for (uint64_t v0 = gwarp * 32; v0 < n; v0 += nwarps * 32) {
+        const uint64_t v = v0 + lane;
+        unsigned long long sv = 0;
+        bool heavy = false;
+        if (v < n && a.g.degree((uint32_t)v) >= kMsWarpDeg) {
+          sv = ld_cg(a.seen + v);
+          heavy = sv != full;
+        }
+        uint32_t hm = __ballot_sync(0xFFFFFFFFu, heavy);
+        while (hm) {
+          const int l = __ffs(hm) - 1;
+          hm &= hm - 1;
+          const uint32_t x = (uint32_t)(v0 + l);
+          const unsigned long long sx = __shfl_sync(0xFFFFFFFFu, sv, l);
+          const Seg s = a.g.seg(x);
+          unsigned long long acc = 0;
+          for (uint32_t k = 0; k < s.len; k += 128) {
+            unsigned long long w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const uint32_t idx = k + 32 * j + lane;
+              w[j] = idx < s.len ? ld_cg(a.visit + __ldg(s.p + idx)) : 0ull;
+            }
+            acc |= (w[0] | w[1]) | (w[2] | w[3]);
+            const uint32_t lo = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)acc);
+            const uint32_t hi = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(acc >> 32));
+            acc = ((unsigned long long)hi << 32) | lo;
+            if ((acc | sx) == full) break;  // warp-uniform
+          }
+          acc &= ~sx;
+          if (lane == 0 && acc) a.next[x] = acc;
+        }
       }
     }
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
