@@ -85,7 +85,11 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
  * container comparison, Section 6.5): for the CSR, the offsets and the
  * neighbour ids ((n+1) x 4 or 8 + 4m); for the dynamic container, the 64-byte
  * vertex records and the 128-byte blocks of the runs its lists hold (free pool
- * capacity is not counted).  Library scratch is not included.  Synchronises
+ * capacity is not counted); for the compressed container, the offsets, the
+ * byte offsets ((n+1) x 8), the code bytes and, for lists of more than 4,096
+ * values, a 16-byte checkpoint every 4,096 values (where the value's code
+ * starts and the id before it, so that several warps can decode one long
+ * list) plus 12 bytes per such list.  Library scratch is not included.  Synchronises
  * the stream.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
 byo_status byo_space(const byo_graph* g, uint64_t* host_bytes, void* stream);
 

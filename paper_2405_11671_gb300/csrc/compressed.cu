@@ -29,14 +29,32 @@
 
 namespace byo {
 
+// A list is decoded from its start; so that several warps can share a long
+// list, every kCkptValues-th value of it has a checkpoint: where its code
+// starts and the id before it.
+constexpr uint32_t kCkptValues = 4096;
+struct Ckpt {
+  uint64_t byte;  // absolute offset of the value's first code byte
+  uint32_t prev;  // the id before it
+  uint32_t pad;
+};
+
 struct CompStore {
   uint64_t* boff = nullptr;   // n+1 byte offsets
   uint8_t* bytes = nullptr;   // boff[n] bytes + 48 of padding
   uint64_t nbytes = 0;
+  // vertices with checkpoints ((degree-1)/kCkptValues of them), ascending,
+  // and the index of each one's first checkpoint in ck
+  uint32_t* ckv = nullptr;
+  uint64_t* ckfirst = nullptr;
+  uint64_t nckv = 0;
+  Ckpt* ck = nullptr;
+  uint64_t nck = 0;
   // BFS scratch (first use)
   uint32_t* vis = nullptr;    // visited bits
   uint32_t* fb = nullptr;     // two frontier bit arrays
   uint32_t* queue = nullptr;  // two queues of n
+  uint2* spill = nullptr;     // push chunk tasks (nck + 1)
   void* ctl = nullptr;
 };
 
@@ -44,9 +62,13 @@ void comp_free(CompStore* c) {
   if (!c) return;
   dev_free(c->boff);
   dev_free(c->bytes);
+  dev_free(c->ckv);
+  dev_free(c->ckfirst);
+  dev_free(c->ck);
   dev_free(c->vis);
   dev_free(c->fb);
   dev_free(c->queue);
+  dev_free(c->spill);
   dev_free(c->ctl);
   delete c;
 }
@@ -87,14 +109,51 @@ __global__ void comp_size_kernel(CsrView<OffT> g, uint32_t* size) {
 
 // the codes of each vertex (a warp per vertex, 32 values per step: a warp
 // scan of the code lengths places every lane's bytes)
+// checkpoints per vertex (one at each value kCkptValues, 2 kCkptValues, ...
+// below the degree) and whether it has any
 template <typename OffT>
-__global__ void comp_write_kernel(CsrView<OffT> g, const uint64_t* __restrict__ boff, uint8_t* bytes) {
+__global__ void comp_ckcount_kernel(CsrView<OffT> g, uint32_t* cnt, uint32_t* has) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t d = g.degree((uint32_t)v);
+    cnt[v] = d ? (d - 1) / kCkptValues : 0u;
+    has[v] = cnt[v] ? 1u : 0u;
+  }
+}
+
+// the list of vertices with checkpoints and their first checkpoint
+__global__ void comp_cklist_kernel(uint32_t n, const uint32_t* __restrict__ has, const uint64_t* __restrict__ hpos,
+                                   const uint64_t* __restrict__ first, uint32_t* ckv, uint64_t* ckfirst) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+    if (has[v]) {
+      ckv[hpos[v]] = (uint32_t)v;
+      ckfirst[hpos[v]] = first[v];
+    }
+}
+
+// index in ck of the checkpoint before value c * kCkptValues of u's list (c >= 1)
+__device__ __forceinline__ uint64_t ckpt_index(const uint32_t* __restrict__ ckv, const uint64_t* __restrict__ ckfirst,
+                                               uint64_t nckv, uint32_t u, uint32_t c) {
+  uint64_t lo = 0, hi = nckv;  // first entry >= u
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (__ldg(ckv + mid) < u) lo = mid + 1;
+    else hi = mid;
+  }
+  return __ldg(ckfirst + lo) + c - 1;
+}
+
+template <typename OffT>
+__global__ void comp_write_kernel(CsrView<OffT> g, const uint64_t* __restrict__ boff, uint8_t* bytes,
+                                  const uint64_t* __restrict__ ckoff, Ckpt* ck) {  // ckoff: per vertex, first checkpoint
+  static_assert(kCkptValues % 32 == 0, "checkpoints fall on the 32-value steps");
   const uint32_t lane = lane_id();
   for (uint64_t v = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < g.n;
        v += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
     const Seg s = g.seg((uint32_t)v);
     uint64_t at = boff[v];
     for (uint32_t i0 = 0; i0 < s.len; i0 += 32) {
+      if (i0 > 0 && i0 % kCkptValues == 0 && lane == 0)
+        ck[ckoff[v] + i0 / kCkptValues - 1] = Ckpt{at, __ldg(s.p + i0 - 1), 0u};
       const uint32_t i = i0 + lane;
       uint64_t w = i < s.len ? code_value(s.p, i, (uint32_t)v) : 0;
       const uint32_t l = i < s.len ? code_len(w) : 0u;
@@ -230,6 +289,7 @@ struct CompCtl {
   uint32_t levels;
   unsigned long long nq[2];    // queue length, by level parity
   unsigned long long mq[2];    // degree sum of the queue
+  unsigned long long nspill[2];  // push chunk tasks of long lists, by level parity
 };
 
 template <typename OffT>
@@ -246,6 +306,11 @@ struct CompBfsArgs {
   uint32_t* fb;
   uint32_t* queue;  // [2][n]
   CompCtl* ctl;
+  const uint32_t* ckv;      // checkpointed vertices (ascending), their first checkpoint, the checkpoints
+  const uint64_t* ckfirst;
+  uint64_t nckv;
+  const Ckpt* ck;
+  uint2* spill;             // push chunk tasks (vertex, chunk >= 1); room for every checkpoint
   float alpha, beta;
   uint64_t limit_ns;
   uint32_t nw;
@@ -338,6 +403,8 @@ __global__ void __launch_bounds__(kCompThreads, 4) comp_bfs_kernel(CompBfsArgs<O
     ctl->mq[0] = (uint64_t)(__ldg(a.off + a.src + 1) - __ldg(a.off + a.src));
     ctl->nq[1] = 0;
     ctl->mq[1] = 0;
+    ctl->nspill[0] = 0;
+    ctl->nspill[1] = 0;
   }
   if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
   const uint64_t t0 = globaltimer();
@@ -363,23 +430,55 @@ __global__ void __launch_bounds__(kCompThreads, 4) comp_bfs_kernel(CompBfsArgs<O
     if (gtid == 0) {  // the level after next starts from zero
       ctl->nq[nxt] = 0;
       ctl->mq[nxt] = 0;
+      ctl->nspill[nxt] = 0;
     }
     const uint32_t* q = a.queue + (size_t)cur * a.n;
     uint64_t acc = 0;
     // the counters of the next level are zeroed before any appends to them
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
     if (dir == 1) {
-      // push: a warp per frontier vertex, decoding its list 32 bytes at a time
+      // push: a warp per frontier vertex, decoding its list 32 bytes at a
+      // time, the first kCkptValues values only; the rest of a longer list
+      // becomes chunk tasks (one per checkpoint) that warps take after a grid
+      // barrier, each decoding from its checkpoint, so that a hub's list is
+      // shared by many warps
       for (uint64_t j = gwarp; j < nf; j += nwarps) {
         const uint32_t u = ld_cg(q + j);
         uint64_t p = __ldg(a.boff + u), ci = 0;
         const uint64_t end = __ldg(a.boff + u + 1);
         const uint64_t d = (uint64_t)(__ldg(a.off + u + 1) - __ldg(a.off + u));
+        const uint64_t lim = d < kCkptValues ? d : kCkptValues;
         uint32_t prev = 0, x = 0;
-        while (ci < d) {
+        while (ci < lim) {
+          const uint64_t c0 = ci;
           const uint32_t T = warp_decode_window(a.bytes, &p, end, u, &ci, &prev, &x);
           if (T == 0) break;
-          comp_claim<OffT, kParents>(a, W, (T >> lane) & 1u, x, u, L + 1, nxt, acc);
+          const bool in = ((T >> lane) & 1u) && c0 + __popc(T & lanemask_lt()) < lim;
+          comp_claim<OffT, kParents>(a, W, in, x, u, L + 1, nxt, acc);
+        }
+        if (d > kCkptValues && lane == 0) {
+          const uint32_t nch = (uint32_t)((d - 1) / kCkptValues);
+          const unsigned long long base = atomicAdd(&ctl->nspill[cur], (unsigned long long)nch);
+          for (uint32_t ch = 1; ch <= nch; ++ch) a.spill[base + ch - 1] = make_uint2(u, ch);
+        }
+      }
+      if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
+      const uint64_t nsp = ld_cg(&ctl->nspill[cur]);
+      for (uint64_t t = gwarp; t < nsp; t += nwarps) {
+        const uint2 e = __ldcg(a.spill + t);
+        const uint32_t u = e.x;
+        const Ckpt k = a.ck[ckpt_index(a.ckv, a.ckfirst, a.nckv, u, e.y)];
+        uint64_t p = k.byte, ci = (uint64_t)e.y * kCkptValues;
+        const uint64_t end = __ldg(a.boff + u + 1);
+        const uint64_t d = (uint64_t)(__ldg(a.off + u + 1) - __ldg(a.off + u));
+        const uint64_t lim = d < ci + kCkptValues ? d : ci + kCkptValues;
+        uint32_t prev = k.prev, x = 0;
+        while (ci < lim) {
+          const uint64_t c0 = ci;
+          const uint32_t T = warp_decode_window(a.bytes, &p, end, u, &ci, &prev, &x);
+          if (T == 0) break;
+          const bool in = ((T >> lane) & 1u) && c0 + __popc(T & lanemask_lt()) < lim;
+          comp_claim<OffT, kParents>(a, W, in, x, u, L + 1, nxt, acc);
         }
       }
       if (W.n) comp_stage_flush(a, W, nxt);
@@ -495,8 +594,36 @@ byo_status comp_encode(byo_graph* g, CompStore* c, cudaStream_t s) {
   BYO_RETURN_IF(dev_alloc_t(&c->bytes, c->nbytes + 48, "compressed bytes"));
   BYO_CUDA(cudaMemcpyAsync(c->boff + g->n, &c->nbytes, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   BYO_CUDA(cudaMemsetAsync(c->bytes + c->nbytes, 0, 48, s));
-  comp_write_kernel<OffT><<<grid_for((uint64_t)g->n * 32, kCompThreads), kCompThreads, 0, s>>>(view, c->boff,
-                                                                                                c->bytes);
+  // checkpoints of the long lists
+  uint32_t *ckc = nullptr, *ckh = nullptr;
+  uint64_t *ckoff = nullptr, *ckpos = nullptr;
+  st = tmp_alloc_t(&ckc, g->n + 1ull, s, "compressed checkpoint counts");
+  if (st == BYO_OK) st = tmp_alloc_t(&ckh, g->n + 1ull, s, "compressed checkpoint flags");
+  if (st == BYO_OK) st = tmp_alloc_t(&ckoff, g->n + 1ull, s, "compressed checkpoint offsets");
+  if (st == BYO_OK) st = tmp_alloc_t(&ckpos, g->n + 1ull, s, "compressed checkpoint list positions");
+  if (st == BYO_OK) {
+    comp_ckcount_kernel<OffT><<<grid_for(g->n, 256), 256, 0, s>>>(view, ckc, ckh);
+    note_launch();
+    cudaMemsetAsync(ckc + g->n, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(ckh + g->n, 0, sizeof(uint32_t), s);
+    st = scan_u32_to_u64(ckc, ckoff, g->n + 1ull, &c->nck, s);
+  }
+  if (st == BYO_OK) st = scan_u32_to_u64(ckh, ckpos, g->n + 1ull, &c->nckv, s);
+  if (st == BYO_OK) st = dev_alloc_t(&c->ck, c->nck + 1, "compressed checkpoints");
+  if (st == BYO_OK) st = dev_alloc_t(&c->ckv, c->nckv + 1, "compressed checkpointed vertices");
+  if (st == BYO_OK) st = dev_alloc_t(&c->ckfirst, c->nckv + 1, "compressed first checkpoints");
+  if (st == BYO_OK) {
+    comp_cklist_kernel<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, ckh, ckpos, ckoff, c->ckv, c->ckfirst);
+    comp_write_kernel<OffT><<<grid_for((uint64_t)g->n * 32, kCompThreads), kCompThreads, 0, s>>>(view, c->boff,
+                                                                                                  c->bytes, ckoff,
+                                                                                                  c->ck);
+    note_launch(2);
+  }
+  tmp_free(ckc, s);
+  tmp_free(ckh, s);
+  tmp_free(ckoff, s);
+  tmp_free(ckpos, s);
+  BYO_RETURN_IF(st);
   note_launch();
   BYO_CHECK_LAUNCH("comp_write_kernel");
   BYO_CUDA(cudaStreamSynchronize(s));
@@ -539,7 +666,10 @@ byo_status comp_from_csr(byo_graph* g, cudaStream_t s) {
   return BYO_OK;
 }
 
-uint64_t comp_bytes(const byo_graph* g) { return g->comp ? g->comp->nbytes : 0; }
+// code bytes plus the checkpoints (16 bytes each) and their vertex list (12 bytes per vertex)
+uint64_t comp_bytes(const byo_graph* g) {
+  return g->comp ? g->comp->nbytes + 16 * g->comp->nck + 12 * g->comp->nckv : 0;
+}
 
 byo_status comp_export(const byo_graph* g, const uint64_t* offsets, uint32_t* col, cudaStream_t s) {
   const unsigned grid = grid_for((uint64_t)g->n * 32, kCompThreads);
@@ -563,6 +693,7 @@ byo_status comp_bfs(const byo_graph* gc, const uint32_t* sources, uint32_t ns, u
     byo_status st = dev_alloc_t(&c->vis, nw, "compressed BFS visited bits");
     if (st == BYO_OK) st = dev_alloc_t(&c->fb, 2ull * nw, "compressed BFS frontier bits");
     if (st == BYO_OK) st = dev_alloc_t(&c->queue, 2ull * g->n, "compressed BFS queues");
+    if (st == BYO_OK) st = dev_alloc_t(&c->spill, c->nck + 1, "compressed BFS chunk tasks");
     if (st == BYO_OK) st = dev_alloc(&c->ctl, sizeof(CompCtl), "compressed BFS control");
     if (st == BYO_OK) {
       cudaError_t e = cudaMemset(c->ctl, 0, sizeof(CompCtl));
@@ -572,8 +703,10 @@ byo_status comp_bfs(const byo_graph* gc, const uint32_t* sources, uint32_t ns, u
       dev_free(c->vis);
       dev_free(c->fb);
       dev_free(c->queue);
+      dev_free(c->spill);
       dev_free(c->ctl);
       c->vis = c->fb = c->queue = nullptr;
+      c->spill = nullptr;
       c->ctl = nullptr;
       return st;
     }
@@ -595,6 +728,11 @@ byo_status comp_bfs(const byo_graph* gc, const uint32_t* sources, uint32_t ns, u
       a.fb = c->fb;
       a.queue = c->queue;
       a.ctl = ctl;
+      a.ckv = c->ckv;
+      a.ckfirst = c->ckfirst;
+      a.nckv = c->nckv;
+      a.ck = c->ck;
+      a.spill = c->spill;
       a.alpha = sp.alpha;
       a.beta = sp.beta;
       a.limit_ns = timeout_ns();
