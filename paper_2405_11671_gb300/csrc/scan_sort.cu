@@ -155,11 +155,12 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
 }
 
 // One tile of kSortTile keys per CTA.  Each key's rank among the tile's keys
-// of its digit comes from warp matches and per-warp digit counters; the tile
+// of its digit comes from per-bit ballots and per-warp digit counters; the tile
 // is then reordered by digit in shared memory (stable: warps, then rounds,
 // then lanes in order) and written out run by run, so that consecutive
 // threads store consecutive addresses of a digit's output range.
 constexpr size_t kScatterSmem = (size_t)kSortTile * sizeof(uint64_t);
+static_assert(kRadix == 1 << 8, "the scatter ranks keys with one ballot per bit of an 8-bit digit");
 
 __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(const uint64_t* __restrict__ keys,
                                                                      uint64_t* __restrict__ out, uint64_t n,
@@ -183,8 +184,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(const ui
     uint64_t idx = base + (uint64_t)r * 32 + lane;
     bool valid = idx < n;
     k[r] = valid ? keys[idx] : 0;
-    uint32_t d = valid ? ((uint32_t)(k[r] >> shift) & mask) : (uint32_t)kRadix;
-    uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t d = valid ? ((uint32_t)(k[r] >> shift) & mask) : 0u;
+    // the valid lanes holding the same digit: one ballot per digit bit (a warp
+    // match instruction is several times slower)
+    uint32_t peers = __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const uint32_t bb = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+      peers &= ((d >> b) & 1u) ? bb : ~bb;
+    }
     uint32_t before = __popc(peers & lanemask_lt());
     uint32_t c = valid ? cnt[w][d] : 0;
     rank[r] = c + before;
