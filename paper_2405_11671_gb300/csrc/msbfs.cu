@@ -193,23 +193,30 @@ __global__ void __launch_bounds__(kMsThreads) msbfs_kernel(MsArgs<G> a) {
     }
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->err, a.limit_ns)) return;
     // finalise: new frontier words, levels of newly reached (vertex, source) pairs
+    // (the levels are written one source at a time across the warp, so that
+    // the lanes' stores to a source's row of levels are consecutive)
     unsigned long long cnt = 0, deg = 0;
-    for (uint64_t v = gtid; v < n; v += gthreads) {
-      unsigned long long x = ld_cg(a.next + v);
-      unsigned long long sv = ld_cg(a.seen + v);
-      x &= ~sv;
-      a.visit[v] = x;
-      if (x) {
-        a.seen[v] = sv | x;
-        a.next[v] = 0;
-        ++cnt;
-        deg += a.g.degree((uint32_t)v);
-        unsigned long long y = x;
-        while (y) {
-          int j = __ffsll((long long)y) - 1;
-          y &= y - 1;
-          a.levels[(uint64_t)j * n + v] = L + 1;
+    for (uint64_t vb = gtid - lane; vb < n; vb += gthreads) {
+      const uint64_t v = vb + lane;
+      unsigned long long x = 0;
+      if (v < n) {
+        x = ld_cg(a.next + v);
+        const unsigned long long sv = ld_cg(a.seen + v);
+        x &= ~sv;
+        a.visit[v] = x;
+        if (x) {
+          a.seen[v] = sv | x;
+          a.next[v] = 0;
+          ++cnt;
+          deg += a.g.degree((uint32_t)v);
         }
+      }
+      unsigned long long any = ((unsigned long long)__reduce_or_sync(0xFFFFFFFFu, (uint32_t)(x >> 32)) << 32) |
+                               __reduce_or_sync(0xFFFFFFFFu, (uint32_t)x);
+      while (any) {
+        const int j = __ffsll((long long)any) - 1;
+        any &= any - 1;
+        if ((x >> j) & 1ull) a.levels[(uint64_t)j * n + v] = L + 1;
       }
     }
 #pragma unroll
