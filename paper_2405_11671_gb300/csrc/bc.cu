@@ -131,33 +131,44 @@ __device__ __forceinline__ double bc_value(uint32_t u, const double* __restrict_
   return kForward ? __ldcg(sigma + u) : __ldcg(ratio + u);
 }
 
+// whether u is at the level the sweep gathers from: its bit in `inlvl`, a
+// bitmap of that level's vertices (n/8 bytes, L2-resident where the level
+// array is not)
+__device__ __forceinline__ bool bc_in(const uint32_t* __restrict__ inlvl, uint32_t u) {
+  return (__ldg(inlvl + (u >> 5)) >> (u & 31)) & 1u;
+}
+
 // Sum over the ids p[k], k = first, first + stride, ... < len, of the values
-// of those at level `want`: four ids, their four levels and then their values
-// in flight per step.
+// of those at the gathered level: four ids, their four bits and then their
+// values in flight per step.
 template <bool kForward>
 __device__ __forceinline__ double bc_gather(const uint32_t* __restrict__ p, uint32_t first, uint32_t len,
-                                            uint32_t stride, uint32_t want, const uint32_t* __restrict__ level,
+                                            uint32_t stride, const uint32_t* __restrict__ inlvl,
                                             const double* __restrict__ sigma, const double* __restrict__ ratio) {
   double acc = 0.0;
   uint32_t k = first;
   for (; k + 3 * stride < len; k += 4 * stride) {
-    uint32_t u[4], l[4];
+    uint32_t u[4];
+    bool in[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) u[j] = __ldg(p + k + j * stride);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) l[j] = __ldg(level + u[j]);
+    for (int j = 0; j < 4; ++j) in[j] = bc_in(inlvl, u[j]);
     double x[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) x[j] = l[j] == want ? bc_value<kForward>(u[j], sigma, ratio) : 0.0;
+    for (int j = 0; j < 4; ++j) x[j] = in[j] ? bc_value<kForward>(u[j], sigma, ratio) : 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc += x[j];
   }
   for (; k < len; k += stride) {
     const uint32_t u = __ldg(p + k);
-    if (__ldg(level + u) == want) acc += bc_value<kForward>(u, sigma, ratio);
+    if (bc_in(inlvl, u)) acc += bc_value<kForward>(u, sigma, ratio);
   }
   return acc;
 }
+
+// the source's bit: level 0, gathered by the first forward level
+__global__ void bc_source_bit_kernel(uint32_t* bits, uint32_t src) { bits[src >> 5] = 1u << (src & 31); }
 
 // forward: sigma(v), and the ratio a vertex without deeper neighbours keeps;
 // backward: delta(v) = sigma(v) * sum, and v's ratio for the level above
@@ -176,16 +187,31 @@ __device__ __forceinline__ void bc_store(uint32_t v, double acc, double* sigma, 
 
 // One level of a sweep.  Blocks [0, light_blocks) take the level's light
 // vertices, eight lanes each; the remaining blocks take its heavy vertices,
-// one CTA each.
+// one CTA each.  Level membership comes from two bitmaps by level parity
+// (bits + (l & 1) * nw): the kernel of level l reads the other parity's
+// bitmap (the gathered level, l - 1 forward, l + 1 backward), sets its own
+// vertices' bits in its parity's bitmap for the next kernel, and clears from
+// that bitmap the level two steps back, whose last reader was the previous
+// kernel.  No kernel reads the bitmap it writes.
 template <typename G, bool kForward>
 __global__ void __launch_bounds__(kBcThreads) bc_level_kernel(G g, const uint32_t* __restrict__ order,
                                                               const uint64_t* __restrict__ lstart,
                                                               const uint32_t* __restrict__ lcnt, uint32_t l,
-                                                              uint32_t light_blocks, const uint32_t* __restrict__ level,
-                                                              double* sigma, double* delta, double* ratio) {
+                                                              uint32_t light_blocks, uint32_t* bits, uint32_t nw,
+                                                              uint32_t L, double* sigma, double* delta, double* ratio) {
   const uint64_t begin = lstart[l], end = lstart[l + 1];
+  const uint32_t* __restrict__ inlvl = bits + (size_t)((l & 1) ^ 1) * nw;
+  uint32_t* own = bits + (size_t)(l & 1) * nw;
+  const bool clear = kForward ? l >= 2 : l + 2 < L;
+  if (clear) {
+    const uint32_t lc = kForward ? l - 2 : l + 2;
+    for (uint64_t i = lstart[lc] + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lstart[lc + 1];
+         i += (uint64_t)gridDim.x * blockDim.x) {
+      const uint32_t v = order[i];
+      atomicAnd(own + (v >> 5), ~(1u << (v & 31)));
+    }
+  }
   const uint64_t mid = begin + lcnt[l];
-  const uint32_t want = kForward ? l - 1 : l + 1;
   if (blockIdx.x < light_blocks) {
     const uint32_t lane = threadIdx.x & (kGroup - 1);
     const uint64_t grp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
@@ -198,18 +224,21 @@ __global__ void __launch_bounds__(kBcThreads) bc_level_kernel(G g, const uint32_
       if (i < mid) {
         v = order[i];
         const Seg s = g.seg(v);
-        acc = bc_gather<kForward>(s.p, lane, s.len, kGroup, want, level, sigma, ratio);
+        acc = bc_gather<kForward>(s.p, lane, s.len, kGroup, inlvl, sigma, ratio);
       }
 #pragma unroll
       for (int o = kGroup / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o, kGroup);
-      if (i < mid && lane == 0) bc_store<kForward>(v, acc, sigma, delta, ratio);
+      if (i < mid && lane == 0) {
+        bc_store<kForward>(v, acc, sigma, delta, ratio);
+        atomicOr(own + (v >> 5), 1u << (v & 31));
+      }
     }
   } else {
     __shared__ double red[kBcThreads / 32];
     for (uint64_t i = mid + (blockIdx.x - light_blocks); i < end; i += gridDim.x - light_blocks) {
       const uint32_t v = order[i];
       const Seg s = g.seg(v);
-      double acc = bc_gather<kForward>(s.p, threadIdx.x, s.len, blockDim.x, want, level, sigma, ratio);
+      double acc = bc_gather<kForward>(s.p, threadIdx.x, s.len, blockDim.x, inlvl, sigma, ratio);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
       if (lane_id() == 0) red[threadIdx.x >> 5] = acc;
@@ -218,6 +247,7 @@ __global__ void __launch_bounds__(kBcThreads) bc_level_kernel(G g, const uint32_
         double t = 0.0;
         for (int w = 0; w < kBcThreads / 32; ++w) t += red[w];
         bc_store<kForward>(v, t, sigma, delta, ratio);
+        atomicOr(own + (v >> 5), 1u << (v & 31));
       }
       __syncthreads();
     }
@@ -255,6 +285,14 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
   if (st == BYO_OK) st = tmp_alloc_t(&cur, 2 * L, s, "BC cursors");
   if (st == BYO_OK) st = tmp_alloc_t(&lstart, L + 1, s, "BC level starts");
   if (st == BYO_OK) st = tmp_alloc_t(&order, n, s, "BC level order");
+  const uint32_t nw = (n + 31) / 32;
+  uint32_t* bits = nullptr;  // two level bitmaps, by level parity
+  if (st == BYO_OK) st = tmp_alloc_t(&bits, 2ull * nw, s, "BC level bits");
+  if (st == BYO_OK) {
+    cudaMemsetAsync(bits, 0, sizeof(uint32_t) * 2ull * nw, s);
+    bc_source_bit_kernel<<<1, 1, 0, s>>>(bits, src);
+    note_launch();
+  }
   std::vector<uint64_t> hstart;
   std::vector<uint32_t> hlight;  // light vertices per level
   if (st == BYO_OK) {
@@ -291,12 +329,22 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
       const uint64_t h = hstart[l + 1] - hstart[l] - hlight[l];
       return (uint32_t)(h < cap ? (h ? h : 1) : cap);
     };
+    // the level kernel also clears level lc's bits: at least a thread per
+    // cleared vertex up to the cap, or a small level's kernel would clear a
+    // large level with a handful of CTAs (the extra CTAs join the heavy part)
+    auto grid = [&](uint32_t l, uint32_t lb, uint64_t lc) {
+      const uint32_t g = lb + heavy_blocks(l);
+      if (lc >= L) return g;
+      const uint64_t c = (hstart[lc + 1] - hstart[lc] + kBcThreads - 1) / kBcThreads;
+      const uint32_t cb = (uint32_t)(c < cap ? c : cap);
+      return g > cb ? g : cb;
+    };
     {
       ProfScope ps("bc_forward", s);
       for (uint32_t l = 1; l < L; ++l) {
         const uint32_t lb = blocks(hlight[l]);
-        bc_level_kernel<G, true><<<lb + heavy_blocks(l), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
-                                                                                   level, sigma, delta, ratio);
+        bc_level_kernel<G, true><<<grid(l, lb, l >= 2 ? l - 2 : L), kBcThreads, 0, s>>>(
+            view, order, lstart, lcnt, l, lb, bits, nw, (uint32_t)L, sigma, delta, ratio);
         note_launch();
       }
     }
@@ -304,8 +352,8 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
       ProfScope ps("bc_backward", s);
       for (uint32_t l = depth; l-- > 1;) {  // the deepest level has no deeper neighbour; delta(s) stays 0
         const uint32_t lb = blocks(hlight[l]);
-        bc_level_kernel<G, false><<<lb + heavy_blocks(l), kBcThreads, 0, s>>>(view, order, lstart, lcnt, l, lb,
-                                                                                    level, sigma, delta, ratio);
+        bc_level_kernel<G, false><<<grid(l, lb, l + 2 < L ? l + 2 : L), kBcThreads, 0, s>>>(
+            view, order, lstart, lcnt, l, lb, bits, nw, (uint32_t)L, sigma, delta, ratio);
         note_launch();
       }
     }
@@ -318,6 +366,7 @@ byo_status run_bc(const byo_graph* g, G view, uint32_t src, uint32_t* level, dou
   tmp_free(cur, s);
   tmp_free(lstart, s);
   tmp_free(order, s);
+  tmp_free(bits, s);
   tmp_free(ratio, s);
   return st;
 }
