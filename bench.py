@@ -668,6 +668,7 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
     ins_ms, del_ms, alg_ms, csr_alg_ms, rebuild_ms, e2e_ms, ins_bytes = [], [], [], [], [], [], []
+    m_rounds = []
     lv_h = torch.empty(n, dtype=torch.int32).pin_memory()
     lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
     rk_h = torch.empty(n, dtype=torch.float32).pin_memory()
@@ -727,8 +728,12 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
         csr_alg_ms.append(a.elapsed_time(b))
         gc.close()
         del rows, off, col
+        m_rounds.append(g.m)
     launches = byo.byo_kernel_launches() - l0
     clk = clocks.stop()
+    space_sorted = byo.byo_space(g.handle)
+    g.close()
+    hashed = run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds)
     med = statistics.median
     peak, peak_kind = measured_peaks()
     round_ms = [i + d + x for i, d, x in zip(ins_ms, del_ms, alg_ms)]
@@ -737,7 +742,7 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
             "higher_is_better": True, "n_gpus": 1, "steps": rounds, "warmup": 0,
             "ms_per_step": round(med(round_ms), 3), "dtype": "u32+f32", "data": "synthetic", "scaling": "weak",
             "vs_baseline": None,
-            "config": {"workload": "rmat24-dynamic", "n": n, "m_final": g.m, "rounds": rounds, "batch_pairs": batch,
+            "config": {"workload": "rmat24-dynamic", "n": n, "m_final": m_rounds[-1], "rounds": rounds, "batch_pairs": batch,
                        "l2": "inputs larger than L2 (2.1 GB of neighbour ids)"},
             "insert_ms_median": round(med(ins_ms), 3), "delete_ms_median": round(med(del_ms), 3),
             "insert_pairs_per_s": round(batch / (med(ins_ms) / 1e3), 1),
@@ -751,10 +756,55 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
                     "ms_per_step": round(med(e2e_ms), 3), "h2d_bytes_per_step": 16 * batch,
                     "d2h_bytes_per_step": 12 * n,
                     "note": "pairs in, both updates, BFS + CC + PageRank, their outputs out"},
-            "gpu_launches": int(launches), "clocks": clk,
+            "gpu_launches": int(launches), "clocks": clk, "space_bytes": space_sorted,
+            "hashed": {**hashed,
+                       "insert_speedup_vs_sorted": round(med(ins_ms) / hashed["insert_ms_median"], 3),
+                       "delete_speedup_vs_sorted": round(med(del_ms) / hashed["delete_ms_median"], 3),
+                       "bfs_cc_pr_over_sorted": round(hashed["bfs_cc_pr_ms"] / med(alg_ms), 3)},
             "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_dynamic()}
     print(json.dumps(line), flush=True)
+
+
+def run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds):
+    """The same rounds on the hash-indexed container (BYO_DYN_HASH: semisorted
+    batches, unsorted lists, per-run hash indexes): insert, delete and BFS + CC
+    + PageRank times per round, and the container's bytes.  Its edge count must
+    equal the sorted container's after every round."""
+    import graphgen
+    g = byo.Graph(n, dev_u32(torch, src), dev_u32(torch, dst),
+                  byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE | byo.BYO_DYN_HASH)
+    levels = torch.empty((1, n), dtype=torch.int32, device="cuda")
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    ranks = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    ins_ms, del_ms, alg_ms = [], [], []
+    for r, (ins_s, ins_d, del_s, del_d) in enumerate(graphgen.dynamic_rounds(n, src, dst, rounds, batch)):
+        di, dd_, ds, dd = (dev_u32(torch, x) for x in (ins_s, ins_d, del_s, del_d))
+        torch.cuda.synchronize()
+        a, b, c, x1 = ev(), ev(), ev(), ev()
+        a.record(stream)
+        byo.byo_insert_batch(g.handle, di, dd_)
+        b.record(stream)
+        byo.byo_delete_batch(g.handle, ds, dd)
+        c.record(stream)
+        byo.byo_bfs(g.handle, [s0], levels, None, None, want_parents=False)
+        byo.byo_cc(g.handle, labels)
+        byo.byo_pagerank(g.handle, DAMPING, PR_ITERS, ranks, want_residual=False)
+        x1.record(stream)
+        torch.cuda.synchronize()
+        ins_ms.append(a.elapsed_time(b))
+        del_ms.append(b.elapsed_time(c))
+        alg_ms.append(c.elapsed_time(x1))
+        if g.m != m_rounds[r]:
+            raise RuntimeError(f"hashed container: m {g.m} != {m_rounds[r]} after round {r}")
+    med = statistics.median
+    out = {"insert_ms_median": round(med(ins_ms), 3), "delete_ms_median": round(med(del_ms), 3),
+           "insert_pairs_per_s": round(batch / (med(ins_ms) / 1e3), 1),
+           "delete_pairs_per_s": round(batch / (med(del_ms) / 1e3), 1),
+           "bfs_cc_pr_ms": round(med(alg_ms), 3), "space_bytes": byo.byo_space(g.handle)}
     g.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- API ablation

@@ -47,6 +47,7 @@ typedef enum byo_status {
 #define BYO_OFFSETS64 0x8u  /* CSR offsets as uint64 even when m < 2^32 */
 #define BYO_DYN_NO_INLINE 0x10u /* BYO_DYNAMIC without the inline head: every list in pool blocks */
 #define BYO_COMPRESSED 0x20u    /* BYO_CSR with difference-encoded, byte-coded lists (BFS, degree, export) */
+#define BYO_DYN_HASH 0x40u      /* BYO_DYNAMIC with unsorted lists, per-run hash indexes and semisorted batches */
 
 typedef struct byo_graph byo_graph;
 
@@ -60,7 +61,14 @@ const char* byo_last_error(void);
  * of Section 4.1 -- else a run of 128-byte blocks from a device pool), which
  * accepts byo_insert_batch / byo_delete_batch.  BYO_DYN_NO_INLINE (with
  * BYO_DYNAMIC only) keeps every non-empty list in pool blocks, for the
- * inline-head ablation.  BYO_COMPRESSED (with BYO_CSR only) keeps the CSR
+ * inline-head ablation.  BYO_DYN_HASH (with BYO_DYNAMIC only) is the
+ * hashed-blocks design of DHB (Section 5.2) with the semisort-only batch form
+ * of Section 4.1: the same records, inline head and runs, but each list kept
+ * in insertion order, a list in a run of C ids indexed by an open-addressing
+ * table of 2C slots (id and position), and each batch grouped by source with
+ * a counting semisort instead of being sorted; every algorithm runs on it
+ * unchanged (levels, labels and counts are order-free; PageRank sums in list
+ * order, within its tolerance).  BYO_COMPRESSED (with BYO_CSR only) keeps the CSR
  * offsets and stores each list as the paper's compressed graphs do (Section 2,
  * Section 6.5): the first neighbour relative to the vertex (2|u0 - v| +
  * (u0 < v)), then the gaps, each in 7-bit groups least significant first with
@@ -85,7 +93,8 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
  * container comparison, Section 6.5): for the CSR, the offsets and the
  * neighbour ids ((n+1) x 4 or 8 + 4m); for the dynamic container, the 64-byte
  * vertex records and the 128-byte blocks of the runs its lists hold (free pool
- * capacity is not counted); for the compressed container, the offsets, the
+ * capacity is not counted), plus 512 bytes of index slots per block with
+ * BYO_DYN_HASH; for the compressed container, the offsets, the
  * byte offsets ((n+1) x 8), the code bytes and, for lists of more than 4,096
  * values, a 16-byte checkpoint every 4,096 values (where the value's code
  * starts and the id before it, so that several warps can decode one long
@@ -117,7 +126,8 @@ byo_status byo_degree(const byo_graph* g, const uint32_t* vs, uint64_t k, uint32
 /*
  * Batch updates of a BYO_DYNAMIC container: insert_sorted_batch and
  * delete_sorted_batch of the GraphContainer API (Section 4.2).  The batch is k
- * raw device pairs in any order; as BYO does, the library sorts it first.  Set
+ * raw device pairs in any order; as BYO does, the library sorts it first (with
+ * BYO_DYN_HASH it only groups it by source, Section 4.1's semisort form).  Set
  * semantics (Section 3.1): each pair is applied in both directions, self-loops
  * are ignored, duplicates collapse, inserting a present edge or deleting an
  * absent one changes nothing.  num_edges() and degree() reflect the batch when
@@ -128,8 +138,9 @@ byo_status byo_insert_batch(byo_graph* g, const uint32_t* src, const uint32_t* d
 byo_status byo_delete_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t k, void* stream);
 
 /* Copy the container out as a CSR: offsets[n+1] (uint64) and col[m], neighbours
- * ascending.  For a dynamic container this is the snapshot used to compare its
- * contents after each batch. */
+ * ascending (a BYO_DYN_HASH container's lists are sorted on the way out).  For
+ * a dynamic container this is the snapshot used to compare its contents after
+ * each batch. */
 byo_status byo_graph_export_csr(const byo_graph* g, uint64_t* offsets, uint32_t* col, void* stream);
 
 /* ------------------------------------------------------------------------ */

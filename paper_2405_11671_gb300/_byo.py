@@ -32,6 +32,7 @@ BYO_SYMMETRIZE = 0x4
 BYO_OFFSETS64 = 0x8
 BYO_DYN_NO_INLINE = 0x10
 BYO_COMPRESSED = 0x20
+BYO_DYN_HASH = 0x40
 
 BYO_SCHED_HEURISTIC = 0
 BYO_SCHED_LEARNED = 1

@@ -141,6 +141,9 @@ byo_status rebuild_buckets(byo_graph* g, cudaStream_t s);
 byo_status dyn_from_csr(byo_graph* g, cudaStream_t s);
 // Bytes of a dynamic container's records and held pool blocks (synchronises).
 byo_status dyn_space(const byo_graph* g, uint64_t* host_bytes, cudaStream_t s);
+// Sort each list of an exported CSR (off, col) ascending: the hash-indexed
+// dynamic container keeps its lists in insertion order.
+byo_status dyn_sort_lists(const byo_graph* g, const uint64_t* off, uint32_t* col, cudaStream_t s);
 unsigned grid_for(uint64_t work, int threads);
 }  // namespace byo
 

@@ -71,17 +71,21 @@ namespace byo {
 // 4.1, here ~12 ids next to the vertex record).  A vertex with at most
 // kInline neighbours keeps them in its 64-byte record; a larger one keeps all
 // of them, ascending, in a run of 2^cls blocks of 32 ids (128 bytes each) from
-// a device pool.  Either way the list is ONE contiguous ascending segment, so
-// every algorithm kernel runs unchanged over both containers.
+// a device pool.  Either way the list is ONE contiguous segment, so every
+// algorithm kernel runs unchanged over both containers; it is ascending except
+// in the hash-indexed variant (BYO_DYN_HASH), which keeps insertion order and
+// finds an id through a per-run hash index instead (DHB's design, Section 5.2).
 constexpr uint32_t kInline = 12;
 constexpr uint32_t kBlockIds = 32;
 constexpr uint32_t kNoRun = 0xFFFFFFFFu;
+constexpr uint32_t kHashSlots = 2 * kBlockIds;  // index slots per pool block (load <= 1/2 from live ids)
+constexpr uint32_t kTomb = 0xFFFFFFFEu;         // a deleted index key (ids are below n <= 0xFFFFFFFE)
 
 struct __align__(64) DynVertex {
   uint32_t deg;
   uint32_t cls;  // kNoRun when the list is inline
   uint64_t run;  // first block of the run (block index into the pool)
-  uint32_t inl[kInline];
+  uint32_t inl[kInline];  // the inline list; in the hash-indexed variant a run list keeps its index's tombstone count in inl[0]
 };
 
 struct DynView {
@@ -124,6 +128,14 @@ struct DynStore {
   uint64_t stack_cap[kClasses] = {0};
   long long* tops = nullptr;       // kClasses stack tops (device)
   uint32_t icap = kInline;         // inline capacity: kInline, or 0 (BYO_DYN_NO_INLINE)
+  // BYO_DYN_HASH: lists unsorted; the run at block r (class c, 32 * 2^c ids)
+  // has an open-addressing index of 64 * 2^c slots at [64 r, 64 (r + 2^c)):
+  // hkey holds an id (kInf empty, kTomb deleted), hpos its position in the list
+  bool hashed = false;
+  uint32_t* hkey = nullptr;        // 64 * pool_blocks slots
+  uint32_t* hpos = nullptr;        // 64 * pool_blocks slots
+  uint32_t* vcnt = nullptr;        // n batch counters of the semisort (zero between batches)
+  uint32_t* vslot = nullptr;       // n: vertex -> its group in the current batch
 };
 
 inline DynView dyn_view(const byo_graph* g) { return DynView{g->n, g->m, g->dyn->vtx, g->dyn->pool, g->dyn->icap}; }

@@ -32,6 +32,10 @@ void dyn_free(DynStore* d) {
   dev_free(d->bump);
   for (int c = 0; c < kClasses; ++c) dev_free(d->stacks[c]);
   dev_free(d->tops);
+  dev_free(d->hkey);
+  dev_free(d->hpos);
+  dev_free(d->vcnt);
+  dev_free(d->vslot);
   delete d;
 }
 
@@ -67,7 +71,7 @@ __global__ void dyn_blocks_kernel(const OffT* __restrict__ off, uint32_t n, uint
 
 template <typename OffT>
 __global__ void dyn_load_kernel(const OffT* __restrict__ off, const uint32_t* __restrict__ col, uint32_t n,
-                                uint32_t icap, const uint64_t* __restrict__ first_block, DynVertex* vtx,
+                                uint32_t icap, bool hashed, const uint64_t* __restrict__ first_block, DynVertex* vtx,
                                 uint32_t* pool) {
   const uint32_t lane = lane_id();
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -87,7 +91,7 @@ __global__ void dyn_load_kernel(const OffT* __restrict__ off, const uint32_t* __
       uint64_t run = first_block[v];
       uint32_t* dst = pool + run * kBlockIds;
       for (uint32_t i = lane; i < d; i += 32) dst[i] = col[b + i];
-      if (lane < kInline) r->inl[lane] = kInf;
+      if (lane < kInline) r->inl[lane] = lane == 0 && hashed ? 0u : kInf;  // no tombstones yet
       if (lane == 0) {
         r->deg = d;
         r->cls = run_class(d);
@@ -326,10 +330,30 @@ byo_status alloc_stacks(DynStore* d) {
 byo_status grow_pool(DynStore* d, uint64_t used, uint64_t blocks, cudaStream_t s) {
   uint32_t* np = nullptr;
   BYO_RETURN_IF(dev_alloc_t(&np, blocks * kBlockIds, "dynamic pool"));
+  uint32_t *nk = nullptr, *npos = nullptr;
+  if (d->hashed) {  // the index arrays grow with the pool (64 slots per block)
+    byo_status st = dev_alloc_t(&nk, blocks * kHashSlots, "hash index keys");
+    if (st == BYO_OK) st = dev_alloc_t(&npos, blocks * kHashSlots, "hash index positions");
+    if (st != BYO_OK) {
+      dev_free(np);
+      dev_free(nk);
+      return st;
+    }
+  }
   if (used) BYO_CUDA(cudaMemcpyAsync(np, d->pool, used * kBlockIds * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  if (d->hashed && used) {
+    BYO_CUDA(cudaMemcpyAsync(nk, d->hkey, used * kHashSlots * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    BYO_CUDA(cudaMemcpyAsync(npos, d->hpos, used * kHashSlots * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  }
   BYO_CUDA(cudaStreamSynchronize(s));
   dev_free(d->pool);
   d->pool = np;
+  if (d->hashed) {
+    dev_free(d->hkey);
+    dev_free(d->hpos);
+    d->hkey = nk;
+    d->hpos = npos;
+  }
   d->pool_blocks = blocks;
   return BYO_OK;
 }
@@ -357,8 +381,8 @@ byo_status load_from_csr(byo_graph* g, DynStore* d, cudaStream_t s) {
     cudaMemsetAsync(d->tops, 0, sizeof(long long) * kClasses, s);
     cudaMemcpyAsync(d->bump, &total, sizeof(total), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(d->vtx + g->n, 0, sizeof(DynVertex), s);
-    dyn_load_kernel<OffT><<<grid_for((uint64_t)g->n * 32, 256), 256, 0, s>>>(off, g->col, g->n, d->icap, first,
-                                                                               d->vtx, d->pool);
+    dyn_load_kernel<OffT><<<grid_for((uint64_t)g->n * 32, 256), 256, 0, s>>>(off, g->col, g->n, d->icap, d->hashed,
+                                                                               first, d->vtx, d->pool);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -369,9 +393,720 @@ byo_status load_from_csr(byo_graph* g, DynStore* d, cudaStream_t s) {
   return st;
 }
 
+// ---------------------------------------------------------------- hash-indexed variant
+// BYO_DYN_HASH: the hashed-blocks container of DHB (Section 5.2) fed by the
+// semisort-only batch form of Section 4.1 (group the batch by source, order
+// nothing).  Records, inline head and pool runs are the ones above; a list is
+// kept dense in insertion order, and a list held in a run of C ids has an
+// open-addressing index of 2C slots (linear probing, multiplicative hash):
+// hkey the id (kInf empty, kTomb deleted), hpos the id's position in the list.
+// One warp owns each vertex the batch touches, so no two warps ever update
+// one list or one index and nothing waits on another thread.
+//   insert: plan per vertex (stay inline; insert in place; rebuild the index
+//     in place when tombstones crowd it; move to a larger run), allocate,
+//     clear and fill the moved or rebuilt indexes (chunk tasks), then the
+//     vertex's warp probes the index for each batch id: a CAS that takes an
+//     empty slot admits a new id, appended at the end of the list; meeting
+//     the id itself means it is present (or a duplicate in the batch);
+//   delete: the vertex's warp turns the keys it finds into tombstones, then
+//     fills the holes below the new degree with the ids that survive above
+//     it and re-points their index entries; a list that falls to the inline
+//     capacity goes back inline and frees its run.
+// Live ids plus tombstones never exceed 3/4 of an index's slots (the plan
+// rebuilds or moves before an insert could pass that; deletes only turn live
+// keys into tombstones), so every probe meets an empty slot within the index.
+enum : uint32_t { kActInline = 0, kActKeep = 1, kActRebuild = 2, kActMove = 3 };
+
+__device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t c) {  // index of class c: 2^(c+6) slots
+  return (x * 2654435769u) >> (26 - c);
+}
+__device__ __forceinline__ uint32_t hmask(uint32_t c) { return 0xFFFFFFFFu >> (26 - c); }
+
+// Both directions of each pair; self-loops, and pairs with an id >= n (which
+// also set *bad), get the row kInf and are skipped by the semisort.
+__global__ void hsym_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t k, uint32_t n,
+                            uint32_t* rows, uint32_t* cols, uint32_t* bad) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t u = src[i], v = dst[i];
+    const bool ok = u < n && v < n;
+    if (!ok) *bad = 1u;
+    const bool keep = ok && u != v;
+    rows[2 * i] = keep ? u : kInf;
+    cols[2 * i] = v;
+    rows[2 * i + 1] = keep ? v : kInf;
+    cols[2 * i + 1] = u;
+  }
+}
+
+// Semisort, pass 1: count the entries per source; the first entry of a
+// source gives it a group slot (one atomic per warp for the slots).
+__global__ void hhist_kernel(const uint32_t* __restrict__ rows, uint64_t B, uint32_t* vcnt, uint32_t* vslot,
+                             uint32_t* aff, unsigned long long* nA) {
+  const uint32_t lane = lane_id();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < B; i0 += stride) {
+    const uint64_t i = i0 + lane;
+    const uint32_t r = i < B ? rows[i] : kInf;
+    const bool first = r != kInf && atomicAdd(vcnt + r, 1u) == 0u;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, first);
+    uint32_t base = 0;
+    if (lane == 0 && m) base = (uint32_t)atomicAdd(nA, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (first) {
+      const uint32_t a = base + __popc(m & lanemask_lt());
+      aff[a] = r;
+      vslot[r] = a;
+    }
+  }
+}
+
+// group sizes (gcnt[A] = 0, so that a scan of A + 1 entries ends with the total)
+__global__ void hgcount_kernel(const uint32_t* __restrict__ aff, uint64_t A, const uint32_t* __restrict__ vcnt,
+                               uint32_t* gcnt) {
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x)
+    gcnt[a] = vcnt[aff[a]];
+  if (blockIdx.x == 0 && threadIdx.x == 0) gcnt[A] = 0;
+}
+
+// Semisort, pass 2: each entry takes a place in its source's group by
+// counting the source's counter back down (which leaves it zero again).
+__global__ void hscatter_kernel(const uint32_t* __restrict__ rows, const uint32_t* __restrict__ cols, uint64_t B,
+                                uint32_t* vcnt, const uint32_t* __restrict__ vslot, const uint64_t* __restrict__ gstart,
+                                uint32_t* gcols) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = rows[i];
+    if (r == kInf) continue;
+    const uint64_t p = gstart[vslot[r]] + atomicSub(vcnt + r, 1u) - 1u;
+    gcols[p] = cols[i];
+  }
+}
+
+// Insert plan per affected vertex from an upper bound on its new degree
+// (old degree + group size, at most n): the action, the class of the run the
+// list will live in, and the pool blocks moves may take (*need).
+__global__ void hplan_kernel(const DynVertex* __restrict__ vtx, const uint32_t* __restrict__ aff,
+                             const uint64_t* __restrict__ gstart, uint64_t A, uint32_t n, uint32_t icap, uint32_t* act,
+                             uint32_t* new_cls, unsigned long long* need) {
+  unsigned long long sum = 0;
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x) {
+    const DynVertex& r = vtx[aff[a]];
+    const uint32_t cls = r.cls;
+    const uint64_t raw = (uint64_t)r.deg + (gstart[a + 1] - gstart[a]);
+    const uint64_t ub = raw < n ? raw : n;  // no list holds more than n - 1 ids
+    uint32_t ac, c = kNoRun;
+    if (cls == kNoRun) {
+      ac = raw <= icap ? kActInline : kActMove;  // inline inserts take one batch id per lane
+    } else {
+      const uint64_t C = (uint64_t)kBlockIds << cls;
+      if (ub > C) ac = kActMove;
+      else ac = ub + r.inl[0] <= C + C / 2 ? kActKeep : kActRebuild;
+      c = cls;
+    }
+    if (ac == kActMove) {
+      c = run_class((uint32_t)ub);
+      sum += 1ull << c;
+    }
+    act[a] = ac;
+    new_cls[a] = c;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+  if (lane_id() == 0 && sum) atomicAdd(need, sum);
+}
+
+// Runs for moved lists (a free run of the class, else bump-allocated); the
+// old run of a moved list is freed after the batch.  Pops may drive a stack
+// top below zero; clamp_tops_kernel fixes it up.
+__global__ void halloc_kernel(const DynVertex* __restrict__ vtx, const uint32_t* __restrict__ aff,
+                              const uint32_t* __restrict__ act, const uint32_t* __restrict__ new_cls, uint64_t A,
+                              uint32_t* const* stacks, long long* tops, unsigned long long* bump, uint64_t* new_run,
+                              uint64_t* free_run, uint32_t* free_cls) {
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x) {
+    const DynVertex& r = vtx[aff[a]];
+    free_run[a] = ~0ull;
+    free_cls[a] = kNoRun;
+    if (act[a] != kActMove) {
+      new_run[a] = r.run;
+      continue;
+    }
+    const uint32_t c = new_cls[a];
+    uint64_t run;
+    const long long t = atomicAdd((unsigned long long*)(tops + c), (unsigned long long)(-1ll));
+    if (t > 0) run = stacks[c][t - 1];
+    else run = atomicAdd(bump, 1ull << c);
+    new_run[a] = run;
+    if (r.cls != kNoRun) {
+      free_run[a] = r.run;
+      free_cls[a] = r.cls;
+    }
+  }
+}
+
+// chunk tasks per affected vertex: index slots to clear (moved and rebuilt
+// lists), ids to enter into an index (the same lists; with act == NULL every
+// run list, for the initial build, where a = the vertex itself)
+__global__ void htask_count_kernel(const DynVertex* __restrict__ vtx, const uint32_t* __restrict__ aff,
+                                   const uint32_t* __restrict__ act, const uint32_t* __restrict__ new_cls, uint64_t A,
+                                   uint32_t* nclear, uint32_t* nfill) {
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = aff ? aff[a] : (uint32_t)a;
+    const bool build = act ? (act[a] == kActRebuild || act[a] == kActMove) : vtx[v].cls != kNoRun;
+    const uint32_t d = vtx[v].deg;
+    if (nclear) {
+      const uint64_t H = build ? (uint64_t)kHashSlots << new_cls[a] : 0;
+      nclear[a] = (uint32_t)((H + kChunkIds - 1) / kChunkIds);
+    }
+    nfill[a] = build ? (d + kChunkIds - 1) / kChunkIds : 0u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (nclear) nclear[A] = 0;
+    nfill[A] = 0;
+  }
+}
+
+// one warp per task: kChunkIds index slots of a moved or rebuilt list set empty
+__global__ void hclear_kernel(const uint32_t* __restrict__ item, const uint64_t* __restrict__ tstart, uint64_t NT,
+                              const uint64_t* __restrict__ new_run, const uint32_t* __restrict__ new_cls,
+                              uint32_t* hkey) {
+  const uint32_t lane = lane_id();
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t t = w0; t < NT; t += nw) {
+    const uint32_t a = item[t];
+    const uint64_t ch = t - tstart[a];
+    uint32_t* key = hkey + new_run[a] * kHashSlots;
+    const uint64_t H = (uint64_t)kHashSlots << new_cls[a];
+    const uint64_t hi = min(H, (ch + 1) * kChunkIds);
+    for (uint64_t i = ch * kChunkIds + lane; i < hi; i += 32) key[i] = kInf;
+  }
+}
+
+// One warp per task: kChunkIds ids of a list are copied to its new run (a
+// moved list) and entered into the run's index.  Without act/new_run (the
+// initial build) the list stays where the record says.
+__global__ void hfill_kernel(const DynVertex* __restrict__ vtx, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
+                             const uint32_t* __restrict__ aff, const uint64_t* __restrict__ new_run,
+                             const uint32_t* __restrict__ new_cls, const uint32_t* __restrict__ item,
+                             const uint64_t* __restrict__ tstart, uint64_t NT, uint32_t* err) {
+  const uint32_t lane = lane_id();
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t t = w0; t < NT; t += nw) {
+    const uint32_t a = item[t];
+    const uint64_t ch = t - tstart[a];
+    const uint32_t v = aff ? aff[a] : a;
+    const DynVertex& r = vtx[v];
+    const uint32_t d = r.deg;
+    const uint32_t* from = r.cls == kNoRun ? r.inl : pool + r.run * kBlockIds;
+    const uint64_t run = new_run ? new_run[a] : r.run;
+    const uint32_t c = new_cls ? new_cls[a] : r.cls;
+    uint32_t* to = pool + run * kBlockIds;
+    uint32_t* key = hkey + run * kHashSlots;
+    uint32_t* pos = hpos + run * kHashSlots;
+    const uint32_t mask = hmask(c);
+    const uint32_t hi = (uint32_t)min((uint64_t)d, (ch + 1) * kChunkIds);
+    for (uint32_t i = (uint32_t)(ch * kChunkIds) + lane; i < hi; i += 32) {
+      const uint32_t x = from[i];
+      if (from != to) to[i] = x;
+      uint32_t h = hslot(x, c);
+      bool placed = false;
+      for (uint64_t it = 0; it <= mask; ++it) {
+        if (atomicCAS(key + h, kInf, x) == kInf) {
+          pos[h] = i;
+          placed = true;
+          break;
+        }
+        h = (h + 1) & mask;
+      }
+      if (!placed) *err = 1u;
+    }
+  }
+}
+
+// adds a warp's degree changes (lane 0's dsum) into *delta, one atomic per block
+__device__ __forceinline__ void block_add_delta(long long dsum, long long* delta) {
+  __shared__ long long bsum;
+  if (threadIdx.x == 0) bsum = 0;
+  __syncthreads();
+  if (lane_id() == 0 && dsum) atomicAdd((unsigned long long*)&bsum, (unsigned long long)dsum);
+  __syncthreads();
+  if (threadIdx.x == 0 && bsum) atomicAdd((unsigned long long*)delta, (unsigned long long)bsum);
+}
+
+// k-th (from 0) set bit of m, or 0 if m has fewer
+__device__ __forceinline__ uint32_t kth_bit(uint32_t m, uint32_t k) {
+  for (uint32_t j = 0; j < k && m; ++j) m &= m - 1;
+  return m ? (uint32_t)(__ffs(m) - 1) : 0u;
+}
+
+// One warp per affected vertex applies its group of batch ids (insert).
+__global__ void hinsert_kernel(DynVertex* vtx, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
+                               const uint32_t* __restrict__ aff, const uint64_t* __restrict__ gstart,
+                               const uint32_t* __restrict__ gcols, const uint32_t* __restrict__ act,
+                               const uint64_t* __restrict__ new_run, const uint32_t* __restrict__ new_cls, uint64_t A,
+                               uint32_t icap, uint64_t* free_run, uint32_t* free_cls, long long* delta, uint32_t* err) {
+  const uint32_t lane = lane_id();
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  long long dsum = 0;
+  for (uint64_t a = w0; a < A; a += nw) {
+    DynVertex* r = vtx + aff[a];
+    const uint32_t d0 = r->deg, cls0 = r->cls;  // read by every lane before lane 0 rewrites the record
+    const uint64_t g0 = gstart[a], g1 = gstart[a + 1];
+    const uint32_t ac = act[a];
+    uint32_t d = d0;
+    if (ac == kActInline) {  // d0 + group size <= icap <= kInline: one id per lane
+      const uint32_t gs = (uint32_t)(g1 - g0);
+      const uint32_t x = lane < gs ? gcols[g0 + lane] : kInf;
+      bool fresh = lane < gs;
+      for (uint32_t j = 0; j < d0; ++j)
+        if (r->inl[j] == x) fresh = false;
+      for (uint32_t j = 0; j < 32; ++j) {
+        const uint32_t y = __shfl_sync(0xFFFFFFFFu, x, j);
+        if (j < lane && y == x) fresh = false;
+      }
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, fresh);
+      __syncwarp();
+      if (fresh) r->inl[d0 + __popc(m & lanemask_lt())] = x;
+      d = d0 + __popc(m);
+    } else {
+      const uint32_t c = new_cls[a];
+      const uint64_t run = new_run[a];
+      uint32_t* ids = pool + run * kBlockIds;
+      uint32_t* key = hkey + run * kHashSlots;
+      uint32_t* pos = hpos + run * kHashSlots;
+      const uint32_t mask = hmask(c);
+      for (uint64_t i0 = g0; i0 < g1; i0 += 32) {
+        const uint64_t i = i0 + lane;
+        uint32_t x = kInf, slot = 0;
+        bool fresh = false, done = i >= g1;
+        if (!done) {
+          x = gcols[i];
+          uint32_t h = hslot(x, c);
+          for (uint64_t it = 0; it <= mask; ++it) {
+            const uint32_t k = ld_cg(key + h);
+            if (k == x) {
+              done = true;
+              break;
+            }
+            if (k == kInf) {
+              const uint32_t o = atomicCAS(key + h, kInf, x);
+              if (o == kInf) {
+                fresh = done = true;
+                slot = h;
+                break;
+              }
+              if (o == x) {
+                done = true;
+                break;
+              }
+            }
+            h = (h + 1) & mask;
+          }
+          if (!done) *err = 1u;
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, fresh);
+        if (fresh) {
+          const uint32_t p = d + __popc(m & lanemask_lt());
+          ids[p] = x;
+          pos[slot] = p;
+        }
+        d += __popc(m);
+      }
+      __syncwarp();
+      if (ac == kActMove && cls0 == kNoRun && d <= icap) {
+        // an inline list the plan moved (upper bound) that stays within the
+        // inline capacity: back inline, and the new run is freed
+        const uint32_t y = lane < d ? ids[lane] : kInf;
+        __syncwarp();
+        if (lane < kInline) r->inl[lane] = y;
+        if (lane == 0) {
+          free_run[a] = run;
+          free_cls[a] = c;
+        }
+      } else if (lane == 0) {
+        if (ac == kActMove) {
+          r->cls = c;
+          r->run = run;
+        }
+        if (ac != kActKeep) r->inl[0] = 0;  // a fresh index has no tombstones
+      }
+    }
+    if (lane == 0) {
+      r->deg = d;
+      dsum += (long long)d - (long long)d0;
+    }
+  }
+  block_add_delta(dsum, delta);
+}
+
+// One warp per affected vertex applies its group of batch ids (delete).
+// s1, s2, s3: scratch with one entry per batch entry (freed positions, the
+// holes among them, the surviving tail positions), each group in its slice.
+__global__ void hdelete_kernel(DynVertex* vtx, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
+                               const uint32_t* __restrict__ aff, const uint64_t* __restrict__ gstart,
+                               const uint32_t* __restrict__ gcols, uint64_t A, uint32_t icap, uint32_t* s1,
+                               uint32_t* s2, uint32_t* s3, uint64_t* free_run, uint32_t* free_cls, long long* delta,
+                               uint32_t* err) {
+  const uint32_t lane = lane_id();
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  long long dsum = 0;
+  for (uint64_t a = w0; a < A; a += nw) {
+    DynVertex* r = vtx + aff[a];
+    const uint32_t d0 = r->deg, cls = r->cls;
+    const uint64_t g0 = gstart[a], g1 = gstart[a + 1];
+    if (lane == 0) {
+      free_run[a] = ~0ull;
+      free_cls[a] = kNoRun;
+    }
+    uint32_t d;
+    if (cls == kNoRun) {  // inline: lane j checks the j-th id against the group
+      const uint32_t y = lane < d0 ? r->inl[lane] : kInf;
+      bool keep = lane < d0;
+      if (keep)
+        for (uint64_t i = g0; i < g1; ++i)
+          if (gcols[i] == y) {
+            keep = false;
+            break;
+          }
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep);
+      d = __popc(m);
+      const uint32_t z = __shfl_sync(0xFFFFFFFFu, y, kth_bit(m, lane));
+      __syncwarp();
+      if (lane < kInline) r->inl[lane] = lane < d ? z : kInf;
+    } else {
+      const uint64_t run = r->run;
+      uint32_t* ids = pool + run * kBlockIds;
+      uint32_t* key = hkey + run * kHashSlots;
+      uint32_t* pos = hpos + run * kHashSlots;
+      const uint32_t mask = hmask(cls);
+      uint32_t ndel = 0;
+      // 1: found ids become tombstones; s1 = the position each one freed
+      for (uint64_t i0 = g0; i0 < g1; i0 += 32) {
+        const uint64_t i = i0 + lane;
+        uint32_t p = kInf;
+        if (i < g1) {
+          const uint32_t x = gcols[i];
+          uint32_t h = hslot(x, cls);
+          for (uint64_t it = 0; it <= mask; ++it) {
+            const uint32_t k = ld_cg(key + h);
+            if (k == kInf) break;
+            if (k == x) {
+              if (atomicCAS(key + h, x, kTomb) == x) p = pos[h];
+              break;
+            }
+            h = (h + 1) & mask;
+          }
+          s1[i] = p;
+        }
+        ndel += __popc(__ballot_sync(0xFFFFFFFFu, p != kInf));
+      }
+      d = d0 - ndel;
+      __syncwarp();
+      // 2: mark the freed positions
+      for (uint64_t i = g0 + lane; i < g1; i += 32) {
+        const uint32_t p = s1[i];
+        if (p != kInf) ids[p] = kInf;
+      }
+      __syncwarp();
+      // 3: holes (freed positions below d) and survivors (ids left in [d, d0))
+      uint32_t nh = 0, ns = 0;
+      for (uint64_t i0 = g0; i0 < g1; i0 += 32) {
+        const uint64_t i = i0 + lane;
+        const uint32_t p = i < g1 ? s1[i] : kInf;
+        const bool hole = p < d;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, hole);
+        if (hole) s2[g0 + nh + __popc(m & lanemask_lt())] = p;
+        nh += __popc(m);
+      }
+      for (uint32_t q0 = d; q0 < d0; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        const bool live = q < d0 && ids[q] != kInf;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, live);
+        if (live) s3[g0 + ns + __popc(m & lanemask_lt())] = q;
+        ns += __popc(m);
+      }
+      if (ns != nh) {
+        if (lane == 0) *err = 1u;
+        nh = ns < nh ? ns : nh;
+      }
+      __syncwarp();
+      // 4: survivors move into the holes; their index entries follow
+      for (uint32_t k0 = 0; k0 < nh; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        if (k < nh) {
+          const uint32_t p = s2[g0 + k], q = s3[g0 + k];
+          const uint32_t y = ids[q];
+          ids[p] = y;
+          uint32_t h = hslot(y, cls);
+          bool found = false;
+          for (uint64_t it = 0; it <= mask; ++it) {
+            if (ld_cg(key + h) == y) {
+              pos[h] = p;
+              found = true;
+              break;
+            }
+            h = (h + 1) & mask;
+          }
+          if (!found) *err = 1u;
+        }
+      }
+      __syncwarp();
+      if (d <= icap) {  // back inline; the run is freed
+        const uint32_t y = lane < d ? ids[lane] : kInf;
+        __syncwarp();
+        if (lane < kInline) r->inl[lane] = y;
+        if (lane == 0) {
+          r->cls = kNoRun;
+          r->run = 0;
+          free_run[a] = run;
+          free_cls[a] = cls;
+        }
+      } else if (lane == 0) {
+        r->inl[0] += ndel;  // tombstones
+      }
+    }
+    if (lane == 0) {
+      r->deg = d;
+      dsum += (long long)d - (long long)d0;
+    }
+  }
+  block_add_delta(dsum, delta);
+}
+
+// Enter every run list of a freshly loaded container into its index.
+byo_status build_hash_index(byo_graph* g, DynStore* d, uint64_t used_blocks, cudaStream_t s) {
+  const uint32_t n = g->n;
+  uint32_t *nfill = nullptr, *item = nullptr, *err = nullptr;
+  uint64_t* tstart = nullptr;
+  uint64_t NT = 0;
+  byo_status st = dev_alloc_t(&d->hkey, d->pool_blocks * kHashSlots, "hash index keys");
+  if (st == BYO_OK) st = dev_alloc_t(&d->hpos, d->pool_blocks * kHashSlots, "hash index positions");
+  if (st == BYO_OK) st = dev_alloc_t(&d->vcnt, n + 1ull, "semisort counters");
+  if (st == BYO_OK) st = dev_alloc_t(&d->vslot, n + 1ull, "semisort slots");
+  if (st == BYO_OK) st = tmp_alloc_t(&nfill, n + 1ull, s, "index fill tasks");
+  if (st == BYO_OK) st = tmp_alloc_t(&tstart, n + 1ull, s, "index fill starts");
+  if (st == BYO_OK) st = tmp_alloc_t(&err, 1, s, "index error");
+  if (st == BYO_OK) {
+    cudaMemsetAsync(d->vcnt, 0, sizeof(uint32_t) * (n + 1ull), s);
+    cudaMemsetAsync(d->hkey, 0xFF, sizeof(uint32_t) * used_blocks * kHashSlots, s);
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+    htask_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(d->vtx, nullptr, nullptr, nullptr, n, nullptr, nfill);
+    note_launch();
+    st = scan_u32_to_u64(nfill, tstart, n + 1ull, &NT, s);
+  }
+  if (st == BYO_OK) st = tmp_alloc_t(&item, NT + 1, s, "index fill items");
+  if (st == BYO_OK && NT) {
+    chunk_expand_kernel<<<grid_for(n, 256), 256, 0, s>>>(tstart, n, item);
+    hfill_kernel<<<grid_for(NT * 32, 256), 256, 0, s>>>(d->vtx, d->pool, d->hkey, d->hpos, nullptr, nullptr, nullptr,
+                                                         item, tstart, NT, err);
+    note_launch(2);
+  }
+  if (st == BYO_OK) {
+    uint32_t herr = 0;
+    cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "hash index build");
+    else if (herr) {
+      set_error("hash index build: an index ran out of slots");
+      st = BYO_ERR_CUDA;
+    }
+  }
+  tmp_free(nfill, s);
+  tmp_free(tstart, s);
+  tmp_free(item, s);
+  tmp_free(err, s);
+  return st;
+}
+
+// A batch on the hash-indexed variant: symmetrise, semisort by source, then
+// the insert or delete passes above.
+byo_status apply_batch_hashed(byo_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t k, bool insert,
+                              cudaStream_t s) {
+  DynStore* d = g->dyn;
+  const uint32_t n = g->n;
+  const uint64_t B = 2 * k;
+  const uint64_t Amax = B < n ? B : n;
+  uint32_t *rows = nullptr, *cols = nullptr, *flag = nullptr, *aff = nullptr, *gcnt = nullptr, *gcols = nullptr;
+  uint32_t *act = nullptr, *new_cls = nullptr, *free_cls = nullptr, *nclear = nullptr, *nfill = nullptr;
+  uint32_t *item_c = nullptr, *item_f = nullptr, *s1 = nullptr, *s2 = nullptr, *s3 = nullptr;
+  uint64_t *gstart = nullptr, *new_run = nullptr, *free_run = nullptr, *cstart = nullptr, *fstart = nullptr;
+  unsigned long long *nA = nullptr, *need = nullptr;
+  long long* delta = nullptr;
+  uint32_t** d_stacks = nullptr;
+  uint64_t* d_cap = nullptr;
+  uint64_t A = 0, Bv = 0, NTC = 0, NTF = 0;
+  uint32_t hflag[2] = {0, 0};  // [0]: an id >= n in the batch, [1]: an index inconsistency
+  byo_status st = tmp_alloc_t(&rows, B, s, "batch rows");
+  if (st == BYO_OK) st = tmp_alloc_t(&cols, B, s, "batch cols");
+  if (st == BYO_OK) st = tmp_alloc_t(&flag, 2, s, "batch flags");
+  if (st == BYO_OK) st = tmp_alloc_t(&nA, 1, s, "group count");
+  if (st == BYO_OK) st = tmp_alloc_t(&aff, Amax + 1, s, "group vertices");
+  if (st == BYO_OK) st = tmp_alloc_t(&delta, 1, s, "edge delta");
+  if (st == BYO_OK) {
+    cudaMemsetAsync(flag, 0, 2 * sizeof(uint32_t), s);
+    cudaMemsetAsync(nA, 0, sizeof(unsigned long long), s);
+    cudaMemsetAsync(delta, 0, sizeof(long long), s);
+    hsym_kernel<<<grid_for(k, 256), 256, 0, s>>>(src, dst, k, n, rows, cols, flag);
+    note_launch();
+    cudaError_t e = cudaMemcpyAsync(hflag, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "batch check");
+    else if (hflag[0]) {
+      set_error("batch: vertex id >= n");
+      st = BYO_ERR_INVALID_ARG;
+    }
+  }
+  // semisort: count per source, group starts, scatter into groups
+  if (st == BYO_OK) {
+    hhist_kernel<<<grid_for(B, 256), 256, 0, s>>>(rows, B, d->vcnt, d->vslot, aff, nA);
+    note_launch();
+    unsigned long long hA = 0;
+    cudaError_t e = cudaMemcpyAsync(&hA, nA, sizeof(hA), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "batch semisort");
+    A = hA;
+  }
+  if (st == BYO_OK && A > 0) {
+    st = tmp_alloc_t(&gcnt, A + 1, s, "group sizes");
+    if (st == BYO_OK) st = tmp_alloc_t(&gstart, A + 1, s, "group starts");
+    if (st == BYO_OK) {
+      hgcount_kernel<<<grid_for(A, 256), 256, 0, s>>>(aff, A, d->vcnt, gcnt);
+      note_launch();
+      st = scan_u32_to_u64(gcnt, gstart, A + 1, &Bv, s);
+    }
+    if (st == BYO_OK) st = tmp_alloc_t(&gcols, Bv + 1, s, "grouped batch");
+    if (st == BYO_OK) {
+      hscatter_kernel<<<grid_for(B, 256), 256, 0, s>>>(rows, cols, B, d->vcnt, d->vslot, gstart, gcols);
+      note_launch();
+    } else {
+      cudaMemsetAsync(d->vcnt, 0, sizeof(uint32_t) * (n + 1ull), s);  // the counters must be zero between batches
+    }
+  }
+  if (st == BYO_OK && A > 0) st = tmp_alloc_t(&free_run, A + 1, s, "freed runs");
+  if (st == BYO_OK && A > 0) st = tmp_alloc_t(&free_cls, A + 1, s, "freed classes");
+  if (st == BYO_OK && A > 0) st = tmp_alloc_t(&d_stacks, kClasses, s, "stack table");
+  if (st == BYO_OK && A > 0) st = tmp_alloc_t(&d_cap, kClasses, s, "stack capacities");
+  if (st == BYO_OK && A > 0) {
+    cudaMemcpyAsync(d_stacks, d->stacks, sizeof(uint32_t*) * kClasses, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_cap, d->stack_cap, sizeof(uint64_t) * kClasses, cudaMemcpyHostToDevice, s);
+  }
+  if (st == BYO_OK && A > 0 && insert) {
+    st = tmp_alloc_t(&act, A + 1, s, "actions");
+    if (st == BYO_OK) st = tmp_alloc_t(&new_cls, A + 1, s, "new classes");
+    if (st == BYO_OK) st = tmp_alloc_t(&new_run, A + 1, s, "new runs");
+    if (st == BYO_OK) st = tmp_alloc_t(&need, 1, s, "need");
+    if (st == BYO_OK) {
+      cudaMemsetAsync(need, 0, sizeof(unsigned long long), s);
+      hplan_kernel<<<grid_for(A, 256), 256, 0, s>>>(d->vtx, aff, gstart, A, n, d->icap, act, new_cls, need);
+      note_launch();
+      unsigned long long hneed = 0, hbump = 0;
+      cudaError_t e = cudaMemcpyAsync(&hneed, need, sizeof(hneed), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&hbump, d->bump, sizeof(hbump), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = cuda_status(e, "pool check");
+      else if (hbump + hneed > d->pool_blocks) st = grow_pool(d, hbump, (hbump + hneed) * 3 / 2 + 4096, s);
+    }
+    if (st == BYO_OK) st = tmp_alloc_t(&nclear, A + 1, s, "clear tasks");
+    if (st == BYO_OK) st = tmp_alloc_t(&nfill, A + 1, s, "fill tasks");
+    if (st == BYO_OK) st = tmp_alloc_t(&cstart, A + 1, s, "clear task starts");
+    if (st == BYO_OK) st = tmp_alloc_t(&fstart, A + 1, s, "fill task starts");
+    if (st == BYO_OK) {
+      halloc_kernel<<<grid_for(A, 256), 256, 0, s>>>(d->vtx, aff, act, new_cls, A, d_stacks, d->tops, d->bump,
+                                                      new_run, free_run, free_cls);
+      clamp_tops_kernel<<<1, 32, 0, s>>>(d->tops);
+      htask_count_kernel<<<grid_for(A, 256), 256, 0, s>>>(d->vtx, aff, act, new_cls, A, nclear, nfill);
+      note_launch(3);
+      st = scan_u32_to_u64(nclear, cstart, A + 1, &NTC, s);
+    }
+    if (st == BYO_OK) st = scan_u32_to_u64(nfill, fstart, A + 1, &NTF, s);
+    if (st == BYO_OK) st = tmp_alloc_t(&item_c, NTC + 1, s, "clear task items");
+    if (st == BYO_OK) st = tmp_alloc_t(&item_f, NTF + 1, s, "fill task items");
+    if (st == BYO_OK) {
+      if (NTC) {
+        chunk_expand_kernel<<<grid_for(A, 256), 256, 0, s>>>(cstart, A, item_c);
+        hclear_kernel<<<grid_for(NTC * 32, 256), 256, 0, s>>>(item_c, cstart, NTC, new_run, new_cls, d->hkey);
+        note_launch(2);
+      }
+      if (NTF) {
+        chunk_expand_kernel<<<grid_for(A, 256), 256, 0, s>>>(fstart, A, item_f);
+        hfill_kernel<<<grid_for(NTF * 32, 256), 256, 0, s>>>(d->vtx, d->pool, d->hkey, d->hpos, aff, new_run, new_cls,
+                                                              item_f, fstart, NTF, flag + 1);
+        note_launch(2);
+      }
+      hinsert_kernel<<<grid_for(A * 32, 256), 256, 0, s>>>(d->vtx, d->pool, d->hkey, d->hpos, aff, gstart, gcols, act,
+                                                            new_run, new_cls, A, d->icap, free_run, free_cls, delta,
+                                                            flag + 1);
+      note_launch();
+    }
+  }
+  if (st == BYO_OK && A > 0 && !insert) {
+    st = tmp_alloc_t(&s1, Bv + 1, s, "freed positions");
+    if (st == BYO_OK) st = tmp_alloc_t(&s2, Bv + 1, s, "holes");
+    if (st == BYO_OK) st = tmp_alloc_t(&s3, Bv + 1, s, "survivors");
+    if (st == BYO_OK) {
+      hdelete_kernel<<<grid_for(A * 32, 256), 256, 0, s>>>(d->vtx, d->pool, d->hkey, d->hpos, aff, gstart, gcols, A,
+                                                            d->icap, s1, s2, s3, free_run, free_cls, delta, flag + 1);
+      note_launch();
+    }
+  }
+  if (st == BYO_OK && A > 0) {
+    free_kernel<<<grid_for(A, 256), 256, 0, s>>>(free_run, free_cls, A, d_stacks, d->tops, d_cap);
+    note_launch();
+    long long hdelta = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hdelta, delta, sizeof(hdelta), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflag + 1, flag + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = cuda_status(e, "hashed batch apply");
+    } else {
+      g->m = (uint64_t)((long long)g->m + hdelta);
+      if (hflag[1]) {
+        set_error("hashed batch apply: a hash index ran out of slots or lost an id");
+        st = BYO_ERR_CUDA;
+      }
+    }
+  }
+  tmp_free(rows, s);
+  tmp_free(cols, s);
+  tmp_free(flag, s);
+  tmp_free(nA, s);
+  tmp_free(aff, s);
+  tmp_free(delta, s);
+  tmp_free(gcnt, s);
+  tmp_free(gstart, s);
+  tmp_free(gcols, s);
+  tmp_free(act, s);
+  tmp_free(new_cls, s);
+  tmp_free(new_run, s);
+  tmp_free(need, s);
+  tmp_free(free_run, s);
+  tmp_free(free_cls, s);
+  tmp_free(d_stacks, s);
+  tmp_free(d_cap, s);
+  tmp_free(nclear, s);
+  tmp_free(nfill, s);
+  tmp_free(cstart, s);
+  tmp_free(fstart, s);
+  tmp_free(item_c, s);
+  tmp_free(item_f, s);
+  tmp_free(s1, s);
+  tmp_free(s2, s);
+  tmp_free(s3, s);
+  if (A > 0 && st == BYO_OK) {
+    g->buckets_stale = true;
+    st = rebuild_buckets(g, s);
+    if (st == BYO_OK) g->buckets_stale = false;
+  }
+  return st;
+}
+
 byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t k, bool insert,
                        cudaStream_t s) {
   DynStore* d = g->dyn;
+  if (d->hashed) return apply_batch_hashed(g, src, dst, k, insert, s);
   uint32_t *rows = nullptr, *cols = nullptr;
   uint64_t B = 0;
   BYO_RETURN_IF(sort_unique_pairs(g->n, src, dst, k, true, s, &rows, &cols, &B));
@@ -545,21 +1280,64 @@ byo_status dyn_space(const byo_graph* g, uint64_t* host_bytes, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   tmp_free(blocks, s);
   if (e != cudaSuccess) return cuda_status(e, "byo_space");
-  *host_bytes = sizeof(DynVertex) * ((uint64_t)g->n + 1) + (uint64_t)hb * kBlockIds * sizeof(uint32_t);
+  // a block holds 32 ids; the hash-indexed variant adds its 64 index slots (key and position)
+  const uint64_t per_block = kBlockIds * sizeof(uint32_t) + (g->dyn->hashed ? kHashSlots * 2 * sizeof(uint32_t) : 0);
+  *host_bytes = sizeof(DynVertex) * ((uint64_t)g->n + 1) + (uint64_t)hb * per_block;
   return BYO_OK;
 }
 
+__global__ void dyn_sort_keys_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col, uint32_t n,
+                                     uint64_t* keys) {
+  const uint32_t lane = lane_id();
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t v = w0; v < n; v += nw)
+    for (uint64_t i = off[v] + lane; i < off[v + 1]; i += 32) keys[i] = (v << 32) | col[i];
+}
+
+__global__ void dyn_sort_cols_kernel(const uint64_t* __restrict__ keys, uint64_t m, uint32_t* col) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    col[i] = (uint32_t)keys[i];
+}
+
+byo_status dyn_sort_lists(const byo_graph* g, const uint64_t* off, uint32_t* col, cudaStream_t s) {
+  const uint64_t m = g->m;
+  if (m == 0) return BYO_OK;
+  uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr;
+  byo_status st = tmp_alloc_t(&keys, m, s, "export sort keys");
+  if (st == BYO_OK) st = tmp_alloc_t(&tmp, m, s, "export sort scratch");
+  if (st == BYO_OK) {
+    dyn_sort_keys_kernel<<<grid_for((uint64_t)g->n * 32, 256), 256, 0, s>>>(off, col, g->n, keys);
+    note_launch();
+    const int idb = g->n > 1 ? 32 - __builtin_clz(g->n - 1) : 1;
+    st = radix_sort_u64(keys, tmp, m, 32 + idb, &sorted, s);
+  }
+  if (st == BYO_OK) {
+    dyn_sort_cols_kernel<<<grid_for(m, 256), 256, 0, s>>>(sorted, m, col);
+    note_launch();
+  }
+  tmp_free(keys, s);
+  tmp_free(tmp, s);
+  return st;
+}
+
 byo_status dyn_from_csr(byo_graph* g, cudaStream_t s) {
+  if (g->n > (1u << 31)) {  // a list of up to n - 1 ids must fit a run of at most 2^26 blocks
+    set_error("dynamic containers hold at most 2^31 vertices");
+    return BYO_ERR_UNSUPPORTED;
+  }
   DynStore* d = new (std::nothrow) DynStore();
   if (!d) {
     set_error("host allocation failed");
     return BYO_ERR_OUT_OF_MEMORY;
   }
   d->icap = (g->flags & BYO_DYN_NO_INLINE) ? 0u : kInline;
+  d->hashed = (g->flags & BYO_DYN_HASH) != 0;
   byo_status st = dev_alloc_t(&d->vtx, g->n + 1ull, "vertex records");
   if (st == BYO_OK) st = dev_alloc_t(&d->bump, 1, "pool cursor");
   if (st == BYO_OK) st = dev_alloc_t(&d->tops, kClasses, "stack tops");
   if (st == BYO_OK) st = g->off64 ? load_from_csr<uint64_t>(g, d, s) : load_from_csr<uint32_t>(g, d, s);
+  if (st == BYO_OK && d->hashed) st = build_hash_index(g, d, d->pool_blocks, s);
   if (st != BYO_OK) {
     dyn_free(d);
     return st;

@@ -641,6 +641,10 @@ byo_status byo_graph_build(uint32_t n, const uint32_t* src, const uint32_t* dst,
     set_error("byo_graph_build: BYO_DYN_NO_INLINE applies to BYO_DYNAMIC only");
     return BYO_ERR_INVALID_ARG;
   }
+  if ((flags & BYO_DYN_HASH) && !(flags & BYO_DYNAMIC)) {
+    set_error("byo_graph_build: BYO_DYN_HASH applies to BYO_DYNAMIC only");
+    return BYO_ERR_INVALID_ARG;
+  }
   if (!(flags & (BYO_CSR | BYO_DYNAMIC)) || (flags & BYO_CSR && flags & BYO_DYNAMIC)) {
     set_error("byo_graph_build: exactly one of BYO_CSR / BYO_DYNAMIC is required");
     return BYO_ERR_INVALID_ARG;
@@ -783,6 +787,7 @@ byo_status byo_graph_export_csr(const byo_graph* g, uint64_t* offsets, uint32_t*
         ::byo::note_launch();
         return BYO_OK;
       });
+      if (st == BYO_OK && g->dyn && g->dyn->hashed) st = dyn_sort_lists(g, offsets, col, s);
     }
   }
   tmp_free(deg, s);

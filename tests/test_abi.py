@@ -48,3 +48,18 @@ def test_binding_struct_layouts():
     assert _byo.byo_bfs_iter.t_ns.offset == 64
     assert ctypes.sizeof(_byo.byo_sched) == 40 and _byo.byo_sched.mlp.offset == 24
     assert _byo.byo_sched.action.offset == 32 and _byo.byo_sched.flags.offset == 36
+
+
+def test_binding_constants_match_header():
+    """Every numeric #define of include/byo.h has the same value in the binding."""
+    from paper_2405_11671_gb300 import _byo
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defs = re.findall(r"^#define[ \t]+(BYO_[A-Z0-9_]+)[ \t]+(\S.*?)[ \t]*$", txt, flags=re.M)
+    assert len(defs) >= 8
+    for name, val in defs:
+        plain = re.fullmatch(r"(0x[0-9A-Fa-f]+|\d+)u?", val)
+        shift = re.fullmatch(r"\((\d+)u?\s*<<\s*(\d+)\)", val)
+        assert plain or shift, (name, val)
+        want = int(plain.group(1), 0) if plain else int(shift.group(1)) << int(shift.group(2))
+        assert hasattr(_byo, name), name
+        assert getattr(_byo, name) == want, name

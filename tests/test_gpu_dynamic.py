@@ -1,4 +1,6 @@
-"""The dynamic blocked-adjacency container against the oracle's edge set.
+"""The dynamic blocked-adjacency container, sorted and hash-indexed
+(BYO_DYN_HASH: unsorted lists, per-run hash indexes, semisorted batches),
+against the oracle's edge set.
 
 After every batch the container's contents (exported as CSR), m and the
 degrees must equal the oracle's bit for bit; after every round BFS levels
@@ -25,6 +27,12 @@ def byo():
     import paper_2405_11671_gb300 as b
     b.load()
     return b
+
+
+@pytest.fixture(params=["sorted", "hashed"])
+def dflags(request, byo):
+    """BYO_DYNAMIC, alone or with the hash-indexed variant."""
+    return byo.BYO_DYNAMIC | (byo.BYO_DYN_HASH if request.param == "hashed" else 0)
 
 
 def dev(a):
@@ -58,7 +66,7 @@ def algorithms_match(byo, g, ref, sources):
 
 
 @pytest.mark.parametrize("name", ["tiny", "rmat12", "grid"])
-def test_dynamic_build_equals_csr(byo, name):
+def test_dynamic_build_equals_csr(byo, dflags, name):
     if name == "tiny":
         n, src, dst = graphgen.workload("tiny")
     elif name == "rmat12":
@@ -66,16 +74,16 @@ def test_dynamic_build_equals_csr(byo, name):
     else:
         n, src, dst = graphgen.grid_small(50, 60, 0.1, 1e-3, 3)
     ref = oracle.csr_build(n, src, dst)
-    g = byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    g = byo.Graph(n, dev(src), dev(dst), dflags | byo.BYO_SYMMETRIZE)
     same_contents(byo, g, ref)
     algorithms_match(byo, g, ref, [0] + graphgen.pick_sources(n, src, dst, 1, 3).tolist())
     g.close()
 
 
-def test_dynamic_rounds_match_oracle(byo):
+def test_dynamic_rounds_match_oracle(byo, dflags):
     scale, seed = 13, 0xB14
     n, src, dst = graphgen.rmat_small(scale, 8, seed)
-    g = byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    g = byo.Graph(n, dev(src), dev(dst), dflags | byo.BYO_SYMMETRIZE)
     dg = oracle.DynGraph(n, src, dst)
     pool_s, pool_d = [src], [dst]
     for r in range(5):
@@ -102,9 +110,9 @@ def test_dynamic_rounds_match_oracle(byo):
     g.close()
 
 
-def test_hub_grows_through_classes_and_shrinks(byo):
+def test_hub_grows_through_classes_and_shrinks(byo, dflags):
     n = 20000
-    g = byo.Graph(n, dev([1]), dev([2]), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    g = byo.Graph(n, dev([1]), dev([2]), dflags | byo.BYO_SYMMETRIZE)
     dg = oracle.DynGraph(n, [1], [2])
     for hi in (5, 11, 12, 13, 40, 700, 5000, 19999):  # inline -> runs of growing class
         leaves = np.arange(3, hi + 3, dtype=np.uint32) % n
@@ -122,9 +130,9 @@ def test_hub_grows_through_classes_and_shrinks(byo):
     g.close()
 
 
-def test_insert_then_delete_restores(byo):
+def test_insert_then_delete_restores(byo, dflags):
     n, src, dst = graphgen.rmat_small(12, 8, 77)
-    g = byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    g = byo.Graph(n, dev(src), dev(dst), dflags | byo.BYO_SYMMETRIZE)
     before = byo.byo_graph_export_csr(g.handle)
     b_s, b_d = graphgen.er(n, 5000, 99)
     base = oracle.csr_build(n, src, dst)
@@ -138,14 +146,14 @@ def test_insert_then_delete_restores(byo):
     g.close()
 
 
-def test_batch_errors(byo):
+def test_batch_errors(byo, dflags):
     n, src, dst = graphgen.rmat_small(10, 4, 1)
     g = byo.Graph(n, dev(src), dev(dst))
     with pytest.raises(byo.ByoError) as e:
         byo.byo_insert_batch(g.handle, dev([1]), dev([2]))
     assert e.value.status == byo.BYO_ERR_UNSUPPORTED
     g.close()
-    g = byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
+    g = byo.Graph(n, dev(src), dev(dst), dflags | byo.BYO_SYMMETRIZE)
     with pytest.raises(byo.ByoError) as e:
         byo.byo_insert_batch(g.handle, dev([1]), dev([n]))
     assert e.value.status == byo.BYO_ERR_INVALID_ARG
@@ -187,3 +195,50 @@ def test_inline_head_ablation_and_space(byo):
     assert torch.equal(got[12][0], got[0][0]) and torch.equal(got[12][1], got[0][1])
     with pytest.raises(byo.ByoError):
         byo.Graph(n, dev(src), dev(dst), byo.BYO_CSR | byo.BYO_DYN_NO_INLINE)
+
+
+def test_hashed_index_rebuilds_and_space(byo):
+    """The hash-indexed container: a hub whose list is emptied and refilled
+    again and again (tombstones pile up in its index until an insert rebuilds
+    it in place), a small graph flooded with duplicate pairs (an inline list
+    planned into a run that stays within the inline capacity, so it goes back
+    inline), and byo_space: 64-byte records plus, per block of the runs, 128
+    bytes of ids and 512 of index slots."""
+    n = 6000
+    flags = byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE | byo.BYO_DYN_HASH
+    with byo.Graph(n, dev([1]), dev([2]), flags) as g:
+        dg = oracle.DynGraph(n, [1], [2])
+        rng = np.random.default_rng(41)
+        for r in range(8):
+            leaves = rng.choice(np.arange(3, n, dtype=np.uint32), size=900, replace=False)
+            hub = np.zeros(len(leaves), np.uint32)
+            byo.byo_insert_batch(g.handle, dev(hub), dev(leaves))
+            dg.insert(hub, leaves)
+            same_contents(byo, g, dg.csr())
+            gone = leaves[rng.random(len(leaves)) < 0.9]
+            byo.byo_delete_batch(g.handle, dev(gone), dev(np.zeros(len(gone), np.uint32)))
+            dg.delete(gone, np.zeros(len(gone), np.uint32))
+            same_contents(byo, g, dg.csr())
+        algorithms_match(byo, g, dg.csr(), [0, 1])
+    n = 10
+    base_s, base_d = np.zeros(4, np.uint32), np.arange(1, 5, dtype=np.uint32)
+    with byo.Graph(n, dev(base_s), dev(base_d), flags) as g:
+        dg = oracle.DynGraph(n, base_s, base_d)
+        ins_s = np.zeros(80, np.uint32)
+        ins_d = np.array([5, 1] * 40, np.uint32)
+        byo.byo_insert_batch(g.handle, dev(ins_s), dev(ins_d))
+        dg.insert(ins_s, ins_d)
+        same_contents(byo, g, dg.csr())
+        assert byo.byo_space(g.handle) == 64 * (n + 1)  # every list inline again
+        algorithms_match(byo, g, dg.csr(), [0, 5])
+    n, src, dst = graphgen.rmat_small(13, 8, 77)
+    ref = oracle.csr_build(n, src, dst)
+    deg = np.diff(ref.off.astype(np.int64))
+    d = deg[deg > 12]
+    blocks = int(np.sum(1 << np.ceil(np.log2((d + 31) // 32)).astype(np.int64)))
+    with byo.Graph(n, dev(src), dev(dst), flags) as g:
+        assert byo.byo_space(g.handle) == 64 * (n + 1) + (128 + 512) * blocks
+        same_contents(byo, g, ref)
+    with pytest.raises(byo.ByoError) as e:
+        byo.Graph(n, dev(src), dev(dst), byo.BYO_CSR | byo.BYO_DYN_HASH)
+    assert e.value.status == byo.BYO_ERR_INVALID_ARG

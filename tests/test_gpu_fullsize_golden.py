@@ -14,9 +14,9 @@ on the GPU through the C ABI and compares:
   (exact);
 * RMAT-22 and the grid: the triangle count (their BFS, CC and PageRank are
   compared element by element in test_gpu_fullsize.py);
-* the dynamic container (RMAT-24 base, ten rounds of 1 M inserts and 1 M
-  deletes): after every round the container's contents, BFS levels, CC labels
-  and sampled PageRank;
+* the dynamic container, sorted and hash-indexed (RMAT-24 base, ten rounds of
+  1 M inserts and 1 M deletes): after every round the container's contents,
+  BFS levels, CC labels and sampled PageRank;
 * the 256-graph batch: every member's 64-source level block and CC labels.
 """
 import hashlib
@@ -131,12 +131,14 @@ def test_triangle_count_full_size(byo, name):
         assert byo.byo_tc(g.handle) == ref["triangles"]
 
 
-def test_dynamic_rounds_full_size(byo):
+@pytest.mark.parametrize("hashed", [False, True], ids=["sorted", "hashed"])
+def test_dynamic_rounds_full_size(byo, hashed):
     ref = gold("dynamic")
     n, src, dst = graphgen.workload("rmat24")
     s0 = ref["source"]
     assert s0 == int(graphgen.pick_sources(n, src, dst, 1, graphgen.SEEDS["rmat24"] + 1)[0])
-    with byo.Graph(n, dev(src), dev(dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE) as g:
+    flags = byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE | (byo.BYO_DYN_HASH if hashed else 0)
+    with byo.Graph(n, dev(src), dev(dst), flags) as g:
         for want, (ins_s, ins_d, del_s, del_d) in zip(ref["rounds"], graphgen.dynamic_rounds(n, src, dst)):
             byo.byo_insert_batch(g.handle, dev(ins_s), dev(ins_d))
             byo.byo_delete_batch(g.handle, dev(del_s), dev(del_d))
