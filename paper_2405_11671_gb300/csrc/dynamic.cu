@@ -19,6 +19,8 @@
 //   6. choose storage for the new list (inline, keep the run, pop a free run of
 //      the right class, or bump-allocate), copy the list back, free old runs;
 //   7. update m and the degree-bucket order used by the algorithm kernels.
+#include <memory>
+
 #include "byo_internal.cuh"
 #include "container.cuh"
 #include "prof.cuh"
@@ -623,39 +625,439 @@ __global__ void hfill_kernel(const DynVertex* __restrict__ vtx, uint32_t* pool, 
   }
 }
 
-// adds a warp's degree changes (lane 0's dsum) into *delta, one atomic per block
+// adds the threads' degree changes into *delta, one atomic per block
 __device__ __forceinline__ void block_add_delta(long long dsum, long long* delta) {
   __shared__ long long bsum;
   if (threadIdx.x == 0) bsum = 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xFFFFFFFFu, dsum, o);
   __syncthreads();
   if (lane_id() == 0 && dsum) atomicAdd((unsigned long long*)&bsum, (unsigned long long)dsum);
   __syncthreads();
   if (threadIdx.x == 0 && bsum) atomicAdd((unsigned long long*)delta, (unsigned long long)bsum);
 }
 
-// k-th (from 0) set bit of m, or 0 if m has fewer
-__device__ __forceinline__ uint32_t kth_bit(uint32_t m, uint32_t k) {
-  for (uint32_t j = 0; j < k && m; ++j) m &= m - 1;
-  return m ? (uint32_t)(__ffs(m) - 1) : 0u;
+// Groups of at most kSmallGroup ids (most of a batch of scattered pairs) are
+// applied by one thread each; larger ones by a warp (mid[]) or, above
+// kWarpGroupMax ids, by a CTA (huge[]).
+constexpr uint32_t kSmallGroup = 4;
+
+__global__ void hsplit_kernel(const uint64_t* __restrict__ gstart, uint64_t A, uint32_t warp_max, uint32_t* mid,
+                              uint32_t* nmid, uint32_t* huge, uint32_t* nhuge) {
+  const uint32_t lane = lane_id();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t a0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; a0 < A; a0 += stride) {
+    const uint64_t a = a0 + lane;
+    const uint64_t gs = a < A ? gstart[a + 1] - gstart[a] : 0;
+    const bool m1 = gs > kSmallGroup && gs <= warp_max, m2 = gs > warp_max;
+    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, m1), b2 = __ballot_sync(0xFFFFFFFFu, m2);
+    uint32_t base1 = 0, base2 = 0;
+    if (lane == 0 && b1) base1 = atomicAdd(nmid, (uint32_t)__popc(b1));
+    if (lane == 0 && b2) base2 = atomicAdd(nhuge, (uint32_t)__popc(b2));
+    base1 = __shfl_sync(0xFFFFFFFFu, base1, 0);
+    base2 = __shfl_sync(0xFFFFFFFFu, base2, 0);
+    if (m1) mid[base1 + __popc(b1 & lanemask_lt())] = (uint32_t)a;
+    if (m2) huge[base2 + __popc(b2 & lanemask_lt())] = (uint32_t)a;
+  }
 }
 
-// One warp per affected vertex applies its group of batch ids (insert).
+// the slot *h of key y in an index of class c; false if y is not there
+__device__ __forceinline__ bool hfind(const uint32_t* key, uint32_t y, uint32_t c, uint32_t* h) {
+  const uint32_t mask = hmask(c);
+  uint32_t at = hslot(y, c);
+  for (uint64_t it = 0; it <= mask; ++it) {
+    const uint32_t k = key[at];
+    if (k == y) {
+      *h = at;
+      return true;
+    }
+    if (k == kInf) return false;
+    at = (at + 1) & mask;
+  }
+  return false;
+}
+
+// One thread applies a small insert group to a list it alone owns.
+__device__ void hinsert_thread(DynVertex* r, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
+                               const uint32_t* __restrict__ gcols, uint64_t g0, uint64_t g1, uint32_t ac, uint32_t c,
+                               uint64_t run, uint32_t icap, uint64_t* free_run, uint32_t* free_cls, uint64_t a,
+                               long long& dsum, uint32_t* err) {
+  const uint32_t d0 = r->deg, cls0 = r->cls;
+  uint32_t d = d0;
+  if (ac == kActInline) {
+    for (uint64_t i = g0; i < g1; ++i) {
+      const uint32_t x = gcols[i];
+      bool dup = false;
+      for (uint32_t j = 0; j < d; ++j) dup |= r->inl[j] == x;
+      if (!dup) r->inl[d++] = x;
+    }
+  } else {
+    uint32_t* ids = pool + run * kBlockIds;
+    uint32_t* key = hkey + run * kHashSlots;
+    uint32_t* pos = hpos + run * kHashSlots;
+    const uint32_t mask = hmask(c);
+    for (uint64_t i = g0; i < g1; ++i) {
+      const uint32_t x = gcols[i];
+      uint32_t h = hslot(x, c);
+      bool done = false;
+      for (uint64_t it = 0; it <= mask; ++it) {
+        const uint32_t k = key[h];
+        if (k == x) {
+          done = true;
+          break;
+        }
+        if (k == kInf) {
+          key[h] = x;
+          pos[h] = d;
+          ids[d++] = x;
+          done = true;
+          break;
+        }
+        h = (h + 1) & mask;
+      }
+      if (!done) *err = 1u;
+    }
+    if (ac == kActMove && cls0 == kNoRun && d <= icap) {  // stays within the inline capacity
+      for (uint32_t j = 0; j < kInline; ++j) r->inl[j] = j < d ? ids[j] : kInf;
+      free_run[a] = run;
+      free_cls[a] = c;
+    } else {
+      if (ac == kActMove) {
+        r->cls = c;
+        r->run = run;
+      }
+      if (ac != kActKeep) r->inl[0] = 0;
+    }
+  }
+  r->deg = d;
+  dsum += (long long)d - (long long)d0;
+}
+
+// One thread applies a small delete group: each found id becomes a tombstone
+// and the list's last id moves into its place.
+__device__ void hdelete_thread(DynVertex* r, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
+                               const uint32_t* __restrict__ gcols, uint64_t g0, uint64_t g1, uint32_t icap,
+                               uint64_t* free_run, uint32_t* free_cls, uint64_t a, long long& dsum, uint32_t* err) {
+  const uint32_t d0 = r->deg, cls = r->cls;
+  uint32_t d = d0;
+  free_run[a] = ~0ull;
+  free_cls[a] = kNoRun;
+  if (cls == kNoRun) {
+    for (uint64_t i = g0; i < g1; ++i) {
+      const uint32_t x = gcols[i];
+      for (uint32_t j = 0; j < d; ++j)
+        if (r->inl[j] == x) {
+          r->inl[j] = r->inl[d - 1];
+          r->inl[d - 1] = kInf;
+          --d;
+          break;
+        }
+    }
+  } else {
+    const uint64_t run = r->run;
+    uint32_t* ids = pool + run * kBlockIds;
+    uint32_t* key = hkey + run * kHashSlots;
+    uint32_t* pos = hpos + run * kHashSlots;
+    uint32_t tombs = r->inl[0];
+    for (uint64_t i = g0; i < g1; ++i) {
+      uint32_t h;
+      if (!hfind(key, gcols[i], cls, &h)) continue;
+      key[h] = kTomb;
+      const uint32_t p = pos[h];
+      const uint32_t last = d - 1;
+      if (p != last) {
+        const uint32_t y = ids[last];
+        ids[p] = y;
+        uint32_t hy;
+        if (hfind(key, y, cls, &hy)) pos[hy] = p;
+        else *err = 1u;
+      }
+      --d;
+      ++tombs;
+    }
+    if (d <= icap) {  // back inline; the run is freed
+      for (uint32_t j = 0; j < kInline; ++j) r->inl[j] = j < d ? ids[j] : kInf;
+      r->cls = kNoRun;
+      r->run = 0;
+      free_run[a] = run;
+      free_cls[a] = cls;
+    } else {
+      r->inl[0] = tombs;
+    }
+  }
+  r->deg = d;
+  dsum += (long long)d - (long long)d0;
+}
+
+// A team of threads applying one group: a warp (groups of kSmallGroup + 1 ..
+// kWarpGroupMax ids) or a whole CTA (larger groups: a hub's share of a batch).
+constexpr uint32_t kWarpGroupMax = 256;
+
+template <bool kCta>
+struct Team {
+  uint32_t* sh;  // kCta: one word per warp of the CTA
+  __device__ __forceinline__ uint32_t id() const { return kCta ? threadIdx.x : lane_id(); }
+  __device__ __forceinline__ uint32_t size() const { return kCta ? blockDim.x : 32u; }
+  __device__ __forceinline__ void sync() const {
+    if (kCta) __syncthreads();
+    else __syncwarp();
+  }
+  // rank of this thread among the team's threads with f set (in id order),
+  // and their number; a barrier of the team
+  __device__ __forceinline__ uint32_t scan(bool f, uint32_t* total) const {
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
+    if (!kCta) {
+      *total = __popc(m);
+      return __popc(m & lanemask_lt());
+    }
+    const uint32_t w = threadIdx.x >> 5;
+    __syncthreads();  // the previous scan's readers are done with sh
+    if (lane_id() == 0) sh[w] = __popc(m);
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
+    for (uint32_t i = 0; i < (blockDim.x >> 5); ++i) {
+      const uint32_t c = sh[i];
+      before += i < w ? c : 0u;
+      tot += c;
+    }
+    *total = tot;
+    return before + __popc(m & lanemask_lt());
+  }
+};
+
+// A team applies an insert group to a list that is in, or moves into, a run:
+// a CAS that takes an empty slot admits a new id, appended at the list's end.
+template <bool kCta>
+__device__ void hinsert_team(const Team<kCta>& T, DynVertex* r, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
+                             const uint32_t* __restrict__ gcols, uint64_t g0, uint64_t g1, uint32_t ac, uint32_t c,
+                             uint64_t run, uint32_t icap, uint64_t* free_run, uint32_t* free_cls, uint64_t a,
+                             long long& dsum, uint32_t* err) {
+  const uint32_t t = T.id();
+  const uint32_t d0 = r->deg, cls0 = r->cls;
+  uint32_t* ids = pool + run * kBlockIds;
+  uint32_t* key = hkey + run * kHashSlots;
+  uint32_t* pos = hpos + run * kHashSlots;
+  const uint32_t mask = hmask(c);
+  uint32_t d = d0;
+  for (uint64_t i0 = g0; i0 < g1; i0 += T.size()) {
+    const uint64_t i = i0 + t;
+    uint32_t x = kInf, slot = 0;
+    bool fresh = false;
+    if (i < g1) {
+      x = gcols[i];
+      uint32_t h = hslot(x, c);
+      bool done = false;
+      for (uint64_t it = 0; it <= mask; ++it) {
+        const uint32_t k = ld_cg(key + h);
+        if (k == x) {
+          done = true;
+          break;
+        }
+        if (k == kInf) {
+          const uint32_t o = atomicCAS(key + h, kInf, x);
+          if (o == kInf) {
+            fresh = done = true;
+            slot = h;
+            break;
+          }
+          if (o == x) {
+            done = true;
+            break;
+          }
+        }
+        h = (h + 1) & mask;
+      }
+      if (!done) *err = 1u;
+    }
+    uint32_t cnt;
+    const uint32_t rk = T.scan(fresh, &cnt);
+    if (fresh) {
+      ids[d + rk] = x;
+      pos[slot] = d + rk;
+    }
+    d += cnt;
+  }
+  T.sync();
+  if (ac == kActMove && cls0 == kNoRun && d <= icap) {
+    // an inline list the plan moved (upper bound) that stays within the
+    // inline capacity: back inline, and the new run is freed
+    const uint32_t y = t < d ? ids[t] : kInf;
+    T.sync();
+    if (t < kInline) r->inl[t] = y;
+    if (t == 0) {
+      free_run[a] = run;
+      free_cls[a] = c;
+    }
+  } else if (t == 0) {
+    if (ac == kActMove) {
+      r->cls = c;
+      r->run = run;
+    }
+    if (ac != kActKeep) r->inl[0] = 0;  // a fresh index has no tombstones
+  }
+  if (t == 0) {
+    r->deg = d;
+    dsum += (long long)d - (long long)d0;
+  }
+}
+
+// A team applies a delete group.  Run lists: found keys become tombstones;
+// the holes below the new degree are filled with the ids that survive above
+// it, whose index entries follow.  s1, s2, s3: scratch with one entry per
+// batch entry (freed positions, the holes among them, the surviving tail
+// positions), each group in its own slice.
+template <bool kCta>
+__device__ void hdelete_team(const Team<kCta>& T, DynVertex* r, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
+                             const uint32_t* __restrict__ gcols, uint64_t g0, uint64_t g1, uint32_t icap, uint32_t* s1,
+                             uint32_t* s2, uint32_t* s3, uint64_t* free_run, uint32_t* free_cls, uint64_t a,
+                             long long& dsum, uint32_t* err) {
+  const uint32_t t = T.id(), ts = T.size();
+  const uint32_t d0 = r->deg, cls = r->cls;
+  uint32_t d;
+  if (t == 0) {
+    free_run[a] = ~0ull;
+    free_cls[a] = kNoRun;
+  }
+  if (cls == kNoRun) {  // inline: thread j checks the j-th id against the group
+    const uint32_t y = t < d0 ? r->inl[t] : kInf;
+    bool keep = t < d0;
+    if (keep)
+      for (uint64_t i = g0; i < g1; ++i)
+        if (gcols[i] == y) {
+          keep = false;
+          break;
+        }
+    const uint32_t rk = T.scan(keep, &d);
+    if (keep) r->inl[rk] = y;
+    T.sync();
+    if (t >= d && t < kInline) r->inl[t] = kInf;
+  } else {
+    const uint64_t run = r->run;
+    uint32_t* ids = pool + run * kBlockIds;
+    uint32_t* key = hkey + run * kHashSlots;
+    uint32_t* pos = hpos + run * kHashSlots;
+    const uint32_t mask = hmask(cls);
+    uint32_t ndel = 0;
+    // 1: found ids become tombstones; s1 = the position each one freed
+    for (uint64_t i0 = g0; i0 < g1; i0 += ts) {
+      const uint64_t i = i0 + t;
+      uint32_t p = kInf;
+      if (i < g1) {
+        const uint32_t x = gcols[i];
+        uint32_t h = hslot(x, cls);
+        for (uint64_t it = 0; it <= mask; ++it) {
+          const uint32_t k = ld_cg(key + h);
+          if (k == kInf) break;
+          if (k == x) {
+            if (atomicCAS(key + h, x, kTomb) == x) p = pos[h];
+            break;
+          }
+          h = (h + 1) & mask;
+        }
+        s1[i] = p;
+      }
+      uint32_t c;
+      T.scan(p != kInf, &c);
+      ndel += c;
+    }
+    d = d0 - ndel;
+    T.sync();
+    // 2: mark the freed positions
+    for (uint64_t i = g0 + t; i < g1; i += ts) {
+      const uint32_t p = s1[i];
+      if (p != kInf) ids[p] = kInf;
+    }
+    T.sync();
+    // 3: holes (freed positions below d) and survivors (ids left in [d, d0))
+    uint32_t nh = 0, ns = 0;
+    for (uint64_t i0 = g0; i0 < g1; i0 += ts) {
+      const uint64_t i = i0 + t;
+      const uint32_t p = i < g1 ? s1[i] : kInf;
+      const bool hole = p < d;
+      uint32_t c;
+      const uint32_t rk = T.scan(hole, &c);
+      if (hole) s2[g0 + nh + rk] = p;
+      nh += c;
+    }
+    for (uint32_t q0 = d; q0 < d0; q0 += ts) {
+      const uint32_t q = q0 + t;
+      const bool live = q < d0 && ids[q] != kInf;
+      uint32_t c;
+      const uint32_t rk = T.scan(live, &c);
+      if (live) s3[g0 + ns + rk] = q;
+      ns += c;
+    }
+    if (ns != nh) {
+      if (t == 0) *err = 1u;
+      nh = ns < nh ? ns : nh;
+    }
+    T.sync();
+    // 4: survivors move into the holes; their index entries follow
+    for (uint32_t k = t; k < nh; k += ts) {
+      const uint32_t p = s2[g0 + k], q = s3[g0 + k];
+      const uint32_t y = ids[q];
+      ids[p] = y;
+      uint32_t h = hslot(y, cls);
+      bool found = false;
+      for (uint64_t it = 0; it <= mask; ++it) {
+        if (ld_cg(key + h) == y) {
+          pos[h] = p;
+          found = true;
+          break;
+        }
+        h = (h + 1) & mask;
+      }
+      if (!found) *err = 1u;
+    }
+    T.sync();
+    if (d <= icap) {  // back inline; the run is freed
+      const uint32_t y = t < d ? ids[t] : kInf;
+      T.sync();
+      if (t < kInline) r->inl[t] = y;
+      if (t == 0) {
+        r->cls = kNoRun;
+        r->run = 0;
+        free_run[a] = run;
+        free_cls[a] = cls;
+      }
+    } else if (t == 0) {
+      r->inl[0] += ndel;  // tombstones
+    }
+  }
+  if (t == 0) {
+    r->deg = d;
+    dsum += (long long)d - (long long)d0;
+  }
+}
+
+// Inserts: small groups a thread each, mid-sized ones a warp each (mid[]),
+// the largest a CTA each (huge[]).
 __global__ void hinsert_kernel(DynVertex* vtx, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
                                const uint32_t* __restrict__ aff, const uint64_t* __restrict__ gstart,
                                const uint32_t* __restrict__ gcols, const uint32_t* __restrict__ act,
                                const uint64_t* __restrict__ new_run, const uint32_t* __restrict__ new_cls, uint64_t A,
-                               uint32_t icap, uint64_t* free_run, uint32_t* free_cls, long long* delta, uint32_t* err) {
+                               const uint32_t* __restrict__ mid, const uint32_t* __restrict__ nmid,
+                               const uint32_t* __restrict__ huge, const uint32_t* __restrict__ nhuge, uint32_t icap,
+                               uint64_t* free_run, uint32_t* free_cls, long long* delta, uint32_t* err) {
+  __shared__ uint32_t sh[32];
   const uint32_t lane = lane_id();
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   long long dsum = 0;
-  for (uint64_t a = w0; a < A; a += nw) {
-    DynVertex* r = vtx + aff[a];
-    const uint32_t d0 = r->deg, cls0 = r->cls;  // read by every lane before lane 0 rewrites the record
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t g0 = gstart[a], g1 = gstart[a + 1];
-    const uint32_t ac = act[a];
-    uint32_t d = d0;
-    if (ac == kActInline) {  // d0 + group size <= icap <= kInline: one id per lane
+    if (g1 - g0 <= kSmallGroup)
+      hinsert_thread(vtx + aff[a], pool, hkey, hpos, gcols, g0, g1, act[a], new_cls[a], new_run[a], icap, free_run,
+                     free_cls, a, dsum, err);
+  }
+  const Team<false> W{nullptr};
+  const uint32_t NM = *nmid;
+  for (uint64_t b = w0; b < NM; b += nw) {
+    const uint32_t a = mid[b];
+    DynVertex* r = vtx + aff[a];
+    const uint64_t g0 = gstart[a], g1 = gstart[a + 1];
+    if (act[a] == kActInline) {  // d0 + group size <= icap <= kInline: one id per lane
+      const uint32_t d0 = r->deg;
       const uint32_t gs = (uint32_t)(g1 - g0);
       const uint32_t x = lane < gs ? gcols[g0 + lane] : kInf;
       bool fresh = lane < gs;
@@ -668,209 +1070,57 @@ __global__ void hinsert_kernel(DynVertex* vtx, uint32_t* pool, uint32_t* hkey, u
       const uint32_t m = __ballot_sync(0xFFFFFFFFu, fresh);
       __syncwarp();
       if (fresh) r->inl[d0 + __popc(m & lanemask_lt())] = x;
-      d = d0 + __popc(m);
+      if (lane == 0) {
+        r->deg = d0 + __popc(m);
+        dsum += __popc(m);
+      }
     } else {
-      const uint32_t c = new_cls[a];
-      const uint64_t run = new_run[a];
-      uint32_t* ids = pool + run * kBlockIds;
-      uint32_t* key = hkey + run * kHashSlots;
-      uint32_t* pos = hpos + run * kHashSlots;
-      const uint32_t mask = hmask(c);
-      for (uint64_t i0 = g0; i0 < g1; i0 += 32) {
-        const uint64_t i = i0 + lane;
-        uint32_t x = kInf, slot = 0;
-        bool fresh = false, done = i >= g1;
-        if (!done) {
-          x = gcols[i];
-          uint32_t h = hslot(x, c);
-          for (uint64_t it = 0; it <= mask; ++it) {
-            const uint32_t k = ld_cg(key + h);
-            if (k == x) {
-              done = true;
-              break;
-            }
-            if (k == kInf) {
-              const uint32_t o = atomicCAS(key + h, kInf, x);
-              if (o == kInf) {
-                fresh = done = true;
-                slot = h;
-                break;
-              }
-              if (o == x) {
-                done = true;
-                break;
-              }
-            }
-            h = (h + 1) & mask;
-          }
-          if (!done) *err = 1u;
-        }
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, fresh);
-        if (fresh) {
-          const uint32_t p = d + __popc(m & lanemask_lt());
-          ids[p] = x;
-          pos[slot] = p;
-        }
-        d += __popc(m);
-      }
-      __syncwarp();
-      if (ac == kActMove && cls0 == kNoRun && d <= icap) {
-        // an inline list the plan moved (upper bound) that stays within the
-        // inline capacity: back inline, and the new run is freed
-        const uint32_t y = lane < d ? ids[lane] : kInf;
-        __syncwarp();
-        if (lane < kInline) r->inl[lane] = y;
-        if (lane == 0) {
-          free_run[a] = run;
-          free_cls[a] = c;
-        }
-      } else if (lane == 0) {
-        if (ac == kActMove) {
-          r->cls = c;
-          r->run = run;
-        }
-        if (ac != kActKeep) r->inl[0] = 0;  // a fresh index has no tombstones
-      }
+      hinsert_team(W, r, pool, hkey, hpos, gcols, g0, g1, act[a], new_cls[a], new_run[a], icap, free_run, free_cls, a,
+                   dsum, err);
     }
-    if (lane == 0) {
-      r->deg = d;
-      dsum += (long long)d - (long long)d0;
-    }
+  }
+  const Team<true> C{sh};
+  const uint32_t NH = *nhuge;
+  for (uint64_t b = blockIdx.x; b < NH; b += gridDim.x) {  // never an inline action (group > kInline)
+    const uint32_t a = huge[b];
+    hinsert_team(C, vtx + aff[a], pool, hkey, hpos, gcols, gstart[a], gstart[a + 1], act[a], new_cls[a], new_run[a],
+                 icap, free_run, free_cls, a, dsum, err);
+    __syncthreads();  // the record is written before the CTA moves on
   }
   block_add_delta(dsum, delta);
 }
 
-// One warp per affected vertex applies its group of batch ids (delete).
-// s1, s2, s3: scratch with one entry per batch entry (freed positions, the
-// holes among them, the surviving tail positions), each group in its slice.
+// Deletes: small groups a thread each, mid-sized ones a warp each, the
+// largest a CTA each.
 __global__ void hdelete_kernel(DynVertex* vtx, uint32_t* pool, uint32_t* hkey, uint32_t* hpos,
                                const uint32_t* __restrict__ aff, const uint64_t* __restrict__ gstart,
-                               const uint32_t* __restrict__ gcols, uint64_t A, uint32_t icap, uint32_t* s1,
-                               uint32_t* s2, uint32_t* s3, uint64_t* free_run, uint32_t* free_cls, long long* delta,
-                               uint32_t* err) {
-  const uint32_t lane = lane_id();
+                               const uint32_t* __restrict__ gcols, uint64_t A, const uint32_t* __restrict__ mid,
+                               const uint32_t* __restrict__ nmid, const uint32_t* __restrict__ huge,
+                               const uint32_t* __restrict__ nhuge, uint32_t icap, uint32_t* s1, uint32_t* s2,
+                               uint32_t* s3, uint64_t* free_run, uint32_t* free_cls, long long* delta, uint32_t* err) {
+  __shared__ uint32_t sh[32];
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   long long dsum = 0;
-  for (uint64_t a = w0; a < A; a += nw) {
-    DynVertex* r = vtx + aff[a];
-    const uint32_t d0 = r->deg, cls = r->cls;
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A; a += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t g0 = gstart[a], g1 = gstart[a + 1];
-    if (lane == 0) {
-      free_run[a] = ~0ull;
-      free_cls[a] = kNoRun;
-    }
-    uint32_t d;
-    if (cls == kNoRun) {  // inline: lane j checks the j-th id against the group
-      const uint32_t y = lane < d0 ? r->inl[lane] : kInf;
-      bool keep = lane < d0;
-      if (keep)
-        for (uint64_t i = g0; i < g1; ++i)
-          if (gcols[i] == y) {
-            keep = false;
-            break;
-          }
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep);
-      d = __popc(m);
-      const uint32_t z = __shfl_sync(0xFFFFFFFFu, y, kth_bit(m, lane));
-      __syncwarp();
-      if (lane < kInline) r->inl[lane] = lane < d ? z : kInf;
-    } else {
-      const uint64_t run = r->run;
-      uint32_t* ids = pool + run * kBlockIds;
-      uint32_t* key = hkey + run * kHashSlots;
-      uint32_t* pos = hpos + run * kHashSlots;
-      const uint32_t mask = hmask(cls);
-      uint32_t ndel = 0;
-      // 1: found ids become tombstones; s1 = the position each one freed
-      for (uint64_t i0 = g0; i0 < g1; i0 += 32) {
-        const uint64_t i = i0 + lane;
-        uint32_t p = kInf;
-        if (i < g1) {
-          const uint32_t x = gcols[i];
-          uint32_t h = hslot(x, cls);
-          for (uint64_t it = 0; it <= mask; ++it) {
-            const uint32_t k = ld_cg(key + h);
-            if (k == kInf) break;
-            if (k == x) {
-              if (atomicCAS(key + h, x, kTomb) == x) p = pos[h];
-              break;
-            }
-            h = (h + 1) & mask;
-          }
-          s1[i] = p;
-        }
-        ndel += __popc(__ballot_sync(0xFFFFFFFFu, p != kInf));
-      }
-      d = d0 - ndel;
-      __syncwarp();
-      // 2: mark the freed positions
-      for (uint64_t i = g0 + lane; i < g1; i += 32) {
-        const uint32_t p = s1[i];
-        if (p != kInf) ids[p] = kInf;
-      }
-      __syncwarp();
-      // 3: holes (freed positions below d) and survivors (ids left in [d, d0))
-      uint32_t nh = 0, ns = 0;
-      for (uint64_t i0 = g0; i0 < g1; i0 += 32) {
-        const uint64_t i = i0 + lane;
-        const uint32_t p = i < g1 ? s1[i] : kInf;
-        const bool hole = p < d;
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, hole);
-        if (hole) s2[g0 + nh + __popc(m & lanemask_lt())] = p;
-        nh += __popc(m);
-      }
-      for (uint32_t q0 = d; q0 < d0; q0 += 32) {
-        const uint32_t q = q0 + lane;
-        const bool live = q < d0 && ids[q] != kInf;
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, live);
-        if (live) s3[g0 + ns + __popc(m & lanemask_lt())] = q;
-        ns += __popc(m);
-      }
-      if (ns != nh) {
-        if (lane == 0) *err = 1u;
-        nh = ns < nh ? ns : nh;
-      }
-      __syncwarp();
-      // 4: survivors move into the holes; their index entries follow
-      for (uint32_t k0 = 0; k0 < nh; k0 += 32) {
-        const uint32_t k = k0 + lane;
-        if (k < nh) {
-          const uint32_t p = s2[g0 + k], q = s3[g0 + k];
-          const uint32_t y = ids[q];
-          ids[p] = y;
-          uint32_t h = hslot(y, cls);
-          bool found = false;
-          for (uint64_t it = 0; it <= mask; ++it) {
-            if (ld_cg(key + h) == y) {
-              pos[h] = p;
-              found = true;
-              break;
-            }
-            h = (h + 1) & mask;
-          }
-          if (!found) *err = 1u;
-        }
-      }
-      __syncwarp();
-      if (d <= icap) {  // back inline; the run is freed
-        const uint32_t y = lane < d ? ids[lane] : kInf;
-        __syncwarp();
-        if (lane < kInline) r->inl[lane] = y;
-        if (lane == 0) {
-          r->cls = kNoRun;
-          r->run = 0;
-          free_run[a] = run;
-          free_cls[a] = cls;
-        }
-      } else if (lane == 0) {
-        r->inl[0] += ndel;  // tombstones
-      }
-    }
-    if (lane == 0) {
-      r->deg = d;
-      dsum += (long long)d - (long long)d0;
-    }
+    if (g1 - g0 <= kSmallGroup)
+      hdelete_thread(vtx + aff[a], pool, hkey, hpos, gcols, g0, g1, icap, free_run, free_cls, a, dsum, err);
+  }
+  const Team<false> W{nullptr};
+  const uint32_t NM = *nmid;
+  for (uint64_t b = w0; b < NM; b += nw) {
+    const uint32_t a = mid[b];
+    hdelete_team(W, vtx + aff[a], pool, hkey, hpos, gcols, gstart[a], gstart[a + 1], icap, s1, s2, s3, free_run,
+                 free_cls, a, dsum, err);
+  }
+  const Team<true> C{sh};
+  const uint32_t NH = *nhuge;
+  for (uint64_t b = blockIdx.x; b < NH; b += gridDim.x) {
+    const uint32_t a = huge[b];
+    hdelete_team(C, vtx + aff[a], pool, hkey, hpos, gcols, gstart[a], gstart[a + 1], icap, s1, s2, s3, free_run,
+                 free_cls, a, dsum, err);
+    __syncthreads();
   }
   block_add_delta(dsum, delta);
 }
@@ -936,8 +1186,10 @@ byo_status apply_batch_hashed(byo_graph* g, const uint32_t* src, const uint32_t*
   long long* delta = nullptr;
   uint32_t** d_stacks = nullptr;
   uint64_t* d_cap = nullptr;
-  uint64_t A = 0, Bv = 0, NTC = 0, NTF = 0;
+  uint32_t *mid = nullptr, *huge = nullptr, *nsplit = nullptr;  // nsplit: [mid count, huge count]
+  uint64_t A = 0, NTC = 0, NTF = 0;
   uint32_t hflag[2] = {0, 0};  // [0]: an id >= n in the batch, [1]: an index inconsistency
+  std::unique_ptr<ProfScope> phase(new ProfScope("dyn_semisort", s));
   byo_status st = tmp_alloc_t(&rows, B, s, "batch rows");
   if (st == BYO_OK) st = tmp_alloc_t(&cols, B, s, "batch cols");
   if (st == BYO_OK) st = tmp_alloc_t(&flag, 2, s, "batch flags");
@@ -948,36 +1200,40 @@ byo_status apply_batch_hashed(byo_graph* g, const uint32_t* src, const uint32_t*
     cudaMemsetAsync(flag, 0, 2 * sizeof(uint32_t), s);
     cudaMemsetAsync(nA, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(delta, 0, sizeof(long long), s);
+    // semisort: count per source (rows of invalid pairs are skipped), group
+    // starts, scatter into groups
     hsym_kernel<<<grid_for(k, 256), 256, 0, s>>>(src, dst, k, n, rows, cols, flag);
-    note_launch();
-    cudaError_t e = cudaMemcpyAsync(hflag, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    hhist_kernel<<<grid_for(B, 256), 256, 0, s>>>(rows, B, d->vcnt, d->vslot, aff, nA);
+    note_launch(2);
+    unsigned long long hA = 0;
+    cudaError_t e = cudaMemcpyAsync(&hA, nA, sizeof(hA), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflag, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = cuda_status(e, "batch check");
-    else if (hflag[0]) {
+    if (e != cudaSuccess) {
+      st = cuda_status(e, "batch semisort");
+    } else if (hflag[0]) {  // nothing applied; the counters must be zero between batches
+      cudaMemsetAsync(d->vcnt, 0, sizeof(uint32_t) * (n + 1ull), s);
       set_error("batch: vertex id >= n");
       st = BYO_ERR_INVALID_ARG;
     }
-  }
-  // semisort: count per source, group starts, scatter into groups
-  if (st == BYO_OK) {
-    hhist_kernel<<<grid_for(B, 256), 256, 0, s>>>(rows, B, d->vcnt, d->vslot, aff, nA);
-    note_launch();
-    unsigned long long hA = 0;
-    cudaError_t e = cudaMemcpyAsync(&hA, nA, sizeof(hA), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = cuda_status(e, "batch semisort");
     A = hA;
   }
   if (st == BYO_OK && A > 0) {
     st = tmp_alloc_t(&gcnt, A + 1, s, "group sizes");
     if (st == BYO_OK) st = tmp_alloc_t(&gstart, A + 1, s, "group starts");
+    if (st == BYO_OK) st = tmp_alloc_t(&gcols, B + 1, s, "grouped batch");
+    if (st == BYO_OK) st = tmp_alloc_t(&mid, A + 1, s, "warp groups");
+    if (st == BYO_OK) st = tmp_alloc_t(&huge, A + 1, s, "CTA groups");
+    if (st == BYO_OK) st = tmp_alloc_t(&nsplit, 2, s, "group split counts");
     if (st == BYO_OK) {
       hgcount_kernel<<<grid_for(A, 256), 256, 0, s>>>(aff, A, d->vcnt, gcnt);
       note_launch();
-      st = scan_u32_to_u64(gcnt, gstart, A + 1, &Bv, s);
+      st = scan_u32_to_u64(gcnt, gstart, A + 1, nullptr, s);
     }
-    if (st == BYO_OK) st = tmp_alloc_t(&gcols, Bv + 1, s, "grouped batch");
     if (st == BYO_OK) {
+      cudaMemsetAsync(nsplit, 0, 2 * sizeof(uint32_t), s);
+      hsplit_kernel<<<grid_for(A, 256), 256, 0, s>>>(gstart, A, kWarpGroupMax, mid, nsplit, huge, nsplit + 1);
+      note_launch();
       hscatter_kernel<<<grid_for(B, 256), 256, 0, s>>>(rows, cols, B, d->vcnt, d->vslot, gstart, gcols);
       note_launch();
     } else {
@@ -992,6 +1248,7 @@ byo_status apply_batch_hashed(byo_graph* g, const uint32_t* src, const uint32_t*
     cudaMemcpyAsync(d_stacks, d->stacks, sizeof(uint32_t*) * kClasses, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_cap, d->stack_cap, sizeof(uint64_t) * kClasses, cudaMemcpyHostToDevice, s);
   }
+  phase.reset(new ProfScope("dyn_hash_plan", s));
   if (st == BYO_OK && A > 0 && insert) {
     st = tmp_alloc_t(&act, A + 1, s, "actions");
     if (st == BYO_OK) st = tmp_alloc_t(&new_cls, A + 1, s, "new classes");
@@ -1023,6 +1280,7 @@ byo_status apply_batch_hashed(byo_graph* g, const uint32_t* src, const uint32_t*
     if (st == BYO_OK) st = scan_u32_to_u64(nfill, fstart, A + 1, &NTF, s);
     if (st == BYO_OK) st = tmp_alloc_t(&item_c, NTC + 1, s, "clear task items");
     if (st == BYO_OK) st = tmp_alloc_t(&item_f, NTF + 1, s, "fill task items");
+    phase.reset(new ProfScope("dyn_hash_index", s));
     if (st == BYO_OK) {
       if (NTC) {
         chunk_expand_kernel<<<grid_for(A, 256), 256, 0, s>>>(cstart, A, item_c);
@@ -1035,19 +1293,22 @@ byo_status apply_batch_hashed(byo_graph* g, const uint32_t* src, const uint32_t*
                                                               item_f, fstart, NTF, flag + 1);
         note_launch(2);
       }
-      hinsert_kernel<<<grid_for(A * 32, 256), 256, 0, s>>>(d->vtx, d->pool, d->hkey, d->hpos, aff, gstart, gcols, act,
-                                                            new_run, new_cls, A, d->icap, free_run, free_cls, delta,
-                                                            flag + 1);
+      phase.reset(new ProfScope("dyn_hash_apply", s));
+      hinsert_kernel<<<grid_for(A, 256), 256, 0, s>>>(d->vtx, d->pool, d->hkey, d->hpos, aff, gstart, gcols, act,
+                                                       new_run, new_cls, A, mid, nsplit, huge, nsplit + 1, d->icap,
+                                                       free_run, free_cls, delta, flag + 1);
       note_launch();
     }
   }
   if (st == BYO_OK && A > 0 && !insert) {
-    st = tmp_alloc_t(&s1, Bv + 1, s, "freed positions");
-    if (st == BYO_OK) st = tmp_alloc_t(&s2, Bv + 1, s, "holes");
-    if (st == BYO_OK) st = tmp_alloc_t(&s3, Bv + 1, s, "survivors");
+    st = tmp_alloc_t(&s1, B + 1, s, "freed positions");
+    if (st == BYO_OK) st = tmp_alloc_t(&s2, B + 1, s, "holes");
+    if (st == BYO_OK) st = tmp_alloc_t(&s3, B + 1, s, "survivors");
+    phase.reset(new ProfScope("dyn_hash_apply", s));
     if (st == BYO_OK) {
-      hdelete_kernel<<<grid_for(A * 32, 256), 256, 0, s>>>(d->vtx, d->pool, d->hkey, d->hpos, aff, gstart, gcols, A,
-                                                            d->icap, s1, s2, s3, free_run, free_cls, delta, flag + 1);
+      hdelete_kernel<<<grid_for(A, 256), 256, 0, s>>>(d->vtx, d->pool, d->hkey, d->hpos, aff, gstart, gcols, A, mid,
+                                                       nsplit, huge, nsplit + 1, d->icap, s1, s2, s3, free_run,
+                                                       free_cls, delta, flag + 1);
       note_launch();
     }
   }
@@ -1095,7 +1356,12 @@ byo_status apply_batch_hashed(byo_graph* g, const uint32_t* src, const uint32_t*
   tmp_free(s1, s);
   tmp_free(s2, s);
   tmp_free(s3, s);
+  tmp_free(mid, s);
+  tmp_free(huge, s);
+  tmp_free(nsplit, s);
+  phase.reset();
   if (A > 0 && st == BYO_OK) {
+    ProfScope ps("dyn_buckets", s);
     g->buckets_stale = true;
     st = rebuild_buckets(g, s);
     if (st == BYO_OK) g->buckets_stale = false;
@@ -1109,7 +1375,10 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
   if (d->hashed) return apply_batch_hashed(g, src, dst, k, insert, s);
   uint32_t *rows = nullptr, *cols = nullptr;
   uint64_t B = 0;
-  BYO_RETURN_IF(sort_unique_pairs(g->n, src, dst, k, true, s, &rows, &cols, &B));
+  {
+    ProfScope ps("dyn_sort", s);
+    BYO_RETURN_IF(sort_unique_pairs(g->n, src, dst, k, true, s, &rows, &cols, &B));
+  }
   if (B == 0) {
     tmp_free(rows, s);
     tmp_free(cols, s);
@@ -1248,6 +1517,7 @@ byo_status apply_batch(byo_graph* g, const uint32_t* src, const uint32_t* dst, u
   // the batch is applied; if the buckets cannot be re-derived now (no memory
   // for the sort), the next call that reads them does it
   if (st == BYO_OK) {
+    ProfScope ps("dyn_buckets", s);
     g->buckets_stale = true;
     st = rebuild_buckets(g, s);
     if (st == BYO_OK) g->buckets_stale = false;

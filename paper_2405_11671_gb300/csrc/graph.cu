@@ -290,21 +290,42 @@ __global__ void __launch_bounds__(kUniqThreads) unique_write_kernel(const uint64
   }
 }
 
-// keys for grouping vertices by degree bucket, ascending id inside a bucket
+// Keys for grouping vertices by degree bucket, ascending id inside a bucket:
+// (v << kBucketBits) | bucket, written in id order, so that one stable radix
+// pass over the bucket field gives the order.
+constexpr int kBucketBits = 6;
+static_assert(kBuckets <= (1 << kBucketBits), "degree buckets 0..32 fit the bucket field");
+
 template <typename G>
-__global__ void bucket_keys_kernel(G g, int lb, uint64_t* keys, unsigned long long* hist) {
-  __shared__ unsigned long long h[kBuckets];
+__global__ void bucket_keys_kernel(G g, uint64_t* keys, unsigned long long* hist) {
+  __shared__ uint32_t h[kBuckets];  // a CTA counts at most its grid-stride share of n < 2^32
   for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const uint32_t n = g.num_vertices();
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
     int b = degree_bucket(g.degree((uint32_t)v));
-    keys[v] = ((uint64_t)b << lb) | v;
-    atomicAdd(&h[b], 1ull);
+    keys[v] = (v << kBucketBits) | (uint64_t)b;
+    atomicAdd(&h[b], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kBuckets; i += blockDim.x)
-    if (h[i]) atomicAdd(&hist[i], h[i]);
+    if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+// bucket starts = exclusive scan of the bucket sizes (kBuckets + 1 entries)
+__global__ void bucket_starts_kernel(const unsigned long long* __restrict__ hist, uint64_t* bstart) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint64_t acc = 0;
+  for (int b = 0; b < kBuckets; ++b) {
+    bstart[b] = acc;
+    acc += hist[b];
+  }
+  bstart[kBuckets] = acc;
+}
+
+__global__ void high_bits_kernel(const uint64_t* __restrict__ keys, uint64_t n, int shift, uint32_t* out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)(keys[i] >> shift);
 }
 
 __global__ void low32_kernel(const uint64_t* __restrict__ keys, uint64_t n, int lb, uint32_t* out) {
@@ -455,7 +476,6 @@ byo_status unique_write(const uint64_t* sorted, uint64_t cnt, int lb, const uint
 template <typename G>
 byo_status build_buckets(byo_graph* g, G view, cudaStream_t s) {
   uint32_t n = g->n;
-  int lb = bits_for(n > 1 ? n : 2);
   uint64_t *keys = nullptr, *tmp = nullptr, *sorted = nullptr;
   unsigned long long* hist = nullptr;
   BYO_RETURN_IF(tmp_alloc_t(&keys, n, s, "bucket keys"));
@@ -464,26 +484,25 @@ byo_status build_buckets(byo_graph* g, G view, cudaStream_t s) {
   if (st == BYO_OK && !g->vorder) st = dev_alloc_t(&g->vorder, n, "vertex order");
   if (st == BYO_OK && !g->d_bstart) st = dev_alloc_t(&g->d_bstart, kBuckets + 1, "bucket starts");
   if (st == BYO_OK) {
+    ProfScope ps("buckets_keys", s);
     cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kBuckets, s);
-    bucket_keys_kernel<G><<<grid_for(n, 256), 256, 0, s>>>(view, lb, keys, hist); ::byo::note_launch();
+    bucket_keys_kernel<G><<<grid_for(n, 256), 256, 0, s>>>(view, keys, hist); ::byo::note_launch();
+    bucket_starts_kernel<<<1, 32, 0, s>>>(hist, g->d_bstart); ::byo::note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_status(e, "bucket_keys_kernel");
   }
-  if (st == BYO_OK) st = radix_sort_u64(keys, tmp, n, lb + 6, &sorted, s);
   if (st == BYO_OK) {
-    low32_kernel<<<grid_for(n, 256), 256, 0, s>>>(sorted, n, lb, g->vorder); ::byo::note_launch();
+    ProfScope ps("buckets_sort", s);
+    st = radix_sort_u64(keys, tmp, n, kBucketBits, &sorted, s);
+  }
+  if (st == BYO_OK) {
+    ProfScope ps("buckets_order", s);
+    high_bits_kernel<<<grid_for(n, 256), 256, 0, s>>>(sorted, n, kBucketBits, g->vorder); ::byo::note_launch();
     cudaError_t e = cudaGetLastError();
-    unsigned long long h[kBuckets];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g->bstart, g->d_bstart, sizeof(uint64_t) * (kBuckets + 1), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = cuda_status(e, "degree buckets");
-    else {
-      g->bstart[0] = 0;
-      for (int b = 0; b < kBuckets; ++b) g->bstart[b + 1] = g->bstart[b] + h[b];
-      e = cudaMemcpyAsync(g->d_bstart, g->bstart, sizeof(uint64_t) * (kBuckets + 1), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) st = cuda_status(e, "bucket starts");
-    }
   }
   tmp_free(keys, s);
   tmp_free(tmp, s);
