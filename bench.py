@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-schedules", action="store_true", help="skip the schedule comparison")
     ap.add_argument("--sched-reps", type=int, default=5, help="timed repetitions per schedule")
     ap.add_argument("--sample-scale", type=int, default=18, help="RMAT scale of the oracle's bounded sample")
+    ap.add_argument("--rounds", type=int, default=10, help="update rounds of the dynamic workload")
     return ap.parse_args()
 
 
@@ -953,7 +954,7 @@ def main():
         run_batched(args, byo, torch)
         return
     if args.workload == "dynamic":
-        run_dynamic(args, byo, torch)
+        run_dynamic(args, byo, torch, rounds=args.rounds)
         return
     if args.workload == "ablation":
         run_ablation(args, byo, torch)
