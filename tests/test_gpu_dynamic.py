@@ -242,3 +242,40 @@ def test_hashed_index_rebuilds_and_space(byo):
     with pytest.raises(byo.ByoError) as e:
         byo.Graph(n, dev(src), dev(dst), byo.BYO_CSR | byo.BYO_DYN_HASH)
     assert e.value.status == byo.BYO_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("no_inline", [False, True], ids=["inline", "no_inline"])
+def test_hashed_pool_growth_duplicates_and_no_inline(byo, no_inline):
+    """The hash-indexed container outgrowing its pool (the index arrays grow
+    and are copied with it), with and without the inline head; a hub whose
+    group is thousands of copies of a few pairs (the CTA path must admit each
+    id once); and most of the inserted pairs deleted again."""
+    n = 30000
+    rng = np.random.default_rng(5)
+    base_s = rng.integers(0, n, 2000, dtype=np.uint32)
+    base_d = rng.integers(0, n, 2000, dtype=np.uint32)
+    flags = byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE | byo.BYO_DYN_HASH | (byo.BYO_DYN_NO_INLINE if no_inline else 0)
+    with byo.Graph(n, dev(base_s), dev(base_d), flags) as g:
+        dg = oracle.DynGraph(n, base_s, base_d)
+        space0 = byo.byo_space(g.handle)
+        # 6,000 vertices gain about 40 neighbours each: far more runs than the pool's spare blocks
+        hubs = np.repeat(np.arange(6000, dtype=np.uint32), 40)
+        leaves = rng.integers(0, n, len(hubs), dtype=np.uint32)
+        byo.byo_insert_batch(g.handle, dev(hubs), dev(leaves))
+        dg.insert(hubs, leaves)
+        same_contents(byo, g, dg.csr())
+        assert byo.byo_space(g.handle) > space0
+        # vertex 29999: 3,000 copies of 10 pairs
+        dup_d = np.tile(np.arange(100, 110, dtype=np.uint32), 300)
+        dup_s = np.full(len(dup_d), 29999, np.uint32)
+        byo.byo_insert_batch(g.handle, dev(dup_s), dev(dup_d))
+        dg.insert(dup_s, dup_d)
+        same_contents(byo, g, dg.csr())
+        gone = rng.random(len(hubs)) < 0.8
+        byo.byo_delete_batch(g.handle, dev(leaves[gone]), dev(hubs[gone]))
+        dg.delete(leaves[gone], hubs[gone])
+        byo.byo_delete_batch(g.handle, dev(dup_s), dev(dup_d))
+        dg.delete(dup_s, dup_d)
+        ref = dg.csr()
+        same_contents(byo, g, ref)
+        algorithms_match(byo, g, ref, [0, 7000])
