@@ -372,7 +372,8 @@ __device__ __forceinline__ uint32_t chunks(uint32_t len) { return (len + kPartne
 // ids this implementation walks: per edge a->b the shorter out-list, d+(b) at
 // centre a when d+(b) <= d+(a), else N+(a) at centre b (only its ids above b
 // when N+(a) is sorted: kSortedMin <= d+(a) <= smax), nothing when the walked
-// side is the single-entry list of a (see the task rules).  One thread per
+// side is the single-entry list of a (the rules of tc_task_count_kernel and
+// tc_task_fill_kernel below).  One thread per
 // vertex over its out-list (out-lists are short in this order); runs after
 // the sorts.
 __global__ void tc_work_kernel(const RowInfo* __restrict__ row, const uint32_t* __restrict__ dag, uint32_t n,
