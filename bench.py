@@ -651,6 +651,16 @@ def update_method_bytes(torch, ins_s, ins_d, deg_before, deg_after, lb: int):
     return sort_b + merge_b
 
 
+def hashed_insert_bytes(k: int, new_entries: int, touched: int) -> float:
+    """Bytes a batch insert into the hash-indexed container must move: the k
+    pairs read (8 B each); the counting semisort over the 2k symmetrised
+    entries (the source read to count, 4 B, and the entry read and written
+    into its group, 8 + 4 B); one index slot read per entry (4 B); per new
+    stored id its key, position and list slot written (12 B); and per touched
+    vertex its 64-byte record read and written."""
+    return 8.0 * k + 2.0 * k * (4 + 12) + 2.0 * k * 4 + 12.0 * new_entries + 128.0 * touched
+
+
 def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
     """RMAT-24 (ef 16) in the dynamic container, then `rounds` rounds of one
     insert batch of RMAT pairs and one delete batch of earlier pairs
@@ -779,14 +789,17 @@ def run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds):
     ranks = torch.empty(n, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    ins_ms, del_ms, alg_ms = [], [], []
+    ins_ms, del_ms, alg_ms, ins_bytes = [], [], [], []
     for r, (ins_s, ins_d, del_s, del_d) in enumerate(graphgen.dynamic_rounds(n, src, dst, rounds, batch)):
         di, dd_, ds, dd = (dev_u32(torch, x) for x in (ins_s, ins_d, del_s, del_d))
+        touched = int(torch.unique(torch.cat([di, dd_]).long()).numel())
+        m0 = g.m
         torch.cuda.synchronize()
         a, b, c, x1 = ev(), ev(), ev(), ev()
         a.record(stream)
         byo.byo_insert_batch(g.handle, di, dd_)
         b.record(stream)
+        m1 = g.m  # host metadata, updated when the call returns
         byo.byo_delete_batch(g.handle, ds, dd)
         c.record(stream)
         byo.byo_bfs(g.handle, [s0], levels, None, None, want_parents=False)
@@ -797,6 +810,7 @@ def run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds):
         ins_ms.append(a.elapsed_time(b))
         del_ms.append(b.elapsed_time(c))
         alg_ms.append(c.elapsed_time(x1))
+        ins_bytes.append(hashed_insert_bytes(len(ins_s), m1 - m0, touched))
         if g.m != m_rounds[r]:
             raise RuntimeError(f"hashed container: m {g.m} != {m_rounds[r]} after round {r}")
     med = statistics.median
@@ -804,6 +818,8 @@ def run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds):
            "insert_pairs_per_s": round(batch / (med(ins_ms) / 1e3), 1),
            "delete_pairs_per_s": round(batch / (med(del_ms) / 1e3), 1),
            "bfs_cc_pr_ms": round(med(alg_ms), 3), "space_bytes": byo.byo_space(g.handle)}
+    peak, peak_kind = measured_peaks()
+    out["roofline"] = roof_entry("hashed insert batch", med(ins_bytes), med(ins_ms), peak, peak_kind)
     g.close()
     return out
 

@@ -113,3 +113,9 @@ def test_bc_bytes_path():
     n, r, dsum, closer = 3, 3, 4, 2
     want = 16 * n + 8 * n + 4 * r + 2 * (8 * r + 8 * dsum) + 8 * closer + 8 * r + 16 * closer + 16 * r
     assert bench.bc_method_bytes(torch, off, col, lv, 8) == want
+
+
+def test_hashed_insert_bytes():
+    # 10 pairs -> 20 entries: 8 B per pair read, 16 B of semisort and 4 B of
+    # probe per entry; 6 new stored ids at 12 B; 7 touched records at 128 B
+    assert bench.hashed_insert_bytes(10, 6, 7) == 8 * 10 + 20 * 16 + 20 * 4 + 12 * 6 + 128 * 7
