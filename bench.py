@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--sched-reps", type=int, default=5, help="timed repetitions per schedule")
     ap.add_argument("--sample-scale", type=int, default=18, help="RMAT scale of the oracle's bounded sample")
     ap.add_argument("--rounds", type=int, default=10, help="update rounds of the dynamic workload")
+    ap.add_argument("--dyn-scale", type=int, default=24,
+                    help="RMAT scale of the dynamic workload's base graph (batches scale with it)")
     return ap.parse_args()
 
 
@@ -661,7 +663,7 @@ def hashed_insert_bytes(k: int, new_entries: int, touched: int) -> float:
     return 8.0 * k + 2.0 * k * (4 + 12) + 2.0 * k * 4 + 12.0 * new_entries + 128.0 * touched
 
 
-def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
+def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000, scale: int = 24):
     """RMAT-24 (ef 16) in the dynamic container, then `rounds` rounds of one
     insert batch of RMAT pairs and one delete batch of earlier pairs
     (graphgen.dynamic_rounds), each followed by BFS (one source) + CC +
@@ -670,7 +672,10 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
     GPU CSR rebuild of the same edge set."""
     import graphgen
     seed = graphgen.SEEDS["rmat24"]
-    n, src, dst = graphgen.workload("rmat24")
+    if scale == 24:
+        n, src, dst = graphgen.workload("rmat24")
+    else:  # a smaller base (for counter captures of the update kernels)
+        n, src, dst = graphgen.rmat_small(scale, 16, seed)
     g = byo.Graph(n, dev_u32(torch, src), dev_u32(torch, dst), byo.BYO_DYNAMIC | byo.BYO_SYMMETRIZE)
     s0 = int(graphgen.pick_sources(n, src, dst, 1, seed + 1)[0])
     levels = torch.empty((1, n), dtype=torch.int32, device="cuda")
@@ -687,7 +692,8 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     l0 = byo.byo_kernel_launches()
-    for r, (ins_s, ins_d, del_s, del_d) in enumerate(graphgen.dynamic_rounds(n, src, dst, rounds, batch)):
+    for r, (ins_s, ins_d, del_s, del_d) in enumerate(graphgen.dynamic_rounds(n, src, dst, rounds, batch,
+                                                                             scale=scale)):
         # end to end through the C ABI: the round's pairs from pinned host
         # memory, the two updates, the three algorithms, their outputs back
         hs = [pinned_u32(torch, x) for x in (ins_s, ins_d, del_s, del_d)]
@@ -744,7 +750,7 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
     clk = clocks.stop()
     space_sorted = byo.byo_space(g.handle)
     g.close()
-    hashed = run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds)
+    hashed = run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds, scale)
     med = statistics.median
     peak, peak_kind = measured_peaks()
     round_ms = [i + d + x for i, d, x in zip(ins_ms, del_ms, alg_ms)]
@@ -753,8 +759,8 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
             "higher_is_better": True, "n_gpus": 1, "steps": rounds, "warmup": 0,
             "ms_per_step": round(med(round_ms), 3), "dtype": "u32+f32", "data": "synthetic", "scaling": "weak",
             "vs_baseline": None,
-            "config": {"workload": "rmat24-dynamic", "n": n, "m_final": m_rounds[-1], "rounds": rounds, "batch_pairs": batch,
-                       "l2": "inputs larger than L2 (2.1 GB of neighbour ids)"},
+            "config": {"workload": f"rmat{scale}-dynamic", "n": n, "m_final": m_rounds[-1], "rounds": rounds, "batch_pairs": batch,
+                       "l2": f"{4 * m_rounds[-1] / 1e9:.2f} GB of neighbour ids (L2: 129 MB)"},
             "insert_ms_median": round(med(ins_ms), 3), "delete_ms_median": round(med(del_ms), 3),
             "insert_pairs_per_s": round(batch / (med(ins_ms) / 1e3), 1),
             "delete_pairs_per_s": round(batch / (med(del_ms) / 1e3), 1),
@@ -776,7 +782,7 @@ def run_dynamic(args, byo, torch, rounds: int = 10, batch: int = 1_000_000):
     print(json.dumps(line), flush=True)
 
 
-def run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds):
+def run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds, scale=24):
     """The same rounds on the hash-indexed container (BYO_DYN_HASH: semisorted
     batches, unsorted lists, per-run hash indexes): insert, delete and BFS + CC
     + PageRank times per round, and the container's bytes.  Its edge count must
@@ -790,7 +796,8 @@ def run_dynamic_hashed(byo, torch, n, src, dst, s0, rounds, batch, m_rounds):
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
     ins_ms, del_ms, alg_ms, ins_bytes = [], [], [], []
-    for r, (ins_s, ins_d, del_s, del_d) in enumerate(graphgen.dynamic_rounds(n, src, dst, rounds, batch)):
+    for r, (ins_s, ins_d, del_s, del_d) in enumerate(graphgen.dynamic_rounds(n, src, dst, rounds, batch,
+                                                                             scale=scale)):
         di, dd_, ds, dd = (dev_u32(torch, x) for x in (ins_s, ins_d, del_s, del_d))
         touched = int(torch.unique(torch.cat([di, dd_]).long()).numel())
         m0 = g.m
@@ -970,7 +977,8 @@ def main():
         run_batched(args, byo, torch)
         return
     if args.workload == "dynamic":
-        run_dynamic(args, byo, torch, rounds=args.rounds)
+        scale = args.dyn_scale
+        run_dynamic(args, byo, torch, rounds=args.rounds, batch=max(1, 1_000_000 >> max(0, 24 - scale)), scale=scale)
         return
     if args.workload == "ablation":
         run_ablation(args, byo, torch)
