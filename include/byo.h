@@ -387,13 +387,12 @@ byo_status byo_msbfs(const byo_graph* g, const uint32_t* host_sources, uint32_t 
 /*            same meaning as byo_bfs                                        */
 /*   sched    as for byo_bfs (NULL = default)                               */
 /* The first call on a device looks up the array's device address (with     */
-/* that device current) and caches it; make that first call before any     */
-/* stream capture begins.  cudaDeviceReset discards the array, so the      */
-/* cached address is stale afterwards: do not call this entry point on a   */
-/* device after resetting it.  Every call shares the one array: calls that  */
-/* overlap on the GPU (other streams, other host threads) race and must not */
-/* be issued.  Every call ends by reading the kernel's status word back to  */
-/* the host, so it synchronises the stream.                                 */
+/* that device current) and caches it.  cudaDeviceReset discards the       */
+/* array, so the cached address is stale afterwards: do not call this      */
+/* entry point on a device after resetting it.  Every call shares the one  */
+/* array: calls that overlap on the GPU (other streams, other host threads) */
+/* race and must not be issued.  Every call ends by reading the kernel's    */
+/* status word back to the host, so it synchronises the stream.            */
 /* Errors: INVALID_ARG, TIMEOUT, CUDA (the status the kernel reported).     */
 #define BYO_NOALLOC_MAX_VERTICES (1u << 20)
 byo_status byo_bfs_noalloc(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* col, uint32_t source,
